@@ -1,0 +1,74 @@
+"""Exact dense float64 likelihood, gradient and kriging -- oracle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* covariance:  Sigma_ij = C(||s_i - s_j||; theta), eq. 5 with Euclidean distance (Sec. IV).
+* loglik:      eq. 1, l = -n/2 log(2 pi) - 1/2 log|Sigma| - 1/2 z^T Sigma^{-1} z, through a
+               dense Cholesky Sigma = L L^T: log|Sigma| = 2 sum log L_ii, z^T Sigma^{-1} z = ||L^{-1} z||^2.
+* loglik_grad: dl/dtheta_p = 1/2 a^T (dSigma/dtheta_p) a - 1/2 tr(Sigma^{-1} dSigma/dtheta_p),
+               a = Sigma^{-1} z, with Sigma^{-1} formed explicitly (not in the paper).
+* krige:       eq. 4, Z1 = Sigma_12 Sigma_22^{-1} Z2 (zero mean, eq. 3).
+* sample:      z = L e, the synthetic measurement generator of Sec. VIII-D.
+
+Pins: tests/test_oracle_dense.py (eigenvalue log-det, n = 1 and n = 2 closed forms,
+sigma^2 profile identity, permutation invariance, finite differences, explicit
+solve, exact interpolation).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sl
+
+from . import matern as M
+
+
+def distances(xa, ya, xb, yb) -> np.ndarray:
+    """Euclidean distance matrix between point sets a and b (Sec. IV)."""
+    return np.hypot(np.subtract.outer(xa, xb), np.subtract.outer(ya, yb))
+
+
+def covariance(x, y, theta, xb=None, yb=None) -> np.ndarray:
+    """Sigma(theta) (or the cross-covariance to points (xb, yb))."""
+    if xb is None:
+        xb, yb = x, y
+    return M.matern(distances(x, y, xb, yb), *theta)
+
+
+def loglik(x, y, z, theta):
+    """Eq. 1 by dense Cholesky; returns (l, log|Sigma|, z^T Sigma^{-1} z)."""
+    n = len(z)
+    S = covariance(x, y, theta)
+    L = sl.cholesky(S, lower=True)
+    logdet = 2.0 * np.sum(np.log(np.diag(L)))
+    w = sl.solve_triangular(L, z, lower=True)
+    quad = float(w @ w)
+    ll = -0.5 * n * np.log(2.0 * np.pi) - 0.5 * logdet - 0.5 * quad
+    return ll, logdet, quad
+
+
+def loglik_grad(x, y, z, theta):
+    """(l, grad) with grad = dl/d(sigma^2, beta, nu) via the explicit inverse."""
+    n = len(z)
+    R = distances(x, y, x, y)
+    S = M.matern(R, *theta)
+    cf = sl.cho_factor(S, lower=True)
+    Sinv = sl.cho_solve(cf, np.eye(n))
+    a = sl.cho_solve(cf, z)
+    ll, _, _ = loglik(x, y, z, theta)
+    grad = np.empty(3)
+    for p, G in enumerate(M.matern_derivs(R, *theta)):
+        grad[p] = 0.5 * a @ G @ a - 0.5 * np.sum(Sinv * G)
+    return ll, grad
+
+
+def krige(x_obs, y_obs, z_obs, x_new, y_new, theta) -> np.ndarray:
+    """Eq. 4: Sigma_12 Sigma_22^{-1} z_obs at the new locations."""
+    S22 = covariance(x_obs, y_obs, theta)
+    S12 = covariance(x_new, y_new, theta, x_obs, y_obs)
+    return S12 @ sl.cho_solve(sl.cho_factor(S22, lower=True), z_obs)
+
+
+def sample(x, y, theta, e) -> np.ndarray:
+    """z = L e with Sigma(theta) = L L^T (Sec. VIII-D, 'exact computation')."""
+    L = sl.cholesky(covariance(x, y, theta), lower=True)
+    return L @ e
