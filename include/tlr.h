@@ -1,0 +1,144 @@
+/*
+ * tlr.h -- C ABI of the GB300 tile low-rank (TLR) Matérn likelihood library.
+ *
+ * The library evaluates the Gaussian log-likelihood of eq. 1 (Sec. III),
+ *     l(theta) = -n/2 log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 z^T Sigma(theta)^{-1} z,
+ * for the Matérn covariance of eq. 5 (Sec. IV) over n irregular 2-D locations,
+ * with Sigma held in the tile low-rank format of Sec. V: nb x nb tiles, dense
+ * diagonal tiles, off-diagonal tiles U V^T truncated at an absolute threshold
+ * eps.  It also gives the gradient of l in theta (not in the paper) and the
+ * kriging predictor of eq. 4 on the same factor.
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers to contiguous float64 data unless
+ *    stated otherwise; the caller owns them and keeps them alive until the work
+ *    enqueued on `stream` has finished.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls enqueue work on it and return without synchronising, except
+ *    tlr_create / tlr_destroy / tlr_status / tlr_rank_stats, which synchronise.
+ *  - Vectors indexed by point (z, e, outputs) are in the CALLER's point order;
+ *    the internal Morton permutation is applied and undone inside.
+ *  - Return value: TLR_OK (0); -i when argument i (1-based) is invalid (nothing
+ *    is enqueued); a positive TLR_ERR_* code otherwise.  Failures that happen on
+ *    the device (non-SPD pivot, rank cap overflow, wait time-out) are recorded in
+ *    the handle and reported by tlr_status after the stream has drained.
+ *  - The library owns its tile storage, allocated with cudaMalloc in tlr_create
+ *    (and grown there only); everything is released by tlr_destroy.
+ */
+#ifndef TLR_H_
+#define TLR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlr_ctx* tlr_handle;
+typedef void* tlr_stream_t; /* a cudaStream_t */
+
+/* theta = (theta1, theta2, theta3) of eq. 5: variance, range, smoothness. */
+typedef struct {
+  double sigma2;
+  double beta;
+  double nu;
+} tlr_theta;
+
+/* Options.  nb: tile size (Sec. V); eps: absolute truncation threshold of the
+ * off-diagonal tiles (a singular value s of a tile is kept iff s > eps; eps < 0
+ * selects dense mode, every tile dense, the exact full-tile comparator);
+ * rank_cap: largest rank an off-diagonal tile may take (0 = nb/2);
+ * truncate_at_cap: 0 = exceeding rank_cap is an error (TLR_ERR_RANK_CAP),
+ * 1 = keep the rank_cap largest terms; order: 1 = Morton (Z-curve) ordering of
+ * the points before tiling, 0 = keep the caller's order. */
+typedef struct {
+  int nb;
+  double eps;
+  int rank_cap;
+  int truncate_at_cap;
+  int order;
+} tlr_opts;
+
+enum {
+  TLR_OK = 0,
+  TLR_ERR_NOT_SPD = 1,  /* a diagonal pivot <= 0; tlr_status gives the column (1-based, sorted order) */
+  TLR_ERR_RANK_CAP = 2, /* an off-diagonal rank exceeded rank_cap */
+  TLR_ERR_OOM = 3,      /* cudaMalloc failed */
+  TLR_ERR_CUDA = 4,     /* a CUDA launch or runtime call failed */
+  TLR_ERR_TIMEOUT = 5,  /* a device-side wait gave up */
+  TLR_ERR_STATE = 6     /* call out of order (e.g. tlr_loglik before tlr_potrf) */
+};
+
+/* Create a handle for n points (x[i], y[i]) (device pointers, length n).
+ * Copies and (opts->order) Morton-orders the locations and allocates the tile
+ * storage for n, opts->nb and opts->rank_cap.  Synchronises `stream`. */
+int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts,
+               tlr_stream_t stream, tlr_handle* out);
+
+/* Release every device buffer of the handle.  Synchronises the device. */
+int tlr_destroy(tlr_handle h);
+
+/* Sec. IV eq. 5: build the device Bessel-K table for theta and generate the
+ * dense diagonal tiles Sigma_kk (in dense mode every tile).  Restarts the
+ * pipeline: compress and factor must follow. */
+int tlr_matern_generate(tlr_handle h, tlr_theta theta, tlr_stream_t stream);
+
+/* Sec. V: generate and compress every off-diagonal tile to U V^T with the
+ * absolute threshold eps (adaptive cross approximation on generated rows and
+ * columns, then QR + SVD truncation).  No-op in dense mode. */
+int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream);
+
+/* In-place TLR Cholesky Sigma = L L^T (dense POTRF on diagonal tiles,
+ * TRSM/SYRK/low-rank GEMM with recompression off the diagonal; Sec. III
+ * "Cholesky factorization", Sec. VIII-C "TLR matrix-matrix multiplication").
+ * A non-positive pivot sets TLR_ERR_NOT_SPD in the handle. */
+int tlr_potrf(tlr_handle h, tlr_stream_t stream);
+
+/* Eq. 1 on the factor: d_out3[0] = l, d_out3[1] = log|Sigma|,
+ * d_out3[2] = z^T Sigma^{-1} z (device pointer to 3 doubles).  z: length n. */
+int tlr_loglik(tlr_handle h, const double* z, double* d_out3, tlr_stream_t stream);
+
+/* l and dl/dtheta = 1/2 a^T (dSigma/dtheta) a - 1/2 tr(Sigma^{-1} dSigma/dtheta),
+ * a = Sigma^{-1} z (not in the paper).  d_ll: 1 double; d_grad3: 3 doubles
+ * (sigma2, beta, nu).  dSigma tiles are regenerated, never stored. */
+int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, double* d_grad3,
+                    tlr_stream_t stream);
+
+/* Eq. 4: z_new = Sigma_12 Sigma_22^{-1} z_obs at m new locations (x_new, y_new),
+ * Sigma_22 being the factored handle's matrix.  z_obs: length n; z_new: length m. */
+int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_new,
+                const double* y_new, double* z_new, tlr_stream_t stream);
+
+/* Synthetic measurements of Sec. VIII-D: z = L e on the factored handle. */
+int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream);
+
+/* Synchronise the handle's last stream and report the first device-side
+ * failure (TLR_OK if none); *info gets the failing column for
+ * TLR_ERR_NOT_SPD, the offending tile index for TLR_ERR_RANK_CAP. */
+int tlr_status(tlr_handle h, int64_t* info);
+
+/* Rank statistics of the off-diagonal tiles of the current factor (or of the
+ * compressed matrix before tlr_potrf) and the bytes the TLR factor occupies
+ * (dense diagonal tiles + U, V columns actually used).  Synchronises. */
+int tlr_rank_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* bytes);
+
+/* Number of tiles per side (nt) and the tile size of the handle. */
+int tlr_shape(tlr_handle h, int* nt, int* nb);
+
+/* Copy tile (i, j), i >= j, of the handle's current matrix (after
+ * tlr_matern_generate / tlr_compress) or factor (after tlr_potrf) into caller
+ * device buffers, rows and columns in the handle's sorted point order
+ * (tlr_get_perm).  i == j or dense mode: the dense nb x nb tile into U
+ * (column-major, ld nb), *k = nb.  i > j: U and V (nb x k each, column-major,
+ * ld nb) with k the tile's rank; U and V must hold nb * rank_cap doubles.
+ * *k is a host int.  Synchronises `stream`. */
+int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, tlr_stream_t stream);
+
+/* perm[s] = caller index of the s-th point in the handle's sorted order
+ * (device buffer of n int32).  Synchronises `stream`. */
+int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLR_H_ */

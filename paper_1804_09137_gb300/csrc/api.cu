@@ -1,0 +1,400 @@
+// C ABI entry points (include/tlr.h) and the host-side drivers.
+//
+// The driver owns the ordering of the tile algorithm; each step is a batched
+// launch over every tile it touches, enqueued on the caller's stream.  The
+// Morton ordering of the points (setup, once per handle) runs on the host.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+int tlr_launch_trsm_v(tlr_ctx* h, int k, cudaStream_t s);
+int tlr_launch_syrk_lr(tlr_ctx* h, int k, cudaStream_t s);
+int tlr_launch_lr_update(tlr_ctx* h, int k, cudaStream_t s);
+size_t tlr_item_elems(int nb, int kcap);
+
+namespace {
+
+// digamma by upward recurrence to x >= 10 and the asymptotic series
+// psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
+double host_digamma(double x) {
+  double r = 0.0;
+  while (x < 10.0) { r -= 1.0 / x; x += 1.0; }
+  const double f = 1.0 / (x * x);
+  return r + log(x) - 0.5 / x -
+         f * (1.0 / 12 - f * (1.0 / 120 - f * (1.0 / 252 - f * (1.0 / 240 - f * (1.0 / 132)))));
+}
+
+// Morton (Z-curve) order of the points over their bounding square, 16 bits per axis
+std::vector<int> morton_order(const std::vector<double>& x, const std::vector<double>& y) {
+  const size_t n = x.size();
+  double x0 = x[0], x1 = x[0], y0 = y[0], y1 = y[0];
+  for (size_t i = 1; i < n; ++i) {
+    x0 = std::min(x0, x[i]); x1 = std::max(x1, x[i]);
+    y0 = std::min(y0, y[i]); y1 = std::max(y1, y[i]);
+  }
+  const double ext = std::max(x1 - x0, y1 - y0);
+  const double scale = ext > 0 ? 65536.0 / ext : 0.0;
+  std::vector<uint32_t> key(n);
+  for (size_t i = 0; i < n; ++i) {
+    uint32_t qx = (uint32_t)std::min(65535.0, floor((x[i] - x0) * scale));
+    uint32_t qy = (uint32_t)std::min(65535.0, floor((y[i] - y0) * scale));
+    uint32_t k = 0;
+    for (int b = 0; b < 16; ++b) k |= ((qx >> b) & 1u) << (2 * b) | ((qy >> b) & 1u) << (2 * b + 1);
+    key[i] = k;
+  }
+  std::vector<int> p(n);
+  std::iota(p.begin(), p.end(), 0);
+  std::stable_sort(p.begin(), p.end(), [&](int a, int b) { return key[a] < key[b]; });
+  return p;
+}
+
+int set_table_range(tlr_ctx* h, double rmax) {
+  int E = (int)ceil(log2(rmax > 0 ? rmax : 1.0)) + 1;
+  const int e_lo = E - TAB_OCT;
+  if (h->tab_valid && e_lo <= h->mp.e_lo) return 0;  // covered already
+  h->mp.e_lo = e_lo;
+  return 1;
+}
+
+double bbox_diag(const double* x, const double* y, size_t n) {
+  double x0 = x[0], x1 = x[0], y0 = y[0], y1 = y[0];
+  for (size_t i = 1; i < n; ++i) {
+    x0 = std::min(x0, x[i]); x1 = std::max(x1, x[i]);
+    y0 = std::min(y0, y[i]); y1 = std::max(y1, y[i]);
+  }
+  return hypot(x1 - x0, y1 - y0);
+}
+
+template <class T>
+int dmalloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return TLR_ERR_OOM;
+  }
+  return TLR_OK;
+}
+
+void free_ctx(tlr_ctx* h) {
+  void* bufs[] = {h->x, h->y, h->perm, h->D, h->U, h->V, h->rank, h->tab, h->scratch, h->d_stat, h->d_vec, h->d_red};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete h;
+}
+
+#define TRY(x)                 \
+  do {                         \
+    int rc_ = (x);             \
+    if (rc_ != TLR_OK) return rc_; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts, tlr_stream_t stream,
+               tlr_handle* out) {
+  if (n <= 0 || n > (int64_t)INT32_MAX) return -1;
+  if (!x) return -2;
+  if (!y) return -3;
+  if (!opts || opts->nb <= 0 || opts->rank_cap < 0 || !(opts->eps == opts->eps)) return -4;
+  if (!out) return -6;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> hx(n), hy(n);
+  TLR_CUDA_TRY(cudaMemcpyAsync(hx.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(hy.data(), y, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; ++i)
+    if (!(hx[i] == hx[i]) || !(hy[i] == hy[i])) return -2;  // NaN location
+
+  tlr_ctx* h = new tlr_ctx();
+  memset(h, 0, sizeof(*h));
+  h->opts = *opts;
+  h->n = n;
+  h->nb = opts->nb;
+  h->nt = (int)((n + h->nb - 1) / h->nb);
+  h->npad = (int64_t)h->nt * h->nb;
+  h->ntiles = (int64_t)h->nt * (h->nt - 1) / 2;
+  h->dense = opts->eps < 0;
+  int kc = opts->rank_cap > 0 ? opts->rank_cap : std::max(1, h->nb / 2);
+  h->kcap = h->dense ? h->nb : std::min(kc, h->nb);
+
+  std::vector<int> perm(n);
+  if (opts->order) perm = morton_order(hx, hy);
+  else std::iota(perm.begin(), perm.end(), 0);
+  std::vector<double> sx(h->npad, 0.0), sy(h->npad, 0.0);
+  for (int64_t s2 = 0; s2 < n; ++s2) { sx[s2] = hx[perm[s2]]; sy[s2] = hy[perm[s2]]; }
+  h->mp.e_lo = 0;
+  h->tab_valid = 0;
+  set_table_range(h, bbox_diag(hx.data(), hy.data(), n));
+
+  const size_t nb = h->nb;
+  const size_t slot = nb * (size_t)h->kcap;
+  int rc = TLR_OK;
+  rc |= dmalloc(&h->x, h->npad);
+  rc |= dmalloc(&h->y, h->npad);
+  rc |= dmalloc(&h->perm, n);
+  rc |= dmalloc(&h->D, (size_t)h->nt * nb * nb);
+  rc |= dmalloc(&h->U, (size_t)h->ntiles * slot);
+  rc |= dmalloc(&h->V, h->dense ? 1 : (size_t)h->ntiles * slot);
+  rc |= dmalloc(&h->rank, h->ntiles);
+  rc |= dmalloc(&h->tab, TAB_ELEMS);
+  rc |= dmalloc(&h->d_stat, 4);
+  rc |= dmalloc(&h->d_vec, 4 * (size_t)h->npad);
+  h->red_len = 2 * h->nt + 64;
+  rc |= dmalloc(&h->d_red, h->red_len);
+  // workspace: low-rank update items, SYRK items, table nodes, gradient partials
+  const size_t ie = tlr_item_elems(h->nb, h->kcap);
+  const int64_t max_items = std::max<int64_t>(h->ntiles, 1);
+  const int64_t chunk = std::min<int64_t>(max_items, 912);
+  size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
+  ws = std::max(ws, (size_t)(h->nt) * (nb * h->kcap + (size_t)h->kcap * h->kcap));
+  ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->nt * (h->nt + 1) / 2 + 16));
+  h->scratch_elems = ws;
+  rc |= dmalloc(&h->scratch, ws);
+  if (rc != TLR_OK) {
+    free_ctx(h);
+    return TLR_ERR_OOM;
+  }
+  cudaError_t e1 = cudaMemcpyAsync(h->x, sx.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaError_t e2 = cudaMemcpyAsync(h->y, sy.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaError_t e3 = cudaMemcpyAsync(h->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
+  cudaError_t e4 = cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s);
+  cudaError_t e5 = cudaMemsetAsync(h->rank, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
+  cudaError_t e6 = cudaStreamSynchronize(s);
+  if (e1 || e2 || e3 || e4 || e5 || e6) {
+    free_ctx(h);
+    return TLR_ERR_CUDA;
+  }
+  h->last_stream = s;
+  *out = h;
+  return TLR_OK;
+}
+
+int tlr_destroy(tlr_handle h) {
+  if (!h) return -1;
+  cudaDeviceSynchronize();
+  free_ctx(h);
+  return TLR_OK;
+}
+
+int tlr_shape(tlr_handle h, int* nt, int* nb) {
+  if (!h) return -1;
+  if (nt) *nt = h->nt;
+  if (nb) *nb = h->nb;
+  return TLR_OK;
+}
+
+int tlr_matern_generate(tlr_handle h, tlr_theta th, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!(th.sigma2 > 0) || !(th.beta > 0) || !(th.nu > 0) || !isfinite(th.sigma2) || !isfinite(th.beta) ||
+      !isfinite(th.nu))
+    return -2;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  h->mp.sigma2 = th.sigma2;
+  h->mp.beta = th.beta;
+  h->mp.nu = th.nu;
+  h->mp.cnu = 1.0 / (pow(2.0, th.nu - 1.0) * tgamma(th.nu));
+  h->mp.psi = host_digamma(th.nu);
+  TLR_CUDA_TRY(cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s));
+  TRY(tlr_build_table(h, s));
+  TRY(tlr_gen_diag(h, s));
+  if (h->dense) {
+    TRY(tlr_gen_dense_offdiag(h, s));
+    h->state = 2;
+  } else {
+    h->state = 1;
+  }
+  return TLR_OK;
+}
+
+int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!(eps >= 0) && !h->dense) return -2;
+  if (h->state < 1) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  if (h->dense) return TLR_OK;
+  h->opts.eps = eps;
+  if (h->ntiles > 0) TRY(tlr_compress_tiles(h, eps, s));
+  h->state = 2;
+  return TLR_OK;
+}
+
+int tlr_potrf(tlr_handle h, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (h->state != 2) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  TRY(tlr_factor(h, s));
+  h->state = 3;
+  return TLR_OK;
+}
+
+int tlr_loglik(tlr_handle h, const double* z, double* d_out3, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!z) return -2;
+  if (!d_out3) return -3;
+  if (h->state != 3) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  double* w = h->d_vec;
+  TRY(tlr_permute_in(h, z, w, s));
+  TRY(tlr_fwd_solve(h, w, s));
+  TRY(tlr_reduce_loglik(h, w, d_out3, s));
+  return TLR_OK;
+}
+
+int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!e) return -2;
+  if (!z) return -3;
+  if (h->state != 3 || h->dense) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  double* es = h->d_vec;
+  double* zs = h->d_vec + h->npad;
+  TRY(tlr_permute_in(h, e, es, s));
+  TRY(tlr_lmul(h, es, zs, s));
+  TRY(tlr_permute_out(h, zs, z, s));
+  return TLR_OK;
+}
+
+int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_new, const double* y_new,
+                double* z_new, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!z_obs) return -2;
+  if (m < 0) return -3;
+  if (!x_new && m > 0) return -4;
+  if (!y_new && m > 0) return -5;
+  if (!z_new && m > 0) return -6;
+  if (h->state != 3) return TLR_ERR_STATE;
+  if (m == 0) return TLR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  // the table must cover distances to the new points
+  std::vector<double> hx(m + 2), hy(m + 2);
+  TLR_CUDA_TRY(cudaMemcpyAsync(hx.data(), x_new, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(hy.data(), y_new, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // two observed corners (bounding box) join the new points
+  double bx[2], by[2];
+  {
+    std::vector<double> ox(h->n), oy(h->n);
+    TLR_CUDA_TRY(cudaMemcpyAsync(ox.data(), h->x, h->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaMemcpyAsync(oy.data(), h->y, h->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    bx[0] = *std::min_element(ox.begin(), ox.end());
+    bx[1] = *std::max_element(ox.begin(), ox.end());
+    by[0] = *std::min_element(oy.begin(), oy.end());
+    by[1] = *std::max_element(oy.begin(), oy.end());
+  }
+  hx[m] = bx[0]; hy[m] = by[0]; hx[m + 1] = bx[1]; hy[m + 1] = by[1];
+  if (set_table_range(h, bbox_diag(hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
+  double* a = h->d_vec;
+  TRY(tlr_permute_in(h, z_obs, a, s));
+  TRY(tlr_fwd_solve(h, a, s));
+  TRY(tlr_bwd_solve(h, a, s));
+  TRY(tlr_krige(h, a, m, x_new, y_new, z_new, s));
+  return TLR_OK;
+}
+
+int tlr_status(tlr_handle h, int64_t* info) {
+  if (!h) return -1;
+  TLR_CUDA_TRY(cudaStreamSynchronize(h->last_stream));
+  long long st[2];
+  TLR_CUDA_TRY(cudaMemcpy(st, h->d_stat, sizeof(st), cudaMemcpyDeviceToHost));
+  if (info) *info = st[ST_INFO];
+  return (int)st[ST_CODE];
+}
+
+int tlr_rank_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* bytes) {
+  if (!h) return -1;
+  TLR_CUDA_TRY(cudaStreamSynchronize(h->last_stream));
+  std::vector<int> r(std::max<int64_t>(h->ntiles, 1), 0);
+  if (h->ntiles > 0)
+    TLR_CUDA_TRY(cudaMemcpy(r.data(), h->rank, h->ntiles * sizeof(int), cudaMemcpyDeviceToHost));
+  int mn = h->ntiles > 0 ? r[0] : 0, mx = mn;
+  double sum = 0;
+  for (int64_t t = 0; t < h->ntiles; ++t) { mn = std::min(mn, r[t]); mx = std::max(mx, r[t]); sum += r[t]; }
+  if (kmin) *kmin = mn;
+  if (kmax) *kmax = mx;
+  if (kmean) *kmean = h->ntiles > 0 ? sum / h->ntiles : 0.0;
+  if (bytes) *bytes = (int64_t)(8.0 * ((double)h->nt * h->nb * h->nb + (h->dense ? (double)h->ntiles * h->nb * h->nb
+                                                                              : 2.0 * h->nb * sum)));
+  return TLR_OK;
+}
+
+int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (i < 0 || i >= h->nt) return -2;
+  if (j < 0 || j > i) return -3;
+  if (!U) return -4;
+  if (!V && i != j && !h->dense) return -5;
+  if (!k) return -6;
+  if (h->state < 1) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nb = h->nb;
+  if (i == j) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(U, h->D + (size_t)i * nb * nb, nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    *k = h->nb;
+  } else {
+    const int64_t t = tile_index(i, j);
+    const size_t slot = nb * h->kcap;
+    int r = 0;
+    TLR_CUDA_TRY(cudaMemcpyAsync(&r, h->rank + t, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->dense) r = h->nb;
+    if (h->dense) {
+      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + t * slot, nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else if (r > 0) {
+      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TLR_CUDA_TRY(cudaMemcpyAsync(V, h->V + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    *k = r;
+  }
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  return TLR_OK;
+}
+
+int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!perm) return -2;
+  cudaStream_t s = (cudaStream_t)stream;
+  TLR_CUDA_TRY(cudaMemcpyAsync(perm, h->perm, h->n * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  return TLR_OK;
+}
+
+}  // extern "C"
+
+int tlr_factor(tlr_ctx* h, cudaStream_t s) {
+  const int nt = h->nt, nb = h->nb;
+  for (int k = 0; k < nt; ++k) {
+    TRY(tlr_potrf_tile(h, h->D + (size_t)k * nb * nb, nb, nb, (int64_t)k * nb, s));
+    if (k == nt - 1) break;
+    if (h->dense) return TLR_ERR_STATE;  // dense off-diagonal updates: separate path
+    TRY(tlr_launch_trsm_v(h, k, s));
+    TRY(tlr_launch_syrk_lr(h, k, s));
+    TRY(tlr_launch_lr_update(h, k, s));
+  }
+  return TLR_OK;
+}
+
+int tlr_grad_trace(tlr_ctx*, double*, cudaStream_t) { return TLR_ERR_STATE; }
+
+extern "C" int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, double* d_grad3, tlr_stream_t stream) {
+  if (!h) return -1;
+  if (!z) return -2;
+  if (!d_ll) return -3;
+  if (!d_grad3) return -4;
+  return TLR_ERR_STATE;  // trace term pending
+}

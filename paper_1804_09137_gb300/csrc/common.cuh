@@ -1,0 +1,205 @@
+// Internal declarations shared by the CUDA translation units of libtlr.
+// Tile layout: n points in Morton order, padded to npad = nt * nb.  Padded
+// points (index >= n) are "identity" points: covariance 1 with themselves and
+// 0 with every other point, so padded rows/columns factor to the identity and
+// add nothing to log|Sigma| or to the solves.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/tlr.h"
+
+#define TLR_THREADS 256
+
+// Matérn interpolation table: C(r), dC/dbeta(r), dC/dnu(r) on geometric
+// intervals [2^(e_lo + j/4), 2^(e_lo + (j+1)/4)), j = 0..TAB_NINT-1, each a
+// degree TAB_DEG polynomial in t in [-1, 1] (monomial coefficients).
+#define TAB_SUB 4
+#define TAB_OCT 44
+#define TAB_NINT (TAB_SUB * TAB_OCT)
+#define TAB_DEG 12
+#define TAB_NC (TAB_DEG + 1)
+#define TAB_NFUN 3
+#define TAB_ELEMS (TAB_NFUN * TAB_NINT * TAB_NC)
+
+// status words (device): [0] first error code, [1] info
+#define ST_CODE 0
+#define ST_INFO 1
+
+struct MaternParams {
+  double sigma2, beta, nu;
+  double cnu;    // 1 / (2^(nu-1) Gamma(nu))
+  double psi;    // digamma(nu)
+  int e_lo;      // table covers [2^e_lo, 2^(e_lo + TAB_OCT))
+};
+
+struct tlr_ctx {
+  int64_t n, npad;
+  int nb, nt;
+  int64_t ntiles;  // strictly lower tiles nt(nt-1)/2
+  tlr_opts opts;
+  int dense;       // eps < 0: every off-diagonal tile dense
+  int kcap;        // rank capacity of a low-rank tile
+  double* x;       // sorted, padded coordinates (npad)
+  double* y;
+  int* perm;       // perm[s] = caller index of sorted point s (n entries)
+  double* D;       // nt dense diagonal tiles, nb x nb column-major
+  double* U;       // ntiles slots, nb x kcap column-major (dense mode: nb x nb tile in U)
+  double* V;
+  int* rank;       // ntiles ranks (dense mode: nb)
+  double* tab;     // Matérn table (TAB_ELEMS)
+  MaternParams mp;
+  double* scratch; // batched-kernel workspace
+  size_t scratch_elems;
+  size_t item_elems;  // workspace per low-rank update item
+  int items_per_launch;
+  long long* d_stat;  // status words
+  double* d_vec;      // 4 vectors of npad
+  double* d_red;      // reduction partials
+  int red_len;
+  int state;          // 0 created, 1 generated, 2 compressed, 3 factored
+  int tab_valid;
+  cudaStream_t last_stream;
+};
+
+// ---------------------------------------------------------------- helpers
+#define TLR_CUDA_TRY(call)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      fprintf(stderr, "tlr: %s failed: %s (%s:%d)\n", #call,                 \
+              cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+      return TLR_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define TLR_LAUNCH_CHECK()                                                   \
+  do {                                                                       \
+    cudaError_t e_ = cudaGetLastError();                                     \
+    if (e_ != cudaSuccess) {                                                 \
+      fprintf(stderr, "tlr: launch failed: %s (%s:%d)\n",                   \
+              cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+      return TLR_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+static inline int64_t tile_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
+__device__ __forceinline__ int64_t dtile_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
+
+// record the first device-side failure
+__device__ __forceinline__ void set_status(long long* st, long long code, long long info) {
+  if (atomicCAS((unsigned long long*)&st[ST_CODE], 0ull, (unsigned long long)code) == 0ull)
+    st[ST_INFO] = info;
+}
+
+// block-wide sum of one double per thread (blockDim.x == TLR_THREADS); all threads get the result
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (l < (TLR_THREADS / 32)) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) sh[TLR_THREADS / 32] = t;
+  }
+  __syncthreads();
+  return sh[TLR_THREADS / 32];
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide argmax of |v| over threads; returns index (ties: smaller index)
+__device__ __forceinline__ int block_argmax(double a, int idx, double* shv, int* shi, double* outv) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (a2 > a || (a2 == a && i2 < idx)) { a = a2; idx = i2; }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { shv[w] = a; shi[w] = idx; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = (l < TLR_THREADS / 32) ? shv[l] : -1.0;
+    idx = (l < TLR_THREADS / 32) ? shi[l] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+      int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (a2 > a || (a2 == a && i2 < idx)) { a = a2; idx = i2; }
+    }
+    if (l == 0) { shv[TLR_THREADS / 32] = a; shi[TLR_THREADS / 32] = idx; }
+  }
+  __syncthreads();
+  if (outv) *outv = shv[TLR_THREADS / 32];
+  return shi[TLR_THREADS / 32];
+}
+
+// ------------------------------------------------------- Matérn evaluation
+// Interval index and local coordinate t in [-1,1] of r > 0 in the table.
+__device__ __forceinline__ int tab_locate(double r, int e_lo, double* t) {
+  const int hi = __double2hiint(r);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(r));
+  // 2^(q/4) boundaries of the 4 sub-intervals of one octave
+  const double b1 = 1.18920711500272106672, b2 = 1.41421356237309504880, b3 = 1.68179283050742908606;
+  int q = (m >= b1) + (m >= b2) + (m >= b3);
+  double a = q == 0 ? 1.0 : (q == 1 ? b1 : (q == 2 ? b2 : b3));
+  double b = q == 0 ? b1 : (q == 1 ? b2 : (q == 2 ? b3 : 2.0));
+  *t = (2.0 * m - a - b) / (b - a);
+  return TAB_SUB * (e - e_lo) + q;
+}
+
+__device__ __forceinline__ double tab_poly(const double* __restrict__ c, double t) {
+  double s = c[TAB_DEG];
+#pragma unroll
+  for (int d = TAB_DEG - 1; d >= 0; --d) s = fma(s, t, c[d]);
+  return s;
+}
+
+// Evaluate table function f (0: C, 1: dC/dbeta, 2: dC/dnu) at distance r >= 0.
+// Distances below the table (r < 2^e_lo, i.e. 2^-44 of the largest distance)
+// and r = 0 take the r -> 0 limits (sigma2, 0, 0).
+__device__ __forceinline__ double matern_tab(const double* __restrict__ tab, const MaternParams& mp,
+                                             int f, double r) {
+  if (!(r > 0.0)) return f == 0 ? mp.sigma2 : 0.0;
+  double t;
+  int j = tab_locate(r, mp.e_lo, &t);
+  if (j < 0) return f == 0 ? mp.sigma2 : 0.0;
+  if (j >= TAB_NINT) return 0.0;  // beyond the largest distance covered (not reached)
+  return tab_poly(tab + ((size_t)f * TAB_NINT + j) * TAB_NC, t);
+}
+
+// covariance between sorted points p and q (padded points are identity points)
+__device__ __forceinline__ double cov_pts(const double* __restrict__ tab, const MaternParams& mp,
+                                          const double* __restrict__ x, const double* __restrict__ y,
+                                          int64_t n, int64_t p, int64_t q) {
+  if (p >= n || q >= n) return (p == q) ? 1.0 : 0.0;
+  if (p == q) return mp.sigma2;
+  const double dx = x[p] - x[q], dy = y[p] - y[q];
+  return matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy));
+}
+
+// ------------------------------------------------------------ host helpers
+int tlr_build_table(tlr_ctx* h, cudaStream_t s);
+int tlr_gen_diag(tlr_ctx* h, cudaStream_t s);
+int tlr_gen_dense_offdiag(tlr_ctx* h, cudaStream_t s);
+int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s);
+int tlr_factor(tlr_ctx* h, cudaStream_t s);
+int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s);
+int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
+int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
+int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s);
+int tlr_reduce_loglik(tlr_ctx* h, const double* w, double* out3, cudaStream_t s);
+int tlr_grad_quad(tlr_ctx* h, const double* a, double* out2, cudaStream_t s);
+int tlr_grad_trace(tlr_ctx* h, double* out2, cudaStream_t s);
+int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,
+              cudaStream_t s);
+int tlr_permute_in(tlr_ctx* h, const double* src, double* dst, cudaStream_t s);
+int tlr_permute_out(tlr_ctx* h, const double* src, double* dst, cudaStream_t s);

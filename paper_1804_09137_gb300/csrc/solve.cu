@@ -1,0 +1,348 @@
+// Triangular solves on the TLR factor, log-determinant and quadratic form of
+// eq. 1, z = L e (Sec. VIII-D), kriging of eq. 4 and the quadratic part of the
+// likelihood gradient.  Reductions are two-stage (per-block partials summed in
+// a fixed order) so results are bitwise reproducible run to run.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+__global__ void k_perm_in(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ perm,
+                          int64_t n, int64_t npad) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < npad; s += (int64_t)gridDim.x * blockDim.x)
+    dst[s] = (s < n) ? src[perm[s]] : 0.0;
+}
+
+__global__ void k_perm_out(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ perm,
+                           int64_t n) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[s]] = src[s];
+}
+
+// r <- L^{-1} r for one dense lower tile (one CTA)
+__global__ void k_trsv_lower(const double* __restrict__ L, int nb, double* __restrict__ r) {
+  __shared__ double xs[32];
+  const int lane = threadIdx.x & 31;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int w = min(32, nb - b0);
+    if (threadIdx.x < 32) {
+      double xl = 0.0;
+      for (int c = 0; c < w; ++c) {
+        const double part = (lane < c) ? L[(size_t)(b0 + lane) * nb + b0 + c] * xl : 0.0;
+        const double s = warp_sum(part);
+        const double v = (r[b0 + c] - s) / L[(size_t)(b0 + c) * nb + b0 + c];
+        if (lane == c) xl = v;
+      }
+      if (lane < w) { xs[lane] = xl; r[b0 + lane] = xl; }
+    }
+    __syncthreads();
+    for (int row = b0 + w + threadIdx.x; row < nb; row += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l < w; ++l) acc = fma(L[(size_t)(b0 + l) * nb + row], xs[l], acc);
+      r[row] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// r <- L^{-T} r for one dense lower tile (one CTA), backward over row blocks
+__global__ void k_trsv_lower_t(const double* __restrict__ L, int nb, double* __restrict__ r) {
+  __shared__ double xs[32];
+  const int lane = threadIdx.x & 31;
+  const int nblk = (nb + 31) / 32;
+  for (int bb = nblk - 1; bb >= 0; --bb) {
+    const int b0 = bb * 32, w = min(32, nb - b0);
+    if (threadIdx.x < 32) {
+      double xl = 0.0;
+      for (int c = w - 1; c >= 0; --c) {
+        // (L^T x)_c = sum_{l >= c} L[l, c] x_l
+        const double part = (lane > c && lane < w) ? L[(size_t)(b0 + c) * nb + b0 + lane] * xl : 0.0;
+        const double s = warp_sum(part);
+        const double v = (r[b0 + c] - s) / L[(size_t)(b0 + c) * nb + b0 + c];
+        if (lane == c) xl = v;
+      }
+      if (lane < w) { xs[lane] = xl; r[b0 + lane] = xl; }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < b0; a += blockDim.x) {
+      double acc = 0.0;
+      const double* col = L + (size_t)a * nb + b0;
+      for (int l = 0; l < w; ++l) acc = fma(col[l], xs[l], acc);
+      r[a] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// forward update of step k: r_i -= U_ik (V_ik^T r_k), i = k+1 .. nt-1 (one CTA per i)
+__global__ void k_lr_gemv_fwd(int nb, int k, const double* __restrict__ U, const double* __restrict__ V,
+                              size_t slot, const int* __restrict__ rank, double* __restrict__ r) {
+  extern __shared__ double tv[];
+  const int i = k + 1 + blockIdx.x;
+  const int64_t t = dtile_index(i, k);
+  const int kr = rank[t];
+  if (kr == 0) return;
+  const double* Ut = U + t * slot;
+  const double* Vt = V + t * slot;
+  const double* rk = r + (size_t)k * nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < kr; l += nw) {
+    double s = 0.0;
+    for (int q = lane; q < nb; q += 32) s = fma(Vt[(size_t)l * nb + q], rk[q], s);
+    s = warp_sum(s);
+    if (lane == 0) tv[l] = s;
+  }
+  __syncthreads();
+  double* ri = r + (size_t)i * nb;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < kr; ++l) acc = fma(Ut[(size_t)l * nb + a], tv[l], acc);
+    ri[a] -= acc;
+  }
+}
+
+// backward update of step k: r_j -= V_kj (U_kj^T r_k), j = 0 .. k-1 (one CTA per j)
+__global__ void k_lr_gemv_bwd(int nb, int k, const double* __restrict__ U, const double* __restrict__ V,
+                              size_t slot, const int* __restrict__ rank, double* __restrict__ r) {
+  extern __shared__ double tv[];
+  const int j = blockIdx.x;
+  const int64_t t = dtile_index(k, j);
+  const int kr = rank[t];
+  if (kr == 0) return;
+  const double* Ut = U + t * slot;
+  const double* Vt = V + t * slot;
+  const double* rk = r + (size_t)k * nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < kr; l += nw) {
+    double s = 0.0;
+    for (int q = lane; q < nb; q += 32) s = fma(Ut[(size_t)l * nb + q], rk[q], s);
+    s = warp_sum(s);
+    if (lane == 0) tv[l] = s;
+  }
+  __syncthreads();
+  double* rj = r + (size_t)j * nb;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < kr; ++l) acc = fma(Vt[(size_t)l * nb + a], tv[l], acc);
+    rj[a] -= acc;
+  }
+}
+
+// z_i = L_ii e_i + sum_{j<i} U_ij (V_ij^T e_j)   (one CTA per tile row i)
+__global__ void k_lmul(int nb, const double* __restrict__ D, const double* __restrict__ U,
+                       const double* __restrict__ V, size_t slot, const int* __restrict__ rank,
+                       const double* __restrict__ e, double* __restrict__ z, int kcap) {
+  extern __shared__ double tv[];
+  const int i = blockIdx.x;
+  const double* Li = D + (size_t)i * nb * nb;
+  const double* ei = e + (size_t)i * nb;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b <= a; ++b) acc = fma(Li[(size_t)b * nb + a], ei[b], acc);
+    z[(size_t)i * nb + a] = acc;
+  }
+  for (int j = 0; j < i; ++j) {
+    const int64_t t = dtile_index(i, j);
+    const int kr = rank[t];
+    if (kr == 0) continue;
+    const double* Ut = U + t * slot;
+    const double* Vt = V + t * slot;
+    const double* ej = e + (size_t)j * nb;
+    __syncthreads();
+    for (int l = warp; l < kr; l += nw) {
+      double s = 0.0;
+      for (int q = lane; q < nb; q += 32) s = fma(Vt[(size_t)l * nb + q], ej[q], s);
+      s = warp_sum(s);
+      if (lane == 0) tv[l] = s;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      double acc = 0.0;
+      for (int l = 0; l < kr; ++l) acc = fma(Ut[(size_t)l * nb + a], tv[l], acc);
+      z[(size_t)i * nb + a] += acc;
+    }
+  }
+}
+
+// per-tile partial of log|L| (sum of log of the diagonal) and of sum w^2
+__global__ void k_partials(const double* __restrict__ D, int nb, const double* __restrict__ w,
+                           double* __restrict__ part) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  const int k = blockIdx.x;
+  const double* Lk = D + (size_t)k * nb * nb;
+  double ld = 0.0, q = 0.0;
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+    ld += log(Lk[(size_t)a * nb + a]);
+    const double v = w[(size_t)k * nb + a];
+    q = fma(v, v, q);
+  }
+  ld = block_sum(ld, sh);
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) { part[2 * k] = ld; part[2 * k + 1] = q; }
+}
+
+__global__ void k_finish_loglik(const double* __restrict__ part, int nt, int64_t n, double* __restrict__ out3) {
+  if (threadIdx.x != 0) return;
+  double ld = 0.0, q = 0.0;
+  for (int k = 0; k < nt; ++k) { ld += part[2 * k]; q += part[2 * k + 1]; }
+  ld *= 2.0;
+  out3[0] = -0.5 * (double)n * 1.83787706640934548356 - 0.5 * ld - 0.5 * q;  // log(2 pi)
+  out3[1] = ld;
+  out3[2] = q;
+}
+
+// kriging: zn[a] = sum_b C(|new_a - s_b|) alpha_b, one CTA per new point
+__global__ void k_krige(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
+                        const double* __restrict__ y, int64_t n, const double* __restrict__ alpha,
+                        const double* __restrict__ xn, const double* __restrict__ yn, double* __restrict__ zn) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  const int64_t a = blockIdx.x;
+  const double px = xn[a], py = yn[a];
+  double acc = 0.0;
+  for (int64_t b = threadIdx.x; b < n; b += blockDim.x) {
+    const double dx = px - x[b], dy = py - y[b];
+    acc = fma(matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy)), alpha[b], acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) zn[a] = acc;
+}
+
+// quadratic gradient part: per block partials of sum_{a > b} x_a x_b dC/dtheta_p(r_ab), p = beta, nu.
+// Block (I, J, sub): tile pair I >= J, rows of tile I split over gridDim.y sub-blocks.
+__global__ void k_grad_quad(const double* __restrict__ tab_g, const MaternParams mp, const double* __restrict__ x,
+                            const double* __restrict__ y, int64_t n, int nb, const double* __restrict__ av,
+                            double* __restrict__ part) {
+  __shared__ double tb[2 * TAB_NINT * TAB_NC];
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  for (int e = threadIdx.x; e < 2 * TAB_NINT * TAB_NC; e += blockDim.x) tb[e] = tab_g[TAB_NINT * TAB_NC + e];
+  __syncthreads();
+  const int64_t tp = blockIdx.x;  // tile pair index over I >= J: tp = I(I+1)/2 + J
+  int I = (int)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(I + 1) * (I + 2) / 2 <= tp) ++I;
+  while ((int64_t)I * (I + 1) / 2 > tp) --I;
+  const int J = (int)(tp - (int64_t)I * (I + 1) / 2);
+  const int64_t a0 = (int64_t)I * nb, b0 = (int64_t)J * nb;
+  double gb = 0.0, gn = 0.0;
+  const int nsub = gridDim.y;
+  for (int ra = blockIdx.y; ra < nb; ra += nsub) {
+    const int64_t a = a0 + ra;
+    if (a >= n) break;
+    const double xa = x[a], ya = y[a], wa = av[a];
+    const int bend = (I == J) ? ra : nb;  // strictly lower within a diagonal tile pair
+    for (int rb = threadIdx.x; rb < bend; rb += blockDim.x) {
+      const int64_t b = b0 + rb;
+      if (b >= n) break;
+      const double dx = xa - x[b], dy = ya - y[b];
+      const double r = sqrt(dx * dx + dy * dy);
+      const double ww = wa * av[b];
+      if (r > 0.0) {
+        double t;
+        const int j = tab_locate(r, mp.e_lo, &t);
+        if (j >= 0 && j < TAB_NINT) {
+          gb = fma(ww, tab_poly(tb + (size_t)j * TAB_NC, t), gb);
+          gn = fma(ww, tab_poly(tb + (size_t)(TAB_NINT + j) * TAB_NC, t), gn);
+        }
+      }
+    }
+  }
+  gb = block_sum(gb, sh);
+  gn = block_sum(gn, sh);
+  if (threadIdx.x == 0) {
+    const size_t id = (size_t)blockIdx.x * gridDim.y + blockIdx.y;
+    part[2 * id] = gb;
+    part[2 * id + 1] = gn;
+  }
+}
+
+__global__ void k_sum_pairs(const double* __restrict__ part, int64_t cnt, double* __restrict__ out2) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) { s0 += part[2 * i]; s1 += part[2 * i + 1]; }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) { out2[0] = s0; out2[1] = s1; }
+}
+
+}  // namespace
+
+int tlr_permute_in(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) {
+  k_perm_in<<<(unsigned)((h->npad + 255) / 256), 256, 0, s>>>(src, dst, h->perm, h->n, h->npad);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tlr_permute_out(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) {
+  k_perm_out<<<(unsigned)((h->n + 255) / 256), 256, 0, s>>>(src, dst, h->perm, h->n);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
+  const int nb = h->nb, nt = h->nt;
+  const size_t slot = (size_t)nb * h->kcap;
+  const size_t sm = (size_t)h->kcap * sizeof(double);
+  for (int k = 0; k < nt; ++k) {
+    k_trsv_lower<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
+    TLR_LAUNCH_CHECK();
+    if (k < nt - 1) {
+      k_lr_gemv_fwd<<<nt - k - 1, 256, sm, s>>>(nb, k, h->U, h->V, slot, h->rank, r);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  return TLR_OK;
+}
+
+int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
+  const int nb = h->nb, nt = h->nt;
+  const size_t slot = (size_t)nb * h->kcap;
+  const size_t sm = (size_t)h->kcap * sizeof(double);
+  for (int k = nt - 1; k >= 0; --k) {
+    k_trsv_lower_t<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
+    TLR_LAUNCH_CHECK();
+    if (k > 0) {
+      k_lr_gemv_bwd<<<k, 256, sm, s>>>(nb, k, h->U, h->V, slot, h->rank, r);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  return TLR_OK;
+}
+
+int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s) {
+  const size_t sm = (size_t)h->kcap * sizeof(double);
+  k_lmul<<<h->nt, 256, sm, s>>>(h->nb, h->D, h->U, h->V, (size_t)h->nb * h->kcap, h->rank, e, z, h->kcap);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tlr_reduce_loglik(tlr_ctx* h, const double* w, double* out3, cudaStream_t s) {
+  k_partials<<<h->nt, 256, 0, s>>>(h->D, h->nb, w, h->d_red);
+  TLR_LAUNCH_CHECK();
+  k_finish_loglik<<<1, 32, 0, s>>>(h->d_red, h->nt, h->n, out3);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,
+              cudaStream_t s) {
+  for (int64_t a0 = 0; a0 < m; a0 += 65535) {
+    const int64_t cnt = m - a0 < 65535 ? m - a0 : 65535;
+    k_krige<<<(unsigned)cnt, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, a, xn + a0, yn + a0, zn + a0);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+int tlr_grad_quad(tlr_ctx* h, const double* a, double* out2, cudaStream_t s) {
+  const int64_t pairs = (int64_t)h->nt * (h->nt + 1) / 2;
+  const int nsub = 8;
+  const int64_t cnt = pairs * nsub;
+  if ((size_t)(2 * cnt) > h->scratch_elems) return TLR_ERR_OOM;
+  dim3 grid((unsigned)pairs, nsub);
+  k_grad_quad<<<grid, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, h->nb, a, h->scratch);
+  TLR_LAUNCH_CHECK();
+  k_sum_pairs<<<1, 256, 0, s>>>(h->scratch, cnt, out2);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}

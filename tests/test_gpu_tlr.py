@@ -1,0 +1,181 @@
+"""GPU parity of the CUDA path against the CPU oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense as DN
+from oracle import matern as M
+from oracle import tlr as TL
+from paper_1804_09137_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1804_09137_gb300 import tlr
+
+    return tlr
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+def problem(side, theta, n=None):
+    x, y = inputs.jittered_grid(side, n=n)
+    z = DN.sample(x, y, theta, inputs.standard_normal(len(x)))
+    return x, y, z
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.3, 1.0), (1.7, 0.05, 1.5), (0.6, 0.2, 0.8)])
+def test_generation_matches_oracle(T, theta):
+    x, y = inputs.jittered_grid(20)  # n = 400, tiles of 96 (last ragged: 16)
+    h = T.Handle(dev(x), dev(y), nb=96, eps=1e-9)
+    h.matern_generate(theta)
+    p = h.get_perm().cpu().numpy()
+    xs, ys = x[p], y[p]
+    S = DN.covariance(xs, ys, theta)
+    nb = 96
+    for i in range(h.nt):
+        D, _ = h.get_tile(i, i)
+        D = D.cpu().numpy()
+        m = min(nb, len(x) - i * nb)
+        ref = S[i * nb:i * nb + m, i * nb:i * nb + m]
+        assert np.max(np.abs(D[:m, :m] - ref)) <= 1e-13 * theta[0]
+        # padded points are identity points
+        assert np.allclose(D[m:, m:], np.eye(nb - m)) and np.all(D[:m, m:] == 0)
+
+
+@pytest.mark.parametrize("theta,eps", [((1.0, 0.1, 0.5), 1e-9), ((1.0, 0.3, 1.0), 1e-7), ((1.0, 0.03, 0.5), 1e-5)])
+def test_compression_error_bound(T, theta, eps):
+    x, y = inputs.jittered_grid(24)  # n = 576, 5 tiles of 128 (last 64)
+    nb = 128
+    h = T.Handle(dev(x), dev(y), nb=nb, eps=eps, rank_cap=nb)
+    h.matern_generate(theta)
+    h.compress()
+    h.check()
+    p = h.get_perm().cpu().numpy()
+    S = DN.covariance(x[p], y[p], theta)
+    n = len(x)
+    for i in range(h.nt):
+        for j in range(i):
+            U, V = h.get_tile(i, j)
+            U, V = U.cpu().numpy(), V.cpu().numpy()
+            A = np.zeros((nb, nb))
+            ri, rj = min(nb, n - i * nb), min(nb, n - j * nb)
+            A[:ri, :rj] = S[i * nb:i * nb + ri, j * nb:j * nb + rj]
+            err = np.linalg.norm(A - U @ V.T, 2)
+            assert err <= 2.0 * eps, (i, j, err)
+            s = np.linalg.svd(A, compute_uv=False)
+            k_opt = int(np.sum(s > eps))
+            assert U.shape[1] <= k_opt + 2, (i, j, U.shape[1], k_opt)
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.3, 1.0)])
+def test_loglik_small_eps_matches_dense(T, theta):
+    x, y, z = problem(30, theta, n=880)  # 7 tiles of 128, last ragged
+    ll, ld, q = DN.loglik(x, y, z, theta)
+    h = T.Handle(dev(x), dev(y), nb=128, eps=1e-12, rank_cap=128)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    h.check()
+    assert abs(out[0] - ll) <= 1e-9 * abs(ll)
+    assert abs(out[1] - ld) <= 1e-9 * abs(ld)
+    assert abs(out[2] - q) <= 1e-8 * abs(q)
+
+
+def test_single_tile_is_dense(T):
+    theta = (1.3, 0.2, 0.7)
+    x, y, z = problem(15, theta)
+    ll = DN.loglik(x, y, z, theta)[0]
+    h = T.Handle(dev(x), dev(y), nb=256, eps=1e-3)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    assert abs(out[0] - ll) <= 1e-11 * abs(ll)
+
+
+def test_full_rank_equals_dense(T):
+    # eps = 0 with rank_cap = nb keeps every nonzero singular value
+    theta = (1.0, 0.1, 0.5)
+    x, y, z = problem(16, theta)
+    ll = DN.loglik(x, y, z, theta)[0]
+    h = T.Handle(dev(x), dev(y), nb=64, eps=0.0, rank_cap=64)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    h.check()
+    assert abs(out[0] - ll) <= 1e-11 * abs(ll)
+
+
+@pytest.mark.parametrize("eps", [1e-5, 1e-7])
+def test_loglik_matches_cpu_tlr_reference(T, eps):
+    theta = (1.0, 0.3, 1.0)
+    x, y, z = problem(32, theta)
+    nb = 128
+    ll_cpu = TL.loglik(x, y, z, theta, nb=nb, eps=eps)[0]
+    ll_d = DN.loglik(x, y, z, theta)[0]
+    h = T.Handle(dev(x), dev(y), nb=nb, eps=eps, rank_cap=nb)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    h.check()
+    # both approximations sit within the same eps-driven distance of the exact value
+    tol = max(5 * abs(ll_cpu - ll_d), 1e-9 * abs(ll_d))
+    assert abs(out[0] - ll_d) <= tol, (out[0], ll_cpu, ll_d)
+
+
+def test_kriging_matches_oracle(T):
+    theta = (1.0, 0.1, 0.5)
+    x, y, z = problem(30, theta)
+    obs, held = inputs.holdout(len(x), 90)
+    want = DN.krige(x[obs], y[obs], z[obs], x[held], y[held], theta)
+    h = T.Handle(dev(x[obs]), dev(y[obs]), nb=128, eps=1e-12, rank_cap=128)
+    h.factor(theta)
+    got = h.predict(dev(z[obs]), dev(x[held]), dev(y[held])).cpu().numpy()
+    h.check()
+    np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-9)
+
+
+def test_sample_is_cholesky_times_e(T):
+    theta = (1.0, 0.1, 0.5)
+    x, y = inputs.jittered_grid(18)
+    e = inputs.standard_normal(len(x))
+    want = DN.sample(x, y, theta, e)
+    h = T.Handle(dev(x), dev(y), nb=100, eps=1e-13, rank_cap=100, order=False)
+    h.factor(theta)
+    got = h.sample(dev(e)).cpu().numpy()
+    np.testing.assert_allclose(got, want, atol=1e-9)
+
+
+def test_not_spd_reported(T):
+    x, y = inputs.jittered_grid(10)
+    x = np.concatenate([x, x[:3]])  # duplicated locations: singular Sigma
+    y = np.concatenate([y, y[:3]])
+    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-12, rank_cap=64)
+    h.factor((1.0, 0.1, 0.5))
+    rc, info = h.status()
+    assert rc == T.TLR_ERR_NOT_SPD and info >= 1
+
+
+def test_rank_cap_reported(T):
+    x, y = inputs.jittered_grid(16)
+    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-12, rank_cap=2)
+    h.matern_generate((1.0, 0.3, 1.0))
+    h.compress()
+    rc, _ = h.status()
+    assert rc == T.TLR_ERR_RANK_CAP
+
+
+def test_calls_out_of_order(T):
+    x, y = inputs.jittered_grid(8)
+    h = T.Handle(dev(x), dev(y), nb=32, eps=1e-9)
+    z = dev(np.ones(len(x)))
+    with pytest.raises(T.TlrError):
+        h.loglik(z)
+    with pytest.raises(T.TlrError):
+        h.potrf()
