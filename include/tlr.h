@@ -50,13 +50,17 @@ typedef struct {
  * rank_cap: largest rank an off-diagonal tile may take (0 = nb/2);
  * truncate_at_cap: 0 = exceeding rank_cap is an error (TLR_ERR_RANK_CAP),
  * 1 = keep the rank_cap largest terms; order: 1 = Morton (Z-curve) ordering of
- * the points before tiling, 0 = keep the caller's order. */
+ * the points before tiling, 0 = keep the caller's order; dense_rank: an
+ * off-diagonal tile whose eps-rank exceeds it is stored and updated dense
+ * (0 = max(16, nb/16)); tiles are also made dense where a dense x dense
+ * product would land on them during the factorization. */
 typedef struct {
   int nb;
   double eps;
   int rank_cap;
   int truncate_at_cap;
   int order;
+  int dense_rank;
 } tlr_opts;
 
 enum {
@@ -128,11 +132,17 @@ int tlr_shape(tlr_handle h, int* nt, int* nb);
 /* Copy tile (i, j), i >= j, of the handle's current matrix (after
  * tlr_matern_generate / tlr_compress) or factor (after tlr_potrf) into caller
  * device buffers, rows and columns in the handle's sorted point order
- * (tlr_get_perm).  i == j or dense mode: the dense nb x nb tile into U
- * (column-major, ld nb), *k = nb.  i > j: U and V (nb x k each, column-major,
- * ld nb) with k the tile's rank; U and V must hold nb * rank_cap doubles.
- * *k is a host int.  Synchronises `stream`. */
-int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, tlr_stream_t stream);
+ * (tlr_get_perm).  i == j or a dense tile: the dense nb x nb tile into U
+ * (column-major, ld nb; U must hold nb * nb doubles), *k = nb.  A low-rank
+ * tile: U and V (nb x k each, column-major, ld nb) with k the tile's rank;
+ * U and V must hold nb * rank_cap doubles.
+ * *k and *dense are host ints (*dense = 1 for a dense tile).  Synchronises
+ * `stream`. */
+int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, int* dense, tlr_stream_t stream);
+
+/* Number of off-diagonal tiles stored low rank and dense in the current
+ * plan (after tlr_compress, or tlr_matern_generate in dense mode). */
+int tlr_tile_counts(tlr_handle h, int64_t* n_lowrank, int64_t* n_dense);
 
 /* perm[s] = caller index of the s-th point in the handle's sorted order
  * (device buffer of n int32).  Synchronises `stream`. */

@@ -13,10 +13,6 @@
 
 #include "common.cuh"
 
-int tlr_launch_trsm_v(tlr_ctx* h, int k, cudaStream_t s);
-int tlr_launch_syrk_lr(tlr_ctx* h, int k, cudaStream_t s);
-int tlr_launch_lr_update(tlr_ctx* h, int k, cudaStream_t s);
-size_t tlr_item_elems(int nb, int kcap);
 
 namespace {
 
@@ -83,9 +79,13 @@ int dmalloc(T** p, size_t count) {
 }
 
 void free_ctx(tlr_ctx* h) {
-  void* bufs[] = {h->x, h->y, h->perm, h->D, h->U, h->V, h->rank, h->tab, h->scratch, h->d_stat, h->d_vec, h->d_red};
+  void* bufs[] = {h->x,   h->y,      h->perm,   h->D,     h->U,     h->V,      h->rank,
+                  h->tab, h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  free(h->kind);
+  free(h->h_list);
+  free(h->plan_off);
   delete h;
 }
 
@@ -125,7 +125,9 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   h->ntiles = (int64_t)h->nt * (h->nt - 1) / 2;
   h->dense = opts->eps < 0;
   int kc = opts->rank_cap > 0 ? opts->rank_cap : std::max(1, h->nb / 2);
-  h->kcap = h->dense ? h->nb : std::min(kc, h->nb);
+  h->kcap = h->dense ? 1 : std::min(kc, h->nb);
+  h->dense_rank = opts->dense_rank > 0 ? opts->dense_rank : std::max(16, h->nb / 16);
+  if (h->dense_rank > 2 * h->kcap - 8) h->dense_rank = std::max(1, 2 * h->kcap - 8);
 
   std::vector<int> perm(n);
   if (opts->order) perm = morton_order(hx, hy);
@@ -143,20 +145,21 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   rc |= dmalloc(&h->y, h->npad);
   rc |= dmalloc(&h->perm, n);
   rc |= dmalloc(&h->D, (size_t)h->nt * nb * nb);
-  rc |= dmalloc(&h->U, (size_t)h->ntiles * slot);
+  rc |= dmalloc(&h->U, h->dense ? 1 : (size_t)h->ntiles * slot);
   rc |= dmalloc(&h->V, h->dense ? 1 : (size_t)h->ntiles * slot);
   rc |= dmalloc(&h->rank, h->ntiles);
+  rc |= dmalloc(&h->dslot, h->ntiles);
   rc |= dmalloc(&h->tab, TAB_ELEMS);
   rc |= dmalloc(&h->d_stat, 4);
   rc |= dmalloc(&h->d_vec, 4 * (size_t)h->npad);
   h->red_len = 2 * h->nt + 64;
   rc |= dmalloc(&h->d_red, h->red_len);
   // workspace: low-rank update items, SYRK items, table nodes, gradient partials
-  const size_t ie = tlr_item_elems(h->nb, h->kcap);
+  const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap);
   const int64_t max_items = std::max<int64_t>(h->ntiles, 1);
   const int64_t chunk = std::min<int64_t>(max_items, 912);
   size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
-  ws = std::max(ws, (size_t)(h->nt) * (nb * h->kcap + (size_t)h->kcap * h->kcap));
+  ws = std::max(ws, (size_t)std::min<int64_t>(max_items, 912) * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
   ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->nt * (h->nt + 1) / 2 + 16));
   h->scratch_elems = ws;
   rc |= dmalloc(&h->scratch, ws);
@@ -169,6 +172,7 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   cudaError_t e3 = cudaMemcpyAsync(h->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
   cudaError_t e4 = cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s);
   cudaError_t e5 = cudaMemsetAsync(h->rank, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
+  if (e5 == cudaSuccess) e5 = cudaMemsetAsync(h->dslot, 0xff, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
   cudaError_t e6 = cudaStreamSynchronize(s);
   if (e1 || e2 || e3 || e4 || e5 || e6) {
     free_ctx(h);
@@ -209,7 +213,7 @@ int tlr_matern_generate(tlr_handle h, tlr_theta th, tlr_stream_t stream) {
   TRY(tlr_build_table(h, s));
   TRY(tlr_gen_diag(h, s));
   if (h->dense) {
-    TRY(tlr_gen_dense_offdiag(h, s));
+    TRY(tlr_plan(h, s));  // every off-diagonal tile dense, generated by the plan
     h->state = 2;
   } else {
     h->state = 1;
@@ -226,6 +230,7 @@ int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream) {
   if (h->dense) return TLR_OK;
   h->opts.eps = eps;
   if (h->ntiles > 0) TRY(tlr_compress_tiles(h, eps, s));
+  TRY(tlr_plan(h, s));
   h->state = 2;
   return TLR_OK;
 }
@@ -322,25 +327,33 @@ int tlr_rank_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* b
   std::vector<int> r(std::max<int64_t>(h->ntiles, 1), 0);
   if (h->ntiles > 0)
     TLR_CUDA_TRY(cudaMemcpy(r.data(), h->rank, h->ntiles * sizeof(int), cudaMemcpyDeviceToHost));
-  int mn = h->ntiles > 0 ? r[0] : 0, mx = mn;
+  // low-rank tiles only; dense tiles are counted in bytes and in *ndense of tlr_tile_counts
+  int mn = INT32_MAX, mx = 0;
   double sum = 0;
-  for (int64_t t = 0; t < h->ntiles; ++t) { mn = std::min(mn, r[t]); mx = std::max(mx, r[t]); sum += r[t]; }
+  int64_t nlr = 0;
+  for (int64_t t = 0; t < h->ntiles; ++t) {
+    if (h->kind && h->kind[t]) continue;
+    mn = std::min(mn, r[t]); mx = std::max(mx, r[t]); sum += r[t]; ++nlr;
+  }
+  if (nlr == 0) mn = 0;
   if (kmin) *kmin = mn;
   if (kmax) *kmax = mx;
-  if (kmean) *kmean = h->ntiles > 0 ? sum / h->ntiles : 0.0;
-  if (bytes) *bytes = (int64_t)(8.0 * ((double)h->nt * h->nb * h->nb + (h->dense ? (double)h->ntiles * h->nb * h->nb
-                                                                              : 2.0 * h->nb * sum)));
+  if (kmean) *kmean = nlr > 0 ? sum / nlr : 0.0;
+  if (bytes) *bytes = (int64_t)(8.0 * ((double)h->nt * h->nb * h->nb + (double)h->ndense * h->nb * h->nb +
+                                       2.0 * h->nb * sum));
   return TLR_OK;
 }
 
-int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, tlr_stream_t stream) {
+int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, int* dense, tlr_stream_t stream) {
   if (!h) return -1;
   if (i < 0 || i >= h->nt) return -2;
   if (j < 0 || j > i) return -3;
   if (!U) return -4;
   if (!V && i != j && !h->dense) return -5;
   if (!k) return -6;
+  if (!dense) return -7;
   if (h->state < 1) return TLR_ERR_STATE;
+  *dense = 1;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nb = h->nb;
   if (i == j) {
@@ -352,16 +365,30 @@ int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, tlr_s
     int r = 0;
     TLR_CUDA_TRY(cudaMemcpyAsync(&r, h->rank + t, sizeof(int), cudaMemcpyDeviceToHost, s));
     TLR_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h->dense) r = h->nb;
-    if (h->dense) {
-      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + t * slot, nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const bool dense_tile = h->kind && h->kind[t] && h->state >= 2;
+    if (dense_tile) {
+      int sl = -1;
+      TLR_CUDA_TRY(cudaMemcpyAsync(&sl, h->dslot + t, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TLR_CUDA_TRY(cudaStreamSynchronize(s));
+      r = h->nb;
+      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->dpool + (size_t)sl * nb * nb, nb * nb * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s));
     } else if (r > 0) {
+      *dense = 0;
       TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
       TLR_CUDA_TRY(cudaMemcpyAsync(V, h->V + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
+    if (!dense_tile) *dense = 0;
     *k = r;
   }
   TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  return TLR_OK;
+}
+
+int tlr_tile_counts(tlr_handle h, int64_t* n_lowrank, int64_t* n_dense) {
+  if (!h) return -1;
+  if (n_dense) *n_dense = h->kind ? h->ndense : 0;
+  if (n_lowrank) *n_lowrank = h->ntiles - (h->kind ? h->ndense : 0);
   return TLR_OK;
 }
 
@@ -376,15 +403,92 @@ int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream) {
 
 }  // extern "C"
 
-int tlr_factor(tlr_ctx* h, cudaStream_t s) {
-  const int nt = h->nt, nb = h->nb;
+
+// Host plan of one factorization: tile kinds (dense above dense_rank or where
+// fill-in from two dense tiles lands), dense-pool slots, per-step item lists.
+int tlr_plan(tlr_ctx* h, cudaStream_t s) {
+  const int nt = h->nt;
+  const int64_t T = h->ntiles;
+  std::vector<int> rk(std::max<int64_t>(T, 1), 0);
+  if (!h->dense && T > 0) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(rk.data(), h->rank, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  free(h->kind);
+  h->kind = (char*)calloc(std::max<int64_t>(T, 1), 1);
+  if (!h->kind) return TLR_ERR_OOM;
+  for (int64_t t = 0; t < T; ++t) h->kind[t] = h->dense || rk[t] < 0 || rk[t] > h->dense_rank;
+  for (int k = 0; k < nt; ++k)  // symbolic right-looking fill closure
+    for (int j = k + 1; j < nt; ++j)
+      if (h->kind[tile_index(j, k)])
+        for (int i = j + 1; i < nt; ++i)
+          if (h->kind[tile_index(i, k)]) h->kind[tile_index(i, j)] = 1;
+  std::vector<int> slot(std::max<int64_t>(T, 1), -1);
+  int nd = 0;
+  for (int64_t t = 0; t < T; ++t)
+    if (h->kind[t]) slot[t] = nd++;
+  if (nd > h->dcap) {
+    if (h->dpool) cudaFree(h->dpool);
+    h->dpool = nullptr;
+    h->dcap = 0;
+    const int want = nd + nd / 8 + 1;
+    if (cudaMalloc((void**)&h->dpool, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      h->dpool = nullptr;
+      return TLR_ERR_OOM;
+    }
+    h->dcap = want;
+  }
+  h->ndense = nd;
+  // lists: per step 4 phases, then the dense-generation list
+  std::vector<int2> L;
+  std::vector<int64_t> off((size_t)nt * PLAN_PH + 1, 0);
   for (int k = 0; k < nt; ++k) {
-    TRY(tlr_potrf_tile(h, h->D + (size_t)k * nb * nb, nb, nb, (int64_t)k * nb, s));
-    if (k == nt - 1) break;
-    if (h->dense) return TLR_ERR_STATE;  // dense off-diagonal updates: separate path
-    TRY(tlr_launch_trsm_v(h, k, s));
-    TRY(tlr_launch_syrk_lr(h, k, s));
-    TRY(tlr_launch_lr_update(h, k, s));
+    for (int ph = 0; ph < PLAN_PH; ++ph) {
+      off[(size_t)k * PLAN_PH + ph] = (int64_t)L.size();
+      if (ph == PH_TRSM_LR || ph == PH_TRSM_D) {
+        const char want = ph == PH_TRSM_D;
+        for (int i = k + 1; i < nt; ++i)
+          if (h->kind[tile_index(i, k)] == want) L.push_back(make_int2(i, k));
+      } else {
+        const char want = ph == PH_UPD_D;
+        for (int i = k + 2; i < nt; ++i)
+          for (int j = k + 1; j < i; ++j)
+            if (h->kind[tile_index(i, j)] == want) L.push_back(make_int2(i, j));
+      }
+    }
+  }
+  off[(size_t)nt * PLAN_PH] = (int64_t)L.size();
+  const int64_t gen0 = (int64_t)L.size();
+  for (int i = 1; i < nt; ++i)
+    for (int j = 0; j < i; ++j)
+      if (h->kind[tile_index(i, j)]) L.push_back(make_int2(i, j));
+  const int64_t len = std::max<int64_t>((int64_t)L.size(), 1);
+  if (len > h->list_cap) {
+    if (h->d_list) cudaFree(h->d_list);
+    h->d_list = nullptr;
+    if (cudaMalloc((void**)&h->d_list, len * sizeof(int2)) != cudaSuccess) {
+      cudaGetLastError();
+      h->list_cap = 0;
+      return TLR_ERR_OOM;
+    }
+    h->list_cap = len;
+  }
+  free(h->h_list);
+  free(h->plan_off);
+  h->h_list = (int2*)malloc(len * sizeof(int2));
+  h->plan_off = (int64_t*)malloc(off.size() * sizeof(int64_t));
+  if (!h->h_list || !h->plan_off) return TLR_ERR_OOM;
+  if (!L.empty()) memcpy(h->h_list, L.data(), L.size() * sizeof(int2));
+  memcpy(h->plan_off, off.data(), off.size() * sizeof(int64_t));
+  if (!L.empty())
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->d_list, h->h_list, L.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (T > 0)
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->dslot, slot.data(), T * sizeof(int), cudaMemcpyHostToDevice, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors die at return
+  if (nd > 0) {
+    int rc = tlr_gen_dense_tiles(h, h->d_list + gen0, nd, s);
+    if (rc) return rc;
   }
   return TLR_OK;
 }

@@ -24,6 +24,13 @@
 #define TAB_ELEMS (TAB_NFUN * TAB_NINT * TAB_NC)
 
 // status words (device): [0] first error code, [1] info
+// plan phases of one panel step
+#define PH_TRSM_LR 0
+#define PH_TRSM_D 1
+#define PH_UPD_LR 2
+#define PH_UPD_D 3
+#define PLAN_PH 4
+
 #define ST_CODE 0
 #define ST_INFO 1
 
@@ -47,7 +54,17 @@ struct tlr_ctx {
   double* D;       // nt dense diagonal tiles, nb x nb column-major
   double* U;       // ntiles slots, nb x kcap column-major (dense mode: nb x nb tile in U)
   double* V;
-  int* rank;       // ntiles ranks (dense mode: nb)
+  int* rank;       // ntiles ranks (-1 after compression: not compressible below dense_rank)
+  int* dslot;      // ntiles dense-pool slot or -1 (low rank)
+  double* dpool;   // dense off-diagonal tiles, nb x nb each
+  int dcap;        // dense pool capacity (tiles)
+  int ndense;      // dense tiles in use
+  int dense_rank;  // an off-diagonal tile whose rank exceeds this is stored dense
+  char* kind;      // host copy of the tile kinds (1 dense)
+  int2* d_list;    // factorization plan: per-step item lists (device)
+  int2* h_list;    // host copy
+  int64_t list_cap;
+  int64_t* plan_off;  // [nt * PLAN_PH + 1] offsets into the lists
   double* tab;     // Matérn table (TAB_ELEMS)
   MaternParams mp;
   double* scratch; // batched-kernel workspace
@@ -189,9 +206,11 @@ __device__ __forceinline__ double cov_pts(const double* __restrict__ tab, const 
 // ------------------------------------------------------------ host helpers
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_diag(tlr_ctx* h, cudaStream_t s);
-int tlr_gen_dense_offdiag(tlr_ctx* h, cudaStream_t s);
+int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t s);
 int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s);
 int tlr_factor(tlr_ctx* h, cudaStream_t s);
+int tlr_plan(tlr_ctx* h, cudaStream_t s);
+size_t tlr_item_elems(int nb, int kcap);
 int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s);
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);

@@ -1,7 +1,6 @@
-// Dense float64 tile kernels: Cholesky of one diagonal tile (blocked, right
-// looking, 32-column panels), the batched triangular solve L^{-1} X applied to
-// the V factors of a tile column, and the batched C -= A B^T update used by the
-// low-rank SYRK into the diagonal tiles.
+// Dense float64 Cholesky of one diagonal tile: blocked right-looking over
+// 32-column panels (panel POTRF in shared memory, row-parallel panel TRSM,
+// 64 x 64-blocked SYRK of the trailing lower triangle).
 #include "common.cuh"
 
 namespace {
@@ -128,107 +127,6 @@ __global__ void k_syrk_trailing(double* __restrict__ A, int lda, int nrows, int 
   tile_gemm_nt_sub(P, lda, P, lda, C, lda, 64 * bi, 64 * bj, nrows - c1, nrows - c1, w, true);
 }
 
-// batched X_i <- L^{-1} X_i, L: nb x nb lower (ld nb), X_i: nb x k_i (ld nb), 32 columns per block
-// items: V slots of tiles (i, k) for i = k+1 .. nt-1
-__global__ void k_trsm_v(const double* __restrict__ L, int nb, double* __restrict__ Vbase, size_t slot_elems,
-                         const int* __restrict__ rank, int k, int kcap) {
-  const int i = k + 1 + blockIdx.y;
-  const int64_t t = dtile_index(i, k);
-  const int kr = rank[t];
-  const int cb = blockIdx.x * 32;
-  if (cb >= kr) return;
-  const int ncol = min(32, kr - cb);
-  double* X = Vbase + (size_t)t * slot_elems + (size_t)cb * nb;
-  __shared__ double Ls[32][33];
-  __shared__ double Xs[32][33];
-  for (int rb0 = 0; rb0 < nb; rb0 += 32) {
-    const int w = min(32, nb - rb0);
-    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-      const int r = id & 31, c = id >> 5;
-      Ls[r][c] = (r < w && c < w) ? L[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
-      Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < ncol) {  // forward substitution, one column per thread
-      const int c = threadIdx.x;
-      for (int r = 0; r < w; ++r) {
-        double s = Xs[r][c];
-        for (int l = 0; l < r; ++l) s -= Ls[r][l] * Xs[l][c];
-        Xs[r][c] = s / Ls[r][r];
-      }
-    }
-    __syncthreads();
-    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-      const int r = id & 31, c = id >> 5;
-      if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
-    }
-    // rows below: X[r, :] -= L[r, rb0:rb0+w] Xs
-    for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
-      double acc[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-      for (int l = 0; l < w; ++l) {
-        const double lv = L[(size_t)(rb0 + l) * nb + r];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < ncol) X[(size_t)c * nb + r] -= acc[c];
-    }
-    __syncthreads();
-  }
-}
-
-// batched D_i -= T_i U_i^T (lower blocks), T_i in workspace (nb x kcap per item), U_i = U slot of (i, k)
-__global__ void k_syrk_lr_update(double* __restrict__ D, int nb, const double* __restrict__ T, size_t t_elems,
-                                 const double* __restrict__ Ubase, size_t slot_elems, const int* __restrict__ rank,
-                                 int k, int i_first) {
-  const int i = i_first + blockIdx.y;
-  const int64_t t = dtile_index(i, k);
-  const int kr = rank[t];
-  if (kr == 0) return;
-  const int b = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
-  while (bi * (bi + 1) / 2 > b) --bi;
-  const int bj = b - bi * (bi + 1) / 2;
-  tile_gemm_nt_sub(T + (size_t)blockIdx.y * t_elems, nb, Ubase + (size_t)t * slot_elems, nb,
-                   D + (size_t)i * nb * nb, nb, 64 * bi, 64 * bj, nb, nb, kr, true);
-}
-
-// T_i = U_i (V_i^T V_i) for the SYRK of step k; one block per item
-__global__ void k_syrk_lr_prep(int nb, const double* __restrict__ Ubase, const double* __restrict__ Vbase,
-                               size_t slot_elems, const int* __restrict__ rank, int k, int i_first,
-                               double* __restrict__ T, size_t t_elems, double* __restrict__ G, size_t g_elems) {
-  const int i = i_first + blockIdx.x;
-  const int64_t t = dtile_index(i, k);
-  const int kr = rank[t];
-  if (kr == 0) return;
-  const double* U = Ubase + (size_t)t * slot_elems;
-  const double* V = Vbase + (size_t)t * slot_elems;
-  double* Gi = G + (size_t)blockIdx.x * g_elems;
-  double* Ti = T + (size_t)blockIdx.x * t_elems;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // G = V^T V (kr x kr), warp per entry (upper incl. diagonal), mirrored
-  for (int e = warp; e < kr * kr; e += blockDim.x / 32) {
-    const int a = e % kr, c = e / kr;
-    if (a > c) continue;
-    double s = 0.0;
-    for (int r = lane; r < nb; r += 32) s = fma(V[(size_t)a * nb + r], V[(size_t)c * nb + r], s);
-    s = warp_sum(s);
-    if (lane == 0) { Gi[(size_t)c * kr + a] = s; Gi[(size_t)a * kr + c] = s; }
-  }
-  __syncthreads();
-  // T = U G (nb x kr)
-  for (int e = threadIdx.x; e < nb * kr; e += blockDim.x) {
-    const int r = e % nb, c = e / nb;
-    double s = 0.0;
-    for (int l = 0; l < kr; ++l) s = fma(U[(size_t)l * nb + r], Gi[(size_t)c * kr + l], s);
-    Ti[(size_t)c * nb + r] = s;
-  }
-}
-
 }  // namespace
 
 int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s) {
@@ -248,36 +146,3 @@ int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStr
   return TLR_OK;
 }
 
-// launchers used by the factorization driver
-int tlr_launch_trsm_v(tlr_ctx* h, int k, cudaStream_t s) {
-  const int items = h->nt - k - 1;
-  if (items <= 0) return TLR_OK;
-  dim3 grid((h->kcap + 31) / 32, items);
-  k_trsm_v<<<grid, 256, 0, s>>>(h->D + (size_t)k * h->nb * h->nb, h->nb, h->V, (size_t)h->nb * h->kcap, h->rank, k,
-                                h->kcap);
-  TLR_LAUNCH_CHECK();
-  return TLR_OK;
-}
-
-int tlr_launch_syrk_lr(tlr_ctx* h, int k, cudaStream_t s) {
-  const int items = h->nt - k - 1;
-  if (items <= 0) return TLR_OK;
-  const size_t nb = h->nb, kc = h->kcap;
-  const size_t t_elems = nb * kc, g_elems = kc * kc;
-  // workspace: items * (T + G); chunk so that it fits
-  const size_t per = t_elems + g_elems;
-  int chunk = (int)(h->scratch_elems / per);
-  if (chunk > 65535) chunk = 65535;
-  for (int i0 = 0; i0 < items; i0 += chunk) {
-    const int cnt = items - i0 < chunk ? items - i0 : chunk;
-    double* T = h->scratch;
-    double* G = h->scratch + (size_t)cnt * t_elems;
-    k_syrk_lr_prep<<<cnt, 256, 0, s>>>(h->nb, h->U, h->V, nb * kc, h->rank, k, k + 1 + i0, T, t_elems, G, g_elems);
-    TLR_LAUNCH_CHECK();
-    const int Tb = (h->nb + 63) / 64;
-    dim3 grid(Tb * (Tb + 1) / 2, cnt);
-    k_syrk_lr_update<<<grid, 256, 0, s>>>(h->D, h->nb, T, t_elems, h->U, nb * kc, h->rank, k, k + 1 + i0);
-    TLR_LAUNCH_CHECK();
-  }
-  return TLR_OK;
-}

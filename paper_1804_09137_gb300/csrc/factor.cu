@@ -1,0 +1,503 @@
+// TLR Cholesky of Sigma (Sec. III "Cholesky factorization", Sec. V tile
+// low-rank format, Sec. VIII-C TLR GEMM) on hybrid tiles.
+//
+// Compression (Sec. V): each off-diagonal tile is approximated by adaptive
+// cross approximation with partial pivoting, which generates only the rows and
+// columns it pivots on, then recompressed to the eps-truncated SVD.  A tile
+// whose cross approximation has not converged after dense_rank terms is kept
+// dense: near the diagonal the ranks are so high that a dense update (a GEMM)
+// is cheaper than low-rank recompression.  The host closes the dense set under
+// fill-in (dense (i,k) and (j,k) make (i,j) dense), so a dense x dense product
+// never lands in a low-rank tile.
+//
+// Factorization, right looking, panel step k = 0 .. nt-1:
+//   POTRF  D_k = L_kk L_kk^T                              (dense.cu)
+//   TRSM   L_ik = A_ik L_kk^{-T}: low rank V_ik <- L_kk^{-1} V_ik; dense A_ik <- A_ik L_kk^{-T}
+//   SYRK   D_i -= L_ik L_ik^T                             (batched GEMM, lower blocks)
+//   GEMM   A_ij -= L_ik L_jk^T, i > j > k: low-rank targets recompressed to eps
+//          (one CTA per tile), dense targets by batched GEMM.
+#include "recompress.cuh"
+
+namespace {
+
+// ------------------------------------------------------------- compression
+__global__ void k_aca_compress(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
+                               const double* __restrict__ y, int64_t n, TlrView v, int64_t t0, double eps,
+                               int aca_max, int Kmax, int trunc_cap, double* __restrict__ ws, size_t item_elems,
+                               long long* __restrict__ st) {
+  extern __shared__ double dsm[];
+  const int nb = v.nb;
+  double* row = dsm;
+  double* col = dsm + nb;
+  int* used = (int*)(dsm + 2 * nb);
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  const int64_t t = t0 + blockIdx.x;
+  int ti, tj;
+  decode_lower(t, &ti, &tj);
+  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  const int64_t pi0 = (int64_t)ti * nb, pj0 = (int64_t)tj * nb;
+  const int mi = (int)min((int64_t)nb, n - pi0), mj = (int)min((int64_t)nb, n - pj0);
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) used[a] = (a >= mi);
+  const double tol = eps * 0.125;
+  int istar = 0, k = 0, nsmall = 0, conv = 0;
+  __syncthreads();
+  while (true) {
+    if (k >= aca_max) break;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      double val = 0.0;
+      if (b < mj) {
+        val = cov_pts(tab, mp, x, y, n, pi0 + istar, pj0 + b);
+        for (int l = 0; l < k; ++l) val = fma(-w.Up[(size_t)l * nb + istar], w.Vp[(size_t)l * nb + b], val);
+      }
+      row[b] = val;
+    }
+    if (threadIdx.x == 0) used[istar] = 1;
+    double av = -1.0, rmax;
+    int ai = 0x7fffffff;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double a = fabs(row[b]);
+      if (a > av) { av = a; ai = b; }
+    }
+    const int jstar = block_argmax(av, ai, sh, shi, &rmax);
+    if (!(rmax > 1e-3 * tol)) {  // residual row (numerically) zero: sample another row
+      if (++nsmall >= 3) { conv = 1; break; }
+      if (threadIdx.x == 0) {
+        int nxt = -1;
+        for (int s2 = 1; s2 <= nb; ++s2) {
+          const int cand = (int)(((int64_t)istar + (int64_t)97 * s2) % nb);
+          if (!used[cand]) { nxt = cand; break; }
+        }
+        shi[0] = nxt;
+      }
+      __syncthreads();
+      const int nxt = shi[0];
+      __syncthreads();
+      if (nxt < 0) { conv = 1; break; }
+      istar = nxt;
+      continue;
+    }
+    const double delta = row[jstar];
+    double pu = 0.0, pv = 0.0;
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      double val = 0.0;
+      if (a < mi) {
+        val = cov_pts(tab, mp, x, y, n, pi0 + a, pj0 + jstar);
+        for (int l = 0; l < k; ++l) val = fma(-w.Vp[(size_t)l * nb + jstar], w.Up[(size_t)l * nb + a], val);
+      }
+      col[a] = val;
+      w.Up[(size_t)k * nb + a] = val;
+      const double rv = row[a] / delta;
+      w.Vp[(size_t)k * nb + a] = rv;
+      pu = fma(val, val, pu);
+      pv = fma(rv, rv, pv);
+    }
+    const double nu2 = block_sum(pu, sh);
+    const double nv2 = block_sum(pv, sh);
+    ++k;
+    if (sqrt(nu2 * nv2) <= tol) {
+      if (++nsmall >= 2) { conv = 1; break; }
+    } else {
+      nsmall = 0;
+    }
+    av = -1.0;
+    ai = 0x7fffffff;
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      if (!used[a]) {
+        const double val = fabs(col[a]);
+        if (val > av) { av = val; ai = a; }
+      }
+    }
+    double cm;
+    const int nxt = block_argmax(av, ai, sh, shi, &cm);
+    if (cm < 0.0) { conv = 1; break; }  // every row used: the cross approximation is exact
+    istar = nxt;
+  }
+  if (!conv) {  // not compressible within aca_max terms: stored dense
+    if (threadIdx.x == 0) v.rank[t] = -1;
+    return;
+  }
+  __syncthreads();
+  const int kr = cta_recompress(w, nb, k, eps, v.kcap, trunc_cap, tileU(v, t), tileV(v, t), st, t, sh, shi);
+  if (threadIdx.x == 0) v.rank[t] = kr;
+}
+
+// dense generation of listed tiles (Sigma_ij into the dense pool)
+__global__ void k_gen_dense_list(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
+                                 const double* __restrict__ y, int64_t n, TlrView v, const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.y];
+  const int64_t t = dtile_index(it.x, it.y);
+  double* A = tileA(v, t);
+  const int nb = v.nb;
+  const int64_t nn = (int64_t)nb * nb;
+  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(id % nb), b = (int)(id / nb);
+    A[id] = cov_pts(tab, mp, x, y, n, (int64_t)it.x * nb + a, (int64_t)it.y * nb + b);
+  }
+}
+
+// ------------------------------------------------------------------- TRSM
+// low rank: V_ik <- L_kk^{-1} V_ik, items (i, k); 32 columns per CTA
+__global__ void k_trsm_lr(TlrView v, const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.y];
+  const int64_t t = dtile_index(it.x, it.y);
+  const int kr = v.rank[t];
+  const int cb = blockIdx.x * 32;
+  if (cb >= kr) return;
+  const int nb = v.nb;
+  const int ncol = min(32, kr - cb);
+  const double* L = diagT(v, it.y);
+  double* X = tileV(v, t) + (size_t)cb * nb;
+  __shared__ double Ls[32][33];
+  __shared__ double Xs[32][33];
+  for (int rb0 = 0; rb0 < nb; rb0 += 32) {
+    const int w = min(32, nb - rb0);
+    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+      const int r = id & 31, c = id >> 5;
+      Ls[r][c] = (r < w && c < w) ? L[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
+      Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < ncol) {
+      const int c = threadIdx.x;
+      for (int r = 0; r < w; ++r) {
+        double s = Xs[r][c];
+        for (int l = 0; l < r; ++l) s -= Ls[r][l] * Xs[l][c];
+        Xs[r][c] = s / Ls[r][r];
+      }
+    }
+    __syncthreads();
+    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+      const int r = id & 31, c = id >> 5;
+      if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
+    }
+    for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
+      double acc[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+      for (int l = 0; l < w; ++l) {
+        const double lv = L[(size_t)(rb0 + l) * nb + r];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < ncol) X[(size_t)c * nb + r] -= acc[c];
+    }
+    __syncthreads();
+  }
+}
+
+// dense: A_ik <- A_ik L_kk^{-T}, columns c0 .. c0+w of every row (row per thread)
+__global__ void k_trsm_d_panel(TlrView v, const int2* __restrict__ items, int c0, int w) {
+  __shared__ double Ls[32][33];
+  const int2 it = items[blockIdx.y];
+  const int nb = v.nb;
+  const double* L = diagT(v, it.y);
+  double* A = tileA(v, dtile_index(it.x, it.y));
+  for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+    const int r = id & 31, c = id >> 5;
+    Ls[r][c] = (r < w && c < w) ? L[(size_t)(c0 + c) * nb + c0 + r] : 0.0;
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  double xr[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) xr[c] = (c < w) ? A[(size_t)(c0 + c) * nb + r] : 0.0;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < w) {
+      double s = xr[c];
+#pragma unroll
+      for (int l = 0; l < 32; ++l)
+        if (l < c) s -= xr[l] * Ls[c][l];
+      xr[c] = s / Ls[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c < w) A[(size_t)(c0 + c) * nb + r] = xr[c];
+}
+
+// dense: A_ik[:, c1:] -= A_ik[:, c0:c1] L_kk[c1:, c0:c1]^T
+__global__ void k_trsm_d_trail(TlrView v, const int2* __restrict__ items, int c0, int w) {
+  const int2 it = items[blockIdx.y];
+  const int nb = v.nb, c1 = c0 + w;
+  const double* L = diagT(v, it.y);
+  double* A = tileA(v, dtile_index(it.x, it.y));
+  cta_gemm_blocks(nb, nb - c1, w, -1.0, A + (size_t)c0 * nb, nb, 0, L + (size_t)c0 * nb + c1, nb, 1, 1.0,
+                  A + (size_t)c1 * nb, nb, blockIdx.x, gridDim.x, 0);
+}
+
+// ----------------------------------------------------------------- SYRK
+// descriptor of D_i -= L_ik L_ik^T for i = i0 + blockIdx.x (one CTA per i)
+__global__ void k_syrk_prep(TlrView v, int k, int i0, GemmDesc* __restrict__ desc, double* __restrict__ ws,
+                            size_t ws_elems) {
+  const int i = i0 + blockIdx.x;
+  const int64_t t = dtile_index(i, k);
+  const int nb = v.nb;
+  GemmDesc d;
+  d.C = diagT(v, i);
+  d.lower = 1;
+  if (v.dslot[t] >= 0) {
+    d.P = tileA(v, t); d.Q = d.P; d.r = nb;
+  } else {
+    const int kr = v.rank[t];
+    d.Q = tileU(v, t);
+    d.r = kr;
+    double* G = ws + (size_t)blockIdx.x * ws_elems;
+    double* T = G + (size_t)v.kcap * v.kcap;
+    d.P = T;
+    if (kr > 0) {
+      cta_gemm(kr, kr, nb, 1.0, tileV(v, t), nb, 1, tileV(v, t), nb, 0, 0.0, G, kr);   // G = V^T V
+      cta_gemm(nb, kr, kr, 1.0, tileU(v, t), nb, 0, G, kr, 0, 0.0, T, nb);             // T = U G
+    }
+  }
+  if (threadIdx.x == 0) desc[blockIdx.x] = d;
+}
+
+// C -= P Q^T, one 64 x 64 block per CTA
+__global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
+  const GemmDesc d = desc[blockIdx.y];
+  if (d.r <= 0) return;
+  cta_gemm_blocks(nb, nb, d.r, -1.0, d.P, nb, 0, d.Q, nb, 1, 1.0, d.C, nb, blockIdx.x, gridDim.x, d.lower);
+}
+
+// ---------------------------------------------------------------- updates
+// low-rank target A_ij -= L_ik L_jk^T with recompression; items (i, j), step k
+__global__ void k_upd_lr(TlrView v, int k, const int2* __restrict__ items, double eps, int Kmax, int trunc_cap,
+                         double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  const int2 it = items[blockIdx.x];
+  const int i = it.x, j = it.y, nb = v.nb;
+  const int64_t tij = dtile_index(i, j), tik = dtile_index(i, k), tjk = dtile_index(j, k);
+  const bool dik = v.dslot[tik] >= 0, djk = v.dslot[tjk] >= 0;
+  const int k0 = v.rank[tij];
+  const int k1 = dik ? nb : v.rank[tik];
+  const int k2 = djk ? nb : v.rank[tjk];
+  if (k1 == 0 || k2 == 0) return;
+  if (dik && djk) {  // excluded by the fill closure
+    if (threadIdx.x == 0) set_status(st, TLR_ERR_STATE, tij);
+    return;
+  }
+  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  double* Uij = tileU(v, tij);
+  double* Vij = tileV(v, tij);
+  for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) { w.Up[e] = Uij[e]; w.Vp[e] = Vij[e]; }
+  int K;
+  double* Un = w.Up + (size_t)k0 * nb;  // new columns
+  double* Vn = w.Vp + (size_t)k0 * nb;
+  if (!dik && !djk) {
+    const double* Uik = tileU(v, tik);
+    const double* Vik = tileV(v, tik);
+    const double* Ujk = tileU(v, tjk);
+    const double* Vjk = tileV(v, tjk);
+    cta_gemm(k1, k2, nb, 1.0, Vik, nb, 1, Vjk, nb, 0, 0.0, w.W, k1);  // W = V_ik^T V_jk
+    if (k2 <= k1) {  // [-U_ik W] [U_jk]^T
+      cta_gemm(nb, k2, k1, -1.0, Uik, nb, 0, w.W, k1, 0, 0.0, Un, nb);
+      for (size_t e = threadIdx.x; e < (size_t)nb * k2; e += blockDim.x) Vn[e] = Ujk[e];
+      K = k0 + k2;
+    } else {  // [-U_ik] [U_jk W^T]^T
+      cta_gemm(nb, k1, k2, 1.0, Ujk, nb, 0, w.W, k1, 1, 0.0, Vn, nb);
+      for (size_t e = threadIdx.x; e < (size_t)nb * k1; e += blockDim.x) Un[e] = -Uik[e];
+      K = k0 + k1;
+    }
+  } else if (dik) {  // dense L_ik: [-(A_ik V_jk)] [U_jk]^T
+    cta_gemm(nb, k2, nb, -1.0, tileA(v, tik), nb, 0, tileV(v, tjk), nb, 0, 0.0, Un, nb);
+    const double* Ujk = tileU(v, tjk);
+    for (size_t e = threadIdx.x; e < (size_t)nb * k2; e += blockDim.x) Vn[e] = Ujk[e];
+    K = k0 + k2;
+  } else {  // dense L_jk: [-U_ik] [A_jk V_ik]^T
+    cta_gemm(nb, k1, nb, 1.0, tileA(v, tjk), nb, 0, tileV(v, tik), nb, 0, 0.0, Vn, nb);
+    const double* Uik = tileU(v, tik);
+    for (size_t e = threadIdx.x; e < (size_t)nb * k1; e += blockDim.x) Un[e] = -Uik[e];
+    K = k0 + k1;
+  }
+  __syncthreads();
+  const int kr = cta_recompress(w, nb, K, eps, v.kcap, trunc_cap, Uij, Vij, st, tij, sh, shi);
+  if (threadIdx.x == 0) v.rank[tij] = kr;
+}
+
+// dense target A_ij -= L_ik L_jk^T: descriptor P Q^T (thin products in workspace)
+__global__ void k_upd_d_prep(TlrView v, int k, const int2* __restrict__ items, GemmDesc* __restrict__ desc,
+                             double* __restrict__ ws, size_t ws_elems) {
+  const int2 it = items[blockIdx.x];
+  const int i = it.x, j = it.y, nb = v.nb;
+  const int64_t tij = dtile_index(i, j), tik = dtile_index(i, k), tjk = dtile_index(j, k);
+  const bool dik = v.dslot[tik] >= 0, djk = v.dslot[tjk] >= 0;
+  double* W = ws + (size_t)blockIdx.x * ws_elems;
+  double* T = W + (size_t)v.kcap * v.kcap;
+  GemmDesc d;
+  d.C = tileA(v, tij);
+  d.lower = 0;
+  if (dik && djk) {
+    d.P = tileA(v, tik); d.Q = tileA(v, tjk); d.r = nb;
+  } else if (dik) {
+    const int k2 = v.rank[tjk];
+    d.r = k2; d.Q = tileU(v, tjk); d.P = T;
+    if (k2 > 0) cta_gemm(nb, k2, nb, 1.0, tileA(v, tik), nb, 0, tileV(v, tjk), nb, 0, 0.0, T, nb);
+  } else if (djk) {
+    const int k1 = v.rank[tik];
+    d.r = k1; d.P = tileU(v, tik); d.Q = T;
+    if (k1 > 0) cta_gemm(nb, k1, nb, 1.0, tileA(v, tjk), nb, 0, tileV(v, tik), nb, 0, 0.0, T, nb);
+  } else {
+    const int k1 = v.rank[tik], k2 = v.rank[tjk];
+    if (k1 == 0 || k2 == 0) {
+      d.r = 0; d.P = nullptr; d.Q = nullptr;
+    } else {
+      cta_gemm(k1, k2, nb, 1.0, tileV(v, tik), nb, 1, tileV(v, tjk), nb, 0, 0.0, W, k1);
+      if (k2 <= k1) {
+        cta_gemm(nb, k2, k1, 1.0, tileU(v, tik), nb, 0, W, k1, 0, 0.0, T, nb);
+        d.P = T; d.Q = tileU(v, tjk); d.r = k2;
+      } else {
+        cta_gemm(nb, k1, k2, 1.0, tileU(v, tjk), nb, 0, W, k1, 1, 0.0, T, nb);
+        d.P = tileU(v, tik); d.Q = T; d.r = k1;
+      }
+    }
+  }
+  if (threadIdx.x == 0) desc[blockIdx.x] = d;
+}
+
+}  // namespace
+
+size_t tlr_item_elems(int nb, int kcap) {
+  const size_t Kmax = 2 * (size_t)kcap;
+  return 2 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 3 * Kmax;
+}
+
+static int chunk_for(const tlr_ctx* h, size_t per_item, size_t reserve = 0) {
+  size_t avail = h->scratch_elems > reserve ? h->scratch_elems - reserve : 0;
+  size_t c = per_item ? avail / per_item : 65535;
+  if (c > 65535) c = 65535;
+  return (int)c;
+}
+
+int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s) {
+  const int nb = h->nb, kcap = h->kcap, Kmax = 2 * kcap;
+  const size_t ie = tlr_item_elems(nb, kcap);
+  const int chunk = chunk_for(h, ie);
+  if (chunk < 1) return TLR_ERR_OOM;
+  const size_t smem = 2 * (size_t)nb * sizeof(double) + (size_t)nb * sizeof(int);
+  if (smem > 48 * 1024)
+    if (cudaFuncSetAttribute(k_aca_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return TLR_ERR_CUDA;
+  int aca_max = h->dense_rank + 8;
+  if (aca_max > Kmax) aca_max = Kmax;
+  const TlrView v = view_of(h);
+  for (int64_t t0 = 0; t0 < h->ntiles; t0 += chunk) {
+    const int cnt = (int)((h->ntiles - t0) < chunk ? (h->ntiles - t0) : chunk);
+    k_aca_compress<<<cnt, TLR_THREADS, smem, s>>>(h->tab, h->mp, h->x, h->y, h->n, v, t0, eps, aca_max, Kmax,
+                                                   h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t s) {
+  const TlrView v = view_of(h);
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = count - c0 < 65535 ? count - c0 : 65535;
+    dim3 grid(16, cnt);
+    k_gen_dense_list<<<grid, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, v, d_items + c0);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+static int launch_trsm(tlr_ctx* h, int k, cudaStream_t s) {
+  const TlrView v = view_of(h);
+  const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
+  const int nlr = (int)(off[PH_TRSM_LR + 1] - off[PH_TRSM_LR]);
+  if (nlr > 0) {
+    dim3 grid((h->kcap + 31) / 32, nlr);
+    k_trsm_lr<<<grid, 256, 0, s>>>(v, h->d_list + off[PH_TRSM_LR]);
+    TLR_LAUNCH_CHECK();
+  }
+  const int nd = (int)(off[PH_TRSM_D + 1] - off[PH_TRSM_D]);
+  if (nd > 0) {
+    const int2* it = h->d_list + off[PH_TRSM_D];
+    for (int c0 = 0; c0 < h->nb; c0 += 32) {
+      const int w = h->nb - c0 < 32 ? h->nb - c0 : 32;
+      k_trsm_d_panel<<<dim3((h->nb + 127) / 128, nd), 128, 0, s>>>(v, it, c0, w);
+      TLR_LAUNCH_CHECK();
+      const int c1 = c0 + w;
+      if (c1 < h->nb) {
+        const int mb = (h->nb + 63) / 64, nbk = (h->nb - c1 + 63) / 64;
+        k_trsm_d_trail<<<dim3(mb * nbk, nd), 256, 0, s>>>(v, it, c0, w);
+        TLR_LAUNCH_CHECK();
+      }
+    }
+  }
+  return TLR_OK;
+}
+
+static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {
+  const TlrView v = view_of(h);
+  const int items = h->nt - k - 1;
+  const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
+  const size_t desc_elems = (sizeof(GemmDesc) * (size_t)items + 7) / 8 + 1;
+  const int chunk = chunk_for(h, per, desc_elems);
+  if (chunk < 1) return TLR_ERR_OOM;
+  GemmDesc* desc = (GemmDesc*)h->scratch;
+  double* ws = h->scratch + desc_elems;
+  const int mb = (h->nb + 63) / 64;
+  for (int i0 = 0; i0 < items; i0 += chunk) {
+    const int cnt = items - i0 < chunk ? items - i0 : chunk;
+    k_syrk_prep<<<cnt, 256, 0, s>>>(v, k, k + 1 + i0, desc, ws, per);
+    TLR_LAUNCH_CHECK();
+    k_gemm_desc<<<dim3(mb * mb, cnt), 256, 0, s>>>(desc, h->nb);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+static int launch_updates(tlr_ctx* h, int k, cudaStream_t s) {
+  const TlrView v = view_of(h);
+  const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
+  // dense targets first (they read L_ik / L_jk only, like the low-rank ones)
+  const int64_t nd = off[PH_UPD_D + 1] - off[PH_UPD_D];
+  if (nd > 0) {
+    const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
+    const size_t desc_elems = (sizeof(GemmDesc) * (size_t)nd + 7) / 8 + 1;
+    const int chunk = chunk_for(h, per, desc_elems);
+    if (chunk < 1) return TLR_ERR_OOM;
+    GemmDesc* desc = (GemmDesc*)h->scratch;
+    double* ws = h->scratch + desc_elems;
+    const int mb = (h->nb + 63) / 64;
+    for (int64_t q0 = 0; q0 < nd; q0 += chunk) {
+      const int cnt = (int)(nd - q0 < chunk ? nd - q0 : chunk);
+      k_upd_d_prep<<<cnt, 256, 0, s>>>(v, k, h->d_list + off[PH_UPD_D] + q0, desc, ws, per);
+      TLR_LAUNCH_CHECK();
+      k_gemm_desc<<<dim3(mb * mb, cnt), 256, 0, s>>>(desc, h->nb);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  const int64_t nl = off[PH_UPD_LR + 1] - off[PH_UPD_LR];
+  if (nl > 0) {
+    const size_t ie = tlr_item_elems(h->nb, h->kcap);
+    const int chunk = chunk_for(h, ie);
+    if (chunk < 1) return TLR_ERR_OOM;
+    for (int64_t q0 = 0; q0 < nl; q0 += chunk) {
+      const int cnt = (int)(nl - q0 < chunk ? nl - q0 : chunk);
+      k_upd_lr<<<cnt, TLR_THREADS, 0, s>>>(v, k, h->d_list + off[PH_UPD_LR] + q0, h->opts.eps, 2 * h->kcap,
+                                           h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  return TLR_OK;
+}
+
+int tlr_factor(tlr_ctx* h, cudaStream_t s) {
+  const int nt = h->nt, nb = h->nb;
+  for (int k = 0; k < nt; ++k) {
+    int rc = tlr_potrf_tile(h, h->D + (size_t)k * nb * nb, nb, nb, (int64_t)k * nb, s);
+    if (rc) return rc;
+    if (k == nt - 1) break;
+    if ((rc = launch_trsm(h, k, s))) return rc;
+    if ((rc = launch_syrk(h, k, s))) return rc;
+    if ((rc = launch_updates(h, k, s))) return rc;
+  }
+  return TLR_OK;
+}

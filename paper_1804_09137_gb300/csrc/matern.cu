@@ -104,24 +104,6 @@ __global__ void k_gen_diag(const double* __restrict__ tab, const MaternParams mp
   }
 }
 
-// dense mode: every strictly-lower tile (i, j) as a dense nb x nb block in the U slot
-__global__ void k_gen_offdiag_dense(const double* __restrict__ tab, const MaternParams mp,
-                                    const double* __restrict__ x, const double* __restrict__ y, int64_t n,
-                                    int nb, int64_t t0, double* __restrict__ U) {
-  const int64_t t = t0 + blockIdx.y;
-  // decode t = i(i-1)/2 + j
-  int i = (int)((1.0 + sqrt(1.0 + 8.0 * (double)t)) * 0.5);
-  while ((int64_t)i * (i - 1) / 2 > t) --i;
-  while ((int64_t)(i + 1) * i / 2 <= t) ++i;
-  const int j = (int)(t - (int64_t)i * (i - 1) / 2);
-  const int64_t nn = (int64_t)nb * nb;
-  double* A = U + (size_t)t * nn;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < nn; id += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(id % nb), b = (int)(id / nb);
-    A[id] = cov_pts(tab, mp, x, y, n, (int64_t)i * nb + a, (int64_t)j * nb + b);
-  }
-}
-
 }  // namespace
 
 int tlr_build_table(tlr_ctx* h, cudaStream_t s) {
@@ -142,12 +124,3 @@ int tlr_gen_diag(tlr_ctx* h, cudaStream_t s) {
   return TLR_OK;
 }
 
-int tlr_gen_dense_offdiag(tlr_ctx* h, cudaStream_t s) {
-  for (int64_t t0 = 0; t0 < h->ntiles; t0 += 65535) {
-    int64_t cnt = h->ntiles - t0 < 65535 ? h->ntiles - t0 : 65535;
-    dim3 grid(32, (unsigned)cnt);
-    k_gen_offdiag_dense<<<grid, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, h->nb, t0, h->U);
-    TLR_LAUNCH_CHECK();
-  }
-  return TLR_OK;
-}

@@ -1,0 +1,218 @@
+// Low-rank recompression core shared by the factor and inverse kernels.
+//
+// cta_recompress(Up, Vp, K) replaces the rank-K product Up Vp^T (nb x K
+// factors) by its eps-truncated SVD: Householder QR of both factors, the small
+// core R_u R_v^T, one-sided (Hestenes) Jacobi SVD of the core with round-robin
+// pair ordering, keep the singular values > eps, apply both orthogonal factors
+// back.  One CTA of 256 threads per tile; workspace in global memory (L2).
+#pragma once
+#include "tile.cuh"
+
+namespace {
+
+struct ItemWs {  // per-item workspace layout (doubles)
+  double* Up;    // nb x Kmax
+  double* Vp;    // nb x Kmax
+  double* W;     // kcap x kcap
+  double* M;     // Kmax x Kmax
+  double* Y;     // Kmax x Kmax
+  double* tu;    // Kmax
+  double* tv;    // Kmax
+  double* s;     // Kmax
+};
+
+__device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int slot, int nb, int Kmax, int kcap) {
+  ItemWs w;
+  double* p = base + (size_t)slot * item_elems;
+  w.Up = p; p += (size_t)nb * Kmax;
+  w.Vp = p; p += (size_t)nb * Kmax;
+  w.W = p; p += (size_t)kcap * kcap;
+  w.M = p; p += (size_t)Kmax * Kmax;
+  w.Y = p; p += (size_t)Kmax * Kmax;
+  w.tu = p; p += Kmax;
+  w.tv = p; p += Kmax;
+  w.s = p;
+  return w;
+}
+
+// Householder QR in place (R on/above the diagonal, reflector v below it with v0 = 1)
+__device__ void cta_geqr2(double* __restrict__ A, int lda, int m, int K, double* __restrict__ tau, double* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nref = K < m ? K : m;
+  for (int c = 0; c < nref; ++c) {
+    double* a = A + (size_t)c * lda;
+    double p = 0.0;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) p = fma(a[r], a[r], p);
+    const double sig = block_sum(p, sh);
+    const double alpha = a[c];
+    double beta = alpha, tc = 0.0, scal = 1.0;
+    if (sig > 0.0) {
+      beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+      tc = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    if (sig > 0.0)
+      for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) a[r] *= scal;
+    __syncthreads();
+    if (threadIdx.x == 0) { a[c] = beta; tau[c] = tc; }
+    if (tc != 0.0) {
+      for (int j = c + 1 + warp; j < K; j += nw) {
+        double* b = A + (size_t)j * lda;
+        double d = (lane == 0) ? b[c] : 0.0;
+        for (int r = c + 1 + lane; r < m; r += 32) d = fma(a[r], b[r], d);
+        d = warp_sum(d) * tc;
+        if (lane == 0) b[c] -= d;
+        for (int r = c + 1 + lane; r < m; r += 32) b[r] = fma(-d, a[r], b[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B <- Q B for Q = H_0 ... H_{K-1} stored by cta_geqr2; B: m x ncol (ld ldb). Warp per column.
+__device__ void cta_apply_q(const double* __restrict__ A, int lda, int m, int K, const double* __restrict__ tau,
+                            double* __restrict__ B, int ldb, int ncol) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < ncol; j += nw) {
+    double* b = B + (size_t)j * ldb;
+    for (int c = K - 1; c >= 0; --c) {
+      const double tc = tau[c];
+      if (tc == 0.0) continue;
+      const double* v = A + (size_t)c * lda;
+      double d = (lane == 0) ? b[c] : 0.0;
+      for (int r = c + 1 + lane; r < m; r += 32) d = fma(v[r], b[r], d);
+      d = warp_sum(d) * tc;
+      if (lane == 0) b[c] -= d;
+      for (int r = c + 1 + lane; r < m; r += 32) b[r] = fma(-d, v[r], b[r]);
+    }
+  }
+}
+
+// round-robin pairing: round rr of K2-1, pair pi of K2/2
+__device__ __forceinline__ void rr_pair(int K2, int rr, int pi, int* p, int* q) {
+  const int L = K2 - 1;
+  auto el = [&](int pos) { return ((pos - rr) % L + L) % L + 1; };
+  if (pi == 0) { *p = 0; *q = el(0); }
+  else { *p = el(pi); *q = el(L - pi); }
+}
+
+// one-sided Jacobi: M (K x K, ld K) <- M Y with orthogonal columns, Y (K x K) accumulated
+__device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K, int* sh_flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) Y[e] = ((e % K) == (e / K)) ? 1.0 : 0.0;
+  __syncthreads();
+  if (K < 2) return;
+  const int K2 = K + (K & 1);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) *sh_flag = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int rr = 0; rr < K2 - 1; ++rr) {
+      for (int pi = warp; pi < K2 / 2; pi += nw) {
+        int p, q;
+        rr_pair(K2, rr, pi, &p, &q);
+        if (p >= K || q >= K) continue;
+        double* mp = M + (size_t)p * K;
+        double* mq = M + (size_t)q * K;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < K; r += 32) {
+          const double a = mp[r], b = mq[r];
+          al = fma(a, a, al);
+          be = fma(b, b, be);
+          ga = fma(a, b, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al > 0.0 && be > 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int r = lane; r < K; r += 32) {
+            const double a = mp[r], b = mq[r];
+            mp[r] = c * a - s * b;
+            mq[r] = s * a + c * b;
+          }
+          double* yp = Y + (size_t)p * K;
+          double* yq = Y + (size_t)q * K;
+          for (int r = lane; r < K; r += 32) {
+            const double a = yp[r], b = yq[r];
+            yp[r] = c * a - s * b;
+            yq[r] = s * a + c * b;
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated && lane == 0) atomicOr(sh_flag, 1);
+    __syncthreads();
+    if (*sh_flag == 0) break;
+    __syncthreads();
+  }
+}
+
+// Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
+// singular values > eps.  Returns k (same in all threads).
+__device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, double* Uo,
+                              double* Vo, long long* st, long long info, double* sh, int* shi) {
+  if (K == 0) return 0;
+  cta_geqr2(w.Up, nb, nb, K, w.tu, sh);
+  cta_geqr2(w.Vp, nb, nb, K, w.tv, sh);
+  const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
+  // M = R_u R_v^T (Ke x Ke)
+  for (int e = threadIdx.x; e < Ke * Ke; e += blockDim.x) {
+    const int a = e % Ke, b = e / Ke;
+    const int c0 = a > b ? a : b;
+    double s = 0.0;
+    for (int c = c0; c < K; ++c) s = fma(w.Up[(size_t)c * nb + a], w.Vp[(size_t)c * nb + b], s);
+    w.M[(size_t)b * Ke + a] = s;
+  }
+  __syncthreads();
+  cta_jacobi(w.M, w.Y, Ke, shi);
+  // singular values = column norms of M
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int l = warp; l < Ke; l += nw) {
+    double s = 0.0;
+    for (int r = lane; r < Ke; r += 32) s = fma(w.M[(size_t)l * Ke + r], w.M[(size_t)l * Ke + r], s);
+    s = warp_sum(s);
+    if (lane == 0) w.s[l] = sqrt(s);
+  }
+  __syncthreads();
+  // rank of each kept value in descending order; count kept
+  int cnt_local = 0;
+  for (int l = threadIdx.x; l < Ke; l += blockDim.x) cnt_local += (w.s[l] > eps);
+  const int kept = (int)block_sum((double)cnt_local, sh);
+  int k = kept;
+  if (k > kcap) {
+    if (!trunc_cap) set_status(st, TLR_ERR_RANK_CAP, info);
+    k = kcap;
+  }
+  // output columns: position of l among kept values sorted by (s desc, l asc)
+  for (int j = 0; j < k; ++j)
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) { Uo[(size_t)j * nb + r] = 0.0; Vo[(size_t)j * nb + r] = 0.0; }
+  __syncthreads();
+  for (int l = threadIdx.x; l < Ke; l += blockDim.x) {
+    const double sl = w.s[l];
+    if (!(sl > eps)) continue;
+    int pos = 0;
+    for (int l2 = 0; l2 < Ke; ++l2) {
+      const double s2 = w.s[l2];
+      pos += (s2 > sl) || (s2 == sl && l2 < l);
+    }
+    if (pos < k) {
+      for (int r = 0; r < Ke; ++r) {
+        Uo[(size_t)pos * nb + r] = w.M[(size_t)l * Ke + r];
+        Vo[(size_t)pos * nb + r] = w.Y[(size_t)l * Ke + r];
+      }
+    }
+  }
+  __syncthreads();
+  cta_apply_q(w.Up, nb, nb, Ke, w.tu, Uo, nb, k);
+  cta_apply_q(w.Vp, nb, nb, Ke, w.tv, Vo, nb, k);
+  __syncthreads();
+  return k;
+}
+
+}  // namespace
+

@@ -4,7 +4,7 @@
 // a fixed order) so results are bitwise reproducible run to run.
 #include <math.h>
 
-#include "common.cuh"
+#include "tile.cuh"
 
 namespace {
 
@@ -75,17 +75,26 @@ __global__ void k_trsv_lower_t(const double* __restrict__ L, int nb, double* __r
   }
 }
 
-// forward update of step k: r_i -= U_ik (V_ik^T r_k), i = k+1 .. nt-1 (one CTA per i)
-__global__ void k_lr_gemv_fwd(int nb, int k, const double* __restrict__ U, const double* __restrict__ V,
-                              size_t slot, const int* __restrict__ rank, double* __restrict__ r) {
+// forward update of step k: r_i -= L_ik r_k, i = k+1 .. nt-1 (one CTA per i)
+__global__ void k_gemv_fwd(TlrView v, int k, double* __restrict__ r) {
   extern __shared__ double tv[];
-  const int i = k + 1 + blockIdx.x;
+  const int i = k + 1 + blockIdx.x, nb = v.nb;
   const int64_t t = dtile_index(i, k);
-  const int kr = rank[t];
-  if (kr == 0) return;
-  const double* Ut = U + t * slot;
-  const double* Vt = V + t * slot;
   const double* rk = r + (size_t)k * nb;
+  double* ri = r + (size_t)i * nb;
+  if (v.dslot[t] >= 0) {
+    const double* A = tileA(v, t);
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      double acc = 0.0;
+      for (int b = 0; b < nb; ++b) acc = fma(A[(size_t)b * nb + a], rk[b], acc);
+      ri[a] -= acc;
+    }
+    return;
+  }
+  const int kr = v.rank[t];
+  if (kr <= 0) return;
+  const double* Ut = tileU(v, t);
+  const double* Vt = tileV(v, t);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l = warp; l < kr; l += nw) {
     double s = 0.0;
@@ -94,7 +103,6 @@ __global__ void k_lr_gemv_fwd(int nb, int k, const double* __restrict__ U, const
     if (lane == 0) tv[l] = s;
   }
   __syncthreads();
-  double* ri = r + (size_t)i * nb;
   for (int a = threadIdx.x; a < nb; a += blockDim.x) {
     double acc = 0.0;
     for (int l = 0; l < kr; ++l) acc = fma(Ut[(size_t)l * nb + a], tv[l], acc);
@@ -102,18 +110,28 @@ __global__ void k_lr_gemv_fwd(int nb, int k, const double* __restrict__ U, const
   }
 }
 
-// backward update of step k: r_j -= V_kj (U_kj^T r_k), j = 0 .. k-1 (one CTA per j)
-__global__ void k_lr_gemv_bwd(int nb, int k, const double* __restrict__ U, const double* __restrict__ V,
-                              size_t slot, const int* __restrict__ rank, double* __restrict__ r) {
+// backward update of step k: r_j -= L_kj^T r_k, j = 0 .. k-1 (one CTA per j)
+__global__ void k_gemv_bwd(TlrView v, int k, double* __restrict__ r) {
   extern __shared__ double tv[];
-  const int j = blockIdx.x;
+  const int j = blockIdx.x, nb = v.nb;
   const int64_t t = dtile_index(k, j);
-  const int kr = rank[t];
-  if (kr == 0) return;
-  const double* Ut = U + t * slot;
-  const double* Vt = V + t * slot;
   const double* rk = r + (size_t)k * nb;
+  double* rj = r + (size_t)j * nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (v.dslot[t] >= 0) {  // (A^T r_k)_a = sum_b A[b, a] r_k[b]: warp per a, lanes over b
+    const double* A = tileA(v, t);
+    for (int a = warp; a < nb; a += nw) {
+      double s = 0.0;
+      for (int b = lane; b < nb; b += 32) s = fma(A[(size_t)a * nb + b], rk[b], s);
+      s = warp_sum(s);
+      if (lane == 0) rj[a] -= s;
+    }
+    return;
+  }
+  const int kr = v.rank[t];
+  if (kr <= 0) return;
+  const double* Ut = tileU(v, t);
+  const double* Vt = tileV(v, t);
   for (int l = warp; l < kr; l += nw) {
     double s = 0.0;
     for (int q = lane; q < nb; q += 32) s = fma(Ut[(size_t)l * nb + q], rk[q], s);
@@ -121,7 +139,6 @@ __global__ void k_lr_gemv_bwd(int nb, int k, const double* __restrict__ U, const
     if (lane == 0) tv[l] = s;
   }
   __syncthreads();
-  double* rj = r + (size_t)j * nb;
   for (int a = threadIdx.x; a < nb; a += blockDim.x) {
     double acc = 0.0;
     for (int l = 0; l < kr; ++l) acc = fma(Vt[(size_t)l * nb + a], tv[l], acc);
@@ -129,27 +146,35 @@ __global__ void k_lr_gemv_bwd(int nb, int k, const double* __restrict__ U, const
   }
 }
 
-// z_i = L_ii e_i + sum_{j<i} U_ij (V_ij^T e_j)   (one CTA per tile row i)
-__global__ void k_lmul(int nb, const double* __restrict__ D, const double* __restrict__ U,
-                       const double* __restrict__ V, size_t slot, const int* __restrict__ rank,
-                       const double* __restrict__ e, double* __restrict__ z, int kcap) {
+// z_i = L_ii e_i + sum_{j<i} L_ij e_j   (one CTA per tile row i)
+__global__ void k_lmul(TlrView v, const double* __restrict__ e, double* __restrict__ z) {
   extern __shared__ double tv[];
-  const int i = blockIdx.x;
-  const double* Li = D + (size_t)i * nb * nb;
+  const int i = blockIdx.x, nb = v.nb;
+  const double* Li = diagT(v, i);
   const double* ei = e + (size_t)i * nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* zi = z + (size_t)i * nb;
   for (int a = threadIdx.x; a < nb; a += blockDim.x) {
     double acc = 0.0;
     for (int b = 0; b <= a; ++b) acc = fma(Li[(size_t)b * nb + a], ei[b], acc);
-    z[(size_t)i * nb + a] = acc;
+    zi[a] = acc;
   }
   for (int j = 0; j < i; ++j) {
     const int64_t t = dtile_index(i, j);
-    const int kr = rank[t];
-    if (kr == 0) continue;
-    const double* Ut = U + t * slot;
-    const double* Vt = V + t * slot;
     const double* ej = e + (size_t)j * nb;
+    if (v.dslot[t] >= 0) {
+      const double* A = tileA(v, t);
+      for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc = fma(A[(size_t)b * nb + a], ej[b], acc);
+        zi[a] += acc;
+      }
+      continue;
+    }
+    const int kr = v.rank[t];
+    if (kr <= 0) continue;
+    const double* Ut = tileU(v, t);
+    const double* Vt = tileV(v, t);
     __syncthreads();
     for (int l = warp; l < kr; l += nw) {
       double s = 0.0;
@@ -161,7 +186,7 @@ __global__ void k_lmul(int nb, const double* __restrict__ D, const double* __res
     for (int a = threadIdx.x; a < nb; a += blockDim.x) {
       double acc = 0.0;
       for (int l = 0; l < kr; ++l) acc = fma(Ut[(size_t)l * nb + a], tv[l], acc);
-      z[(size_t)i * nb + a] += acc;
+      zi[a] += acc;
     }
   }
 }
@@ -281,13 +306,12 @@ int tlr_permute_out(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) 
 
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
   const int nb = h->nb, nt = h->nt;
-  const size_t slot = (size_t)nb * h->kcap;
   const size_t sm = (size_t)h->kcap * sizeof(double);
   for (int k = 0; k < nt; ++k) {
     k_trsv_lower<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
     TLR_LAUNCH_CHECK();
     if (k < nt - 1) {
-      k_lr_gemv_fwd<<<nt - k - 1, 256, sm, s>>>(nb, k, h->U, h->V, slot, h->rank, r);
+      k_gemv_fwd<<<nt - k - 1, 256, sm, s>>>(view_of(h), k, r);
       TLR_LAUNCH_CHECK();
     }
   }
@@ -296,13 +320,12 @@ int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
 
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
   const int nb = h->nb, nt = h->nt;
-  const size_t slot = (size_t)nb * h->kcap;
   const size_t sm = (size_t)h->kcap * sizeof(double);
   for (int k = nt - 1; k >= 0; --k) {
     k_trsv_lower_t<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
     TLR_LAUNCH_CHECK();
     if (k > 0) {
-      k_lr_gemv_bwd<<<k, 256, sm, s>>>(nb, k, h->U, h->V, slot, h->rank, r);
+      k_gemv_bwd<<<k, 256, sm, s>>>(view_of(h), k, r);
       TLR_LAUNCH_CHECK();
     }
   }
@@ -311,7 +334,7 @@ int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
 
 int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s) {
   const size_t sm = (size_t)h->kcap * sizeof(double);
-  k_lmul<<<h->nt, 256, sm, s>>>(h->nb, h->D, h->U, h->V, (size_t)h->nb * h->kcap, h->rank, e, z, h->kcap);
+  k_lmul<<<h->nt, 256, sm, s>>>(view_of(h), e, z);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }

@@ -21,7 +21,7 @@ ERR_NAMES = {1: "not SPD", 2: "rank cap exceeded", 3: "out of memory", 4: "CUDA 
 
 class TlrOpts(C.Structure):
     _fields_ = [("nb", C.c_int), ("eps", C.c_double), ("rank_cap", C.c_int), ("truncate_at_cap", C.c_int),
-                ("order", C.c_int)]
+                ("order", C.c_int), ("dense_rank", C.c_int)]
 
 
 class TlrTheta(C.Structure):
@@ -40,7 +40,7 @@ _lib = None
 
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
-           "tlr_get_tile", "tlr_get_perm"]
+           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts"]
 
 
 def lib():
@@ -64,8 +64,9 @@ def lib():
     L.tlr_status.argtypes = [vp, C.POINTER(i64)]
     L.tlr_rank_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
     L.tlr_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
-    L.tlr_get_tile.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_int), vp]
+    L.tlr_get_tile.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     L.tlr_get_perm.argtypes = [vp, vp, vp]
+    L.tlr_tile_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -91,9 +92,10 @@ class Handle:
     """Owns one tlr_handle (tile storage on the current CUDA device)."""
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, nb: int, eps: float = 1e-9, rank_cap: int = 0,
-                 truncate_at_cap: bool = False, order: bool = True):
+                 truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0):
         L = lib()
-        self._opts = TlrOpts(int(nb), float(eps), int(rank_cap), int(bool(truncate_at_cap)), int(bool(order)))
+        self._opts = TlrOpts(int(nb), float(eps), int(rank_cap), int(bool(truncate_at_cap)), int(bool(order)),
+                             int(dense_rank))
         h = C.c_void_p()
         _check("tlr_create", L.tlr_create(int(x.numel()), _ptr(x), _ptr(y), C.byref(self._opts), _stream(),
                                           C.byref(h)))
@@ -165,17 +167,22 @@ class Handle:
         if rc != TLR_OK:
             raise TlrError("device", rc, info)
 
-    def get_tile(self, i, j, kcap=None):
-        """(U, V) of tile (i, j) in sorted point order; i == j: (dense tile, None)."""
-        kcap = self.nb if kcap is None else kcap
-        U = torch.zeros(self.nb * max(kcap, 1), dtype=torch.float64, device=self.dev)
+    def get_tile(self, i, j):
+        """Tile (i, j) in sorted point order: (A, None) if dense (or diagonal), else (U, V)."""
+        U = torch.zeros(self.nb * self.nb, dtype=torch.float64, device=self.dev)
         V = torch.zeros_like(U)
-        k = C.c_int()
-        _check("tlr_get_tile", lib().tlr_get_tile(self._h, int(i), int(j), _ptr(U), _ptr(V), C.byref(k), _stream()))
-        if i == j:
-            return U[: self.nb * self.nb].view(self.nb, self.nb).T, None
+        k, dense = C.c_int(), C.c_int()
+        _check("tlr_get_tile", lib().tlr_get_tile(self._h, int(i), int(j), _ptr(U), _ptr(V), C.byref(k),
+                                                  C.byref(dense), _stream()))
+        if dense.value:
+            return U.view(self.nb, self.nb).T, None
         kk = k.value
         return U[: self.nb * kk].view(kk, self.nb).T, V[: self.nb * kk].view(kk, self.nb).T
+
+    def tile_counts(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check("tlr_tile_counts", lib().tlr_tile_counts(self._h, C.byref(a), C.byref(b)))
+        return {"lowrank": a.value, "dense": b.value}
 
     def get_perm(self):
         p = torch.zeros(self.n, dtype=torch.int32, device=self.dev)

@@ -67,10 +67,13 @@ def test_compression_error_bound(T, theta, eps):
     for i in range(h.nt):
         for j in range(i):
             U, V = h.get_tile(i, j)
-            U, V = U.cpu().numpy(), V.cpu().numpy()
             A = np.zeros((nb, nb))
             ri, rj = min(nb, n - i * nb), min(nb, n - j * nb)
             A[:ri, :rj] = S[i * nb:i * nb + ri, j * nb:j * nb + rj]
+            if V is None:  # stored dense: exact generation
+                assert np.max(np.abs(U.cpu().numpy() - A)) <= 1e-13
+                continue
+            U, V = U.cpu().numpy(), V.cpu().numpy()
             err = np.linalg.norm(A - U @ V.T, 2)
             assert err <= 2.0 * eps, (i, j, err)
             s = np.linalg.svd(A, compute_uv=False)
@@ -89,6 +92,34 @@ def test_loglik_small_eps_matches_dense(T, theta):
     assert abs(out[0] - ll) <= 1e-9 * abs(ll)
     assert abs(out[1] - ld) <= 1e-9 * abs(ld)
     assert abs(out[2] - q) <= 1e-8 * abs(q)
+
+
+@pytest.mark.parametrize("dense_rank", [4, 16, 120])
+def test_dense_threshold_does_not_change_result(T, dense_rank):
+    theta = (1.0, 0.3, 1.0)
+    x, y, z = problem(30, theta, n=850)
+    ll = DN.loglik(x, y, z, theta)[0]
+    h = T.Handle(dev(x), dev(y), nb=128, eps=1e-11, rank_cap=128, dense_rank=dense_rank)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    h.check()
+    cnt = h.tile_counts()
+    assert cnt["dense"] + cnt["lowrank"] == h.nt * (h.nt - 1) // 2
+    assert abs(out[0] - ll) <= 1e-8 * abs(ll), (out[0], ll, cnt)
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.3, 1.0)])
+def test_dense_mode_matches_oracle(T, theta):
+    # eps < 0: every tile dense, the exact full-tile comparator
+    x, y, z = problem(30, theta, n=870)
+    ll, ld, q = DN.loglik(x, y, z, theta)
+    h = T.Handle(dev(x), dev(y), nb=96, eps=-1.0)
+    h.factor(theta)
+    out = h.loglik(dev(z)).cpu().numpy()
+    h.check()
+    assert h.tile_counts()["lowrank"] == 0
+    assert abs(out[0] - ll) <= 1e-10 * abs(ll)
+    assert abs(out[1] - ld) <= 1e-10 * abs(ld)
 
 
 def test_single_tile_is_dense(T):
@@ -163,8 +194,9 @@ def test_not_spd_reported(T):
 
 
 def test_rank_cap_reported(T):
+    # low-rank tiles allowed up to rank 24 but storage capped at 16: the overflow is reported
     x, y = inputs.jittered_grid(16)
-    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-12, rank_cap=2)
+    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-12, rank_cap=16, dense_rank=24)
     h.matern_generate((1.0, 0.3, 1.0))
     h.compress()
     rc, _ = h.status()
