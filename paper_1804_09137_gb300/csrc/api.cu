@@ -79,13 +79,17 @@ int dmalloc(T** p, size_t count) {
 }
 
 void free_ctx(tlr_ctx* h) {
-  void* bufs[] = {h->x,   h->y,      h->perm,   h->D,     h->U,     h->V,      h->rank,
-                  h->tab, h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list};
+  void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
+                  h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist};
   for (void* b : bufs)
     if (b) cudaFree(b);
   free(h->kind);
   free(h->h_list);
   free(h->plan_off);
+  free(h->kindz);
+  free(h->h_zlist);
+  free(h->zoff);
   delete h;
 }
 
@@ -161,6 +165,10 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
   ws = std::max(ws, (size_t)std::min<int64_t>(max_items, 912) * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
   ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->nt * (h->nt + 1) / 2 + 16));
+  // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
+  const size_t mb = (nb + 63) / 64;
+  ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->nt * (h->nt + 1) / 2 + 1024));
+  ws = std::max(ws, 2 * nb * nb + 4096);
   h->scratch_elems = ws;
   rc |= dmalloc(&h->scratch, ws);
   if (rc != TLR_OK) {
@@ -440,6 +448,7 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
     h->dcap = want;
   }
   h->ndense = nd;
+  h->zplan_valid = 0;
   // lists: per step 4 phases, then the dense-generation list
   std::vector<int2> L;
   std::vector<int64_t> off((size_t)nt * PLAN_PH + 1, 0);
@@ -493,12 +502,31 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
   return TLR_OK;
 }
 
-int tlr_grad_trace(tlr_ctx*, double*, cudaStream_t) { return TLR_ERR_STATE; }
+namespace {
+__global__ void k_grad_finish(const double* __restrict__ ll3, double* __restrict__ d_ll) {
+  if (threadIdx.x == 0) d_ll[0] = ll3[0];
+}
+}  // namespace
 
 extern "C" int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, double* d_grad3, tlr_stream_t stream) {
   if (!h) return -1;
   if (!z) return -2;
   if (!d_ll) return -3;
   if (!d_grad3) return -4;
-  return TLR_ERR_STATE;  // trace term pending
+  if (h->state != 3) return TLR_ERR_STATE;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  double* w = h->d_vec;              // L^{-1} z
+  double* a = h->d_vec + h->npad;    // Sigma^{-1} z
+  double* ll3 = h->d_red + 2 * h->nt;  // (l, log|Sigma|, quad)
+  TRY(tlr_permute_in(h, z, w, s));
+  TRY(tlr_fwd_solve(h, w, s));
+  TRY(tlr_reduce_loglik(h, w, ll3, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(a, w, h->npad * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TRY(tlr_bwd_solve(h, a, s));
+  TRY(tlr_inverse(h, s));
+  TRY(tlr_grad_fused(h, a, d_grad3, s));
+  k_grad_finish<<<1, 32, 0, s>>>(ll3, d_ll);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
 }

@@ -30,6 +30,18 @@
 #define PH_UPD_LR 2
 #define PH_UPD_D 3
 #define PLAN_PH 4
+// inverse plan phases of one step: TRTRI (1: column k, 2: updates, 3: row k), LAUUM (2: updates, 3: row k)
+#define ZP_T1_LR 0
+#define ZP_T1_D 1
+#define ZP_T2_LR 2
+#define ZP_T2_D 3
+#define ZP_T3_LR 4
+#define ZP_T3_D 5
+#define ZP_L2_LR 6
+#define ZP_L2_D 7
+#define ZP_L3_LR 8
+#define ZP_L3_D 9
+#define ZPH 10
 
 #define ST_CODE 0
 #define ST_INFO 1
@@ -65,6 +77,21 @@ struct tlr_ctx {
   int2* h_list;    // host copy
   int64_t list_cap;
   int64_t* plan_off;  // [nt * PLAN_PH + 1] offsets into the lists
+  // inverse Z = Sigma^{-1} (TLR, same tile layout), allocated by the first gradient call
+  double* Dz;
+  double* Uz;
+  double* Vz;
+  int* rankz;
+  int* dslotz;
+  double* dpoolz;
+  int dcapz;
+  int ndensez;
+  char* kindz;
+  int2* d_zlist;
+  int2* h_zlist;
+  int64_t zlist_cap;
+  int64_t* zoff;      // [nt * ZPH + 1]
+  int zplan_valid;
   double* tab;     // Matérn table (TAB_ELEMS)
   MaternParams mp;
   double* scratch; // batched-kernel workspace
@@ -217,7 +244,8 @@ int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s);
 int tlr_reduce_loglik(tlr_ctx* h, const double* w, double* out3, cudaStream_t s);
 int tlr_grad_quad(tlr_ctx* h, const double* a, double* out2, cudaStream_t s);
-int tlr_grad_trace(tlr_ctx* h, double* out2, cudaStream_t s);
+int tlr_inverse(tlr_ctx* h, cudaStream_t s);
+int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s);
 int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,
               cudaStream_t s);
 int tlr_permute_in(tlr_ctx* h, const double* src, double* dst, cudaStream_t s);

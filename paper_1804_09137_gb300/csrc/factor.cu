@@ -17,6 +17,7 @@
 //   GEMM   A_ij -= L_ik L_jk^T, i > j > k: low-rank targets recompressed to eps
 //          (one CTA per tile), dense targets by batched GEMM.
 #include "recompress.cuh"
+#include "tileops.h"
 
 namespace {
 
@@ -264,102 +265,6 @@ __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
   cta_gemm_blocks(nb, nb, d.r, -1.0, d.P, nb, 0, d.Q, nb, 1, 1.0, d.C, nb, blockIdx.x, gridDim.x, d.lower);
 }
 
-// ---------------------------------------------------------------- updates
-// low-rank target A_ij -= L_ik L_jk^T with recompression; items (i, j), step k
-__global__ void k_upd_lr(TlrView v, int k, const int2* __restrict__ items, double eps, int Kmax, int trunc_cap,
-                         double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
-  __shared__ double sh[TLR_THREADS / 32 + 2];
-  __shared__ int shi[TLR_THREADS / 32 + 2];
-  const int2 it = items[blockIdx.x];
-  const int i = it.x, j = it.y, nb = v.nb;
-  const int64_t tij = dtile_index(i, j), tik = dtile_index(i, k), tjk = dtile_index(j, k);
-  const bool dik = v.dslot[tik] >= 0, djk = v.dslot[tjk] >= 0;
-  const int k0 = v.rank[tij];
-  const int k1 = dik ? nb : v.rank[tik];
-  const int k2 = djk ? nb : v.rank[tjk];
-  if (k1 == 0 || k2 == 0) return;
-  if (dik && djk) {  // excluded by the fill closure
-    if (threadIdx.x == 0) set_status(st, TLR_ERR_STATE, tij);
-    return;
-  }
-  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
-  double* Uij = tileU(v, tij);
-  double* Vij = tileV(v, tij);
-  for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) { w.Up[e] = Uij[e]; w.Vp[e] = Vij[e]; }
-  int K;
-  double* Un = w.Up + (size_t)k0 * nb;  // new columns
-  double* Vn = w.Vp + (size_t)k0 * nb;
-  if (!dik && !djk) {
-    const double* Uik = tileU(v, tik);
-    const double* Vik = tileV(v, tik);
-    const double* Ujk = tileU(v, tjk);
-    const double* Vjk = tileV(v, tjk);
-    cta_gemm(k1, k2, nb, 1.0, Vik, nb, 1, Vjk, nb, 0, 0.0, w.W, k1);  // W = V_ik^T V_jk
-    if (k2 <= k1) {  // [-U_ik W] [U_jk]^T
-      cta_gemm(nb, k2, k1, -1.0, Uik, nb, 0, w.W, k1, 0, 0.0, Un, nb);
-      for (size_t e = threadIdx.x; e < (size_t)nb * k2; e += blockDim.x) Vn[e] = Ujk[e];
-      K = k0 + k2;
-    } else {  // [-U_ik] [U_jk W^T]^T
-      cta_gemm(nb, k1, k2, 1.0, Ujk, nb, 0, w.W, k1, 1, 0.0, Vn, nb);
-      for (size_t e = threadIdx.x; e < (size_t)nb * k1; e += blockDim.x) Un[e] = -Uik[e];
-      K = k0 + k1;
-    }
-  } else if (dik) {  // dense L_ik: [-(A_ik V_jk)] [U_jk]^T
-    cta_gemm(nb, k2, nb, -1.0, tileA(v, tik), nb, 0, tileV(v, tjk), nb, 0, 0.0, Un, nb);
-    const double* Ujk = tileU(v, tjk);
-    for (size_t e = threadIdx.x; e < (size_t)nb * k2; e += blockDim.x) Vn[e] = Ujk[e];
-    K = k0 + k2;
-  } else {  // dense L_jk: [-U_ik] [A_jk V_ik]^T
-    cta_gemm(nb, k1, nb, 1.0, tileA(v, tjk), nb, 0, tileV(v, tik), nb, 0, 0.0, Vn, nb);
-    const double* Uik = tileU(v, tik);
-    for (size_t e = threadIdx.x; e < (size_t)nb * k1; e += blockDim.x) Un[e] = -Uik[e];
-    K = k0 + k1;
-  }
-  __syncthreads();
-  const int kr = cta_recompress(w, nb, K, eps, v.kcap, trunc_cap, Uij, Vij, st, tij, sh, shi);
-  if (threadIdx.x == 0) v.rank[tij] = kr;
-}
-
-// dense target A_ij -= L_ik L_jk^T: descriptor P Q^T (thin products in workspace)
-__global__ void k_upd_d_prep(TlrView v, int k, const int2* __restrict__ items, GemmDesc* __restrict__ desc,
-                             double* __restrict__ ws, size_t ws_elems) {
-  const int2 it = items[blockIdx.x];
-  const int i = it.x, j = it.y, nb = v.nb;
-  const int64_t tij = dtile_index(i, j), tik = dtile_index(i, k), tjk = dtile_index(j, k);
-  const bool dik = v.dslot[tik] >= 0, djk = v.dslot[tjk] >= 0;
-  double* W = ws + (size_t)blockIdx.x * ws_elems;
-  double* T = W + (size_t)v.kcap * v.kcap;
-  GemmDesc d;
-  d.C = tileA(v, tij);
-  d.lower = 0;
-  if (dik && djk) {
-    d.P = tileA(v, tik); d.Q = tileA(v, tjk); d.r = nb;
-  } else if (dik) {
-    const int k2 = v.rank[tjk];
-    d.r = k2; d.Q = tileU(v, tjk); d.P = T;
-    if (k2 > 0) cta_gemm(nb, k2, nb, 1.0, tileA(v, tik), nb, 0, tileV(v, tjk), nb, 0, 0.0, T, nb);
-  } else if (djk) {
-    const int k1 = v.rank[tik];
-    d.r = k1; d.P = tileU(v, tik); d.Q = T;
-    if (k1 > 0) cta_gemm(nb, k1, nb, 1.0, tileA(v, tjk), nb, 0, tileV(v, tik), nb, 0, 0.0, T, nb);
-  } else {
-    const int k1 = v.rank[tik], k2 = v.rank[tjk];
-    if (k1 == 0 || k2 == 0) {
-      d.r = 0; d.P = nullptr; d.Q = nullptr;
-    } else {
-      cta_gemm(k1, k2, nb, 1.0, tileV(v, tik), nb, 1, tileV(v, tjk), nb, 0, 0.0, W, k1);
-      if (k2 <= k1) {
-        cta_gemm(nb, k2, k1, 1.0, tileU(v, tik), nb, 0, W, k1, 0, 0.0, T, nb);
-        d.P = T; d.Q = tileU(v, tjk); d.r = k2;
-      } else {
-        cta_gemm(nb, k1, k2, 1.0, tileU(v, tjk), nb, 0, W, k1, 1, 0.0, T, nb);
-        d.P = tileU(v, tik); d.Q = T; d.r = k1;
-      }
-    }
-  }
-  if (threadIdx.x == 0) desc[blockIdx.x] = d;
-}
-
 }  // namespace
 
 size_t tlr_item_elems(int nb, int kcap) {
@@ -454,39 +359,9 @@ static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {
 }
 
 static int launch_updates(tlr_ctx* h, int k, cudaStream_t s) {
-  const TlrView v = view_of(h);
   const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
-  // dense targets first (they read L_ik / L_jk only, like the low-rank ones)
-  const int64_t nd = off[PH_UPD_D + 1] - off[PH_UPD_D];
-  if (nd > 0) {
-    const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
-    const size_t desc_elems = (sizeof(GemmDesc) * (size_t)nd + 7) / 8 + 1;
-    const int chunk = chunk_for(h, per, desc_elems);
-    if (chunk < 1) return TLR_ERR_OOM;
-    GemmDesc* desc = (GemmDesc*)h->scratch;
-    double* ws = h->scratch + desc_elems;
-    const int mb = (h->nb + 63) / 64;
-    for (int64_t q0 = 0; q0 < nd; q0 += chunk) {
-      const int cnt = (int)(nd - q0 < chunk ? nd - q0 : chunk);
-      k_upd_d_prep<<<cnt, 256, 0, s>>>(v, k, h->d_list + off[PH_UPD_D] + q0, desc, ws, per);
-      TLR_LAUNCH_CHECK();
-      k_gemm_desc<<<dim3(mb * mb, cnt), 256, 0, s>>>(desc, h->nb);
-      TLR_LAUNCH_CHECK();
-    }
-  }
-  const int64_t nl = off[PH_UPD_LR + 1] - off[PH_UPD_LR];
-  if (nl > 0) {
-    const size_t ie = tlr_item_elems(h->nb, h->kcap);
-    const int chunk = chunk_for(h, ie);
-    if (chunk < 1) return TLR_ERR_OOM;
-    for (int64_t q0 = 0; q0 < nl; q0 += chunk) {
-      const int cnt = (int)(nl - q0 < chunk ? nl - q0 : chunk);
-      k_upd_lr<<<cnt, TLR_THREADS, 0, s>>>(v, k, h->d_list + off[PH_UPD_LR] + q0, h->opts.eps, 2 * h->kcap,
-                                           h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
-      TLR_LAUNCH_CHECK();
-    }
-  }
-  return TLR_OK;
+  return tops_update(h, view_of(h), ALG_CHOL, k, h->d_list + off[PH_UPD_LR], off[PH_UPD_LR + 1] - off[PH_UPD_LR],
+                     h->d_list + off[PH_UPD_D], off[PH_UPD_D + 1] - off[PH_UPD_D], h->opts.eps, nullptr, 0.0, s);
 }
 
 int tlr_factor(tlr_ctx* h, cudaStream_t s) {

@@ -1,0 +1,275 @@
+// Tile low-rank inverse Z = Sigma^{-1} = L^{-T} L^{-1} of the factored matrix
+// (needed by the trace term of the likelihood gradient; not in the paper).
+//
+// Right-looking tile TRTRI (M = L^{-1}, in place on a copy of the factor), step k:
+//   1. A_ik <- -A_ik L_kk^{-1}                 i > k  (low rank: V <- -L_kk^{-T} V)
+//   2. A_ij <- A_ij + A_ik A_kj                i > k > j
+//   3. A_kj <- L_kk^{-1} A_kj                  j < k  (low rank: U <- L_kk^{-1} U)
+//   4. A_kk <- L_kk^{-1}
+// then right-looking tile LAUUM (Z = M^T M, lower part), step k:
+//   1. A_nn <- A_nn + A_kn^T A_kn              n < k
+//   2. A_mn <- A_mn + A_km^T A_kn              n < m < k
+//   3. A_kn <- A_kk^T A_kn                     n < k  (low rank: U <- M_kk^T U)
+//   4. A_kk <- A_kk^T A_kk
+// Low-rank targets are recompressed at tau_M = eps sqrt(zeta) (TRTRI) and
+// tau_Z = eps zeta (LAUUM), zeta = max_a 1 / L_aa^2 ~ the scale of Z's
+// diagonal, so that the truncation is relative to the size of M and Z as eps
+// is to Sigma.  The dense set is closed under both algorithms' fill.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tileops.h"
+
+namespace {
+
+__global__ void k_zeta(const double* __restrict__ D, int nb, int nt, double* __restrict__ out) {
+  __shared__ double sh[TLR_THREADS];
+  double m = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)nt * nb; e += blockDim.x) {
+    const int k = (int)(e / nb), a = (int)(e % nb);
+    const double d = D[(size_t)k * nb * nb + (size_t)a * nb + a];
+    m = fmax(m, 1.0 / (d * d));
+  }
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// copy the factor's tiles into the inverse storage (low rank -> dense where Z is dense)
+__global__ void k_copy_to_z(TlrView f, TlrView z, int64_t ntiles) {
+  const int64_t t = blockIdx.y;
+  const int nb = f.nb;
+  const bool fd = f.dslot[t] >= 0, zd = z.dslot[t] >= 0;
+  if (zd) {
+    double* Az = tileA(z, t);
+    if (fd) {
+      const double* Af = tileA(f, t);
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
+           e += (int64_t)gridDim.x * blockDim.x)
+        Az[e] = Af[e];
+    } else {
+      const int kr = f.rank[t];
+      const double* U = tileU(f, t);
+      const double* V = tileV(f, t);
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
+           e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e % nb), b = (int)(e / nb);
+        double s = 0.0;
+        for (int l = 0; l < kr; ++l) s = fma(U[(size_t)l * nb + a], V[(size_t)l * nb + b], s);
+        Az[e] = s;
+      }
+    }
+  } else {
+    const int kr = f.rank[t];
+    const size_t cnt = (size_t)nb * kr;
+    const double* Uf = tileU(f, t);
+    const double* Vf = tileV(f, t);
+    double* Uz = tileU(z, t);
+    double* Vz = tileV(z, t);
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (size_t)gridDim.x * blockDim.x) {
+      Uz[e] = Uf[e];
+      Vz[e] = Vf[e];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) z.rank[t] = kr;
+  }
+}
+
+__global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = a[e];
+}
+
+__global__ void k_eye(double* __restrict__ X, int nb) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
+       e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = ((e % nb) == (e / nb)) ? 1.0 : 0.0;
+}
+
+}  // namespace
+
+static TlrView zview(const tlr_ctx* h) {
+  TlrView v;
+  v.nb = h->nb; v.nt = h->nt; v.kcap = h->kcap;
+  v.D = h->Dz; v.U = h->Uz; v.V = h->Vz; v.rank = h->rankz; v.dslot = h->dslotz; v.dpool = h->dpoolz;
+  return v;
+}
+
+static int zplan(tlr_ctx* h, cudaStream_t s) {
+  const int nt = h->nt;
+  const int64_t T = h->ntiles;
+  free(h->kindz);
+  h->kindz = (char*)calloc(std::max<int64_t>(T, 1), 1);
+  if (!h->kindz) return TLR_ERR_OOM;
+  char* K = h->kindz;
+  for (int64_t t = 0; t < T; ++t) K[t] = h->kind ? h->kind[t] : 0;
+  auto kd = [&](int p, int q) -> char& { return K[tile_index(p, q)]; };
+  for (int k = 0; k < nt; ++k)  // TRTRI fill: A_ij += A_ik A_kj
+    for (int i = k + 1; i < nt; ++i)
+      if (kd(i, k))
+        for (int j = 0; j < k; ++j)
+          if (kd(k, j)) kd(i, j) = 1;
+  for (int k = 0; k < nt; ++k)  // LAUUM fill: A_mn += A_km^T A_kn
+    for (int m = 0; m < k; ++m)
+      if (kd(k, m))
+        for (int n2 = 0; n2 < m; ++n2)
+          if (kd(k, n2)) kd(m, n2) = 1;
+  std::vector<int> slot(std::max<int64_t>(T, 1), -1);
+  int nd = 0;
+  for (int64_t t = 0; t < T; ++t)
+    if (K[t]) slot[t] = nd++;
+  if (nd > h->dcapz) {
+    if (h->dpoolz) cudaFree(h->dpoolz);
+    h->dpoolz = nullptr;
+    h->dcapz = 0;
+    const int want = nd + nd / 8 + 1;
+    if (cudaMalloc((void**)&h->dpoolz, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return TLR_ERR_OOM;
+    }
+    h->dcapz = want;
+  }
+  h->ndensez = nd;
+  std::vector<int2> L;
+  std::vector<int64_t> off((size_t)nt * ZPH + 1, 0);
+  for (int k = 0; k < nt; ++k) {
+    for (int ph = 0; ph < ZPH; ++ph) {
+      off[(size_t)k * ZPH + ph] = (int64_t)L.size();
+      const char want = ph & 1;  // odd phases: dense tiles
+      switch (ph) {
+        case ZP_T1_LR: case ZP_T1_D:
+          for (int i = k + 1; i < nt; ++i) if (kd(i, k) == want) L.push_back(make_int2(i, k));
+          break;
+        case ZP_T2_LR: case ZP_T2_D:
+          for (int i = k + 1; i < nt; ++i)
+            for (int j = 0; j < k; ++j) if (kd(i, j) == want) L.push_back(make_int2(i, j));
+          break;
+        case ZP_T3_LR: case ZP_T3_D: case ZP_L3_LR: case ZP_L3_D:
+          for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
+          break;
+        case ZP_L2_LR: case ZP_L2_D:
+          for (int m = 1; m < k; ++m)
+            for (int n2 = 0; n2 < m; ++n2) if (kd(m, n2) == want) L.push_back(make_int2(m, n2));
+          break;
+      }
+    }
+  }
+  off[(size_t)nt * ZPH] = (int64_t)L.size();
+  const int64_t len = std::max<int64_t>((int64_t)L.size(), 1);
+  if (len > h->zlist_cap) {
+    if (h->d_zlist) cudaFree(h->d_zlist);
+    h->d_zlist = nullptr;
+    if (cudaMalloc((void**)&h->d_zlist, len * sizeof(int2)) != cudaSuccess) {
+      cudaGetLastError();
+      h->zlist_cap = 0;
+      return TLR_ERR_OOM;
+    }
+    h->zlist_cap = len;
+  }
+  free(h->h_zlist);
+  free(h->zoff);
+  h->h_zlist = (int2*)malloc(len * sizeof(int2));
+  h->zoff = (int64_t*)malloc(off.size() * sizeof(int64_t));
+  if (!h->h_zlist || !h->zoff) return TLR_ERR_OOM;
+  if (!L.empty()) memcpy(h->h_zlist, L.data(), L.size() * sizeof(int2));
+  memcpy(h->zoff, off.data(), off.size() * sizeof(int64_t));
+  if (!L.empty())
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->d_zlist, h->h_zlist, L.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (T > 0) TLR_CUDA_TRY(cudaMemcpyAsync(h->dslotz, slot.data(), T * sizeof(int), cudaMemcpyHostToDevice, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  h->zplan_valid = 1;
+  return TLR_OK;
+}
+
+static int ensure_z(tlr_ctx* h) {
+  if (h->Dz) return TLR_OK;
+  const size_t nb = h->nb, slot = nb * h->kcap;
+  const size_t T = std::max<int64_t>(h->ntiles, 1);
+  bool ok = cudaMalloc((void**)&h->Dz, (size_t)h->nt * nb * nb * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->Uz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->Vz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->rankz, T * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->dslotz, T * sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return TLR_ERR_OOM;
+  }
+  return TLR_OK;
+}
+
+#define ZTRY(x)                    \
+  do {                             \
+    int rc_ = (x);                 \
+    if (rc_ != TLR_OK) return rc_; \
+  } while (0)
+
+int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
+  ZTRY(ensure_z(h));
+  if (!h->zplan_valid) ZTRY(zplan(h, s));
+  const int nt = h->nt, nb = h->nb;
+  const TlrView f = view_of(h);
+  const TlrView z = zview(h);
+  const size_t nn = (size_t)nb * nb;
+  // zeta lives in the last reduction slot
+  double* d_zeta = h->d_red + h->red_len - 1;
+  k_zeta<<<1, TLR_THREADS, 0, s>>>(h->D, nb, nt, d_zeta);
+  TLR_LAUNCH_CHECK();
+  k_copy<<<1024, 256, 0, s>>>(h->D, h->Dz, (int64_t)nt * nn);
+  TLR_LAUNCH_CHECK();
+  TLR_CUDA_TRY(cudaMemsetAsync(h->rankz, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s));
+  if (h->ntiles > 0) {
+    for (int64_t t0 = 0; t0 < h->ntiles; t0 += 65535) {
+      // one grid row per tile (gridDim.y), offset via pointer arithmetic is not possible: launch per chunk
+      const int64_t cnt = std::min<int64_t>(65535, h->ntiles - t0);
+      TlrView fo = f, zo = z;
+      fo.rank = f.rank + t0; fo.dslot = f.dslot + t0;
+      zo.rank = z.rank + t0; zo.dslot = z.dslot + t0;
+      fo.U = f.U ? f.U + (size_t)t0 * nb * h->kcap : f.U; fo.V = f.V ? f.V + (size_t)t0 * nb * h->kcap : f.V;
+      zo.U = z.U ? z.U + (size_t)t0 * nb * h->kcap : z.U; zo.V = z.V ? z.V + (size_t)t0 * nb * h->kcap : z.V;
+      if (h->dense) { fo.U = f.U; fo.V = f.V; zo.U = z.U; zo.V = z.V; }
+      k_copy_to_z<<<dim3(8, (unsigned)cnt), 256, 0, s>>>(fo, zo, cnt);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  const double eps = h->opts.eps > 0 ? h->opts.eps : 0.0;
+  double* X = h->scratch;  // nb x nb workspace for the diagonal tiles
+  // ---- TRTRI
+  for (int k = 0; k < nt; ++k) {
+    const int64_t* off = h->zoff + (size_t)k * ZPH;
+    auto L = [&](int ph) { return h->d_zlist + off[ph]; };
+    auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
+    ZTRY(tops_trop(h, z, k, L(ZP_T1_LR), N(ZP_T1_LR), 1, L(ZP_T1_D), N(ZP_T1_D), 1, TOP_SOLVE_T, -1.0, s));
+    ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s));
+    ZTRY(tops_trop(h, z, k, L(ZP_T3_LR), N(ZP_T3_LR), 0, L(ZP_T3_D), N(ZP_T3_D), 0, TOP_SOLVE, 1.0, s));
+    k_eye<<<256, 256, 0, s>>>(X, nb);
+    TLR_LAUNCH_CHECK();
+    ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, X, nb, TOP_SOLVE, 1.0, s));
+    k_copy<<<256, 256, 0, s>>>(X, h->Dz + (size_t)k * nn, (int64_t)nn);
+    TLR_LAUNCH_CHECK();
+  }
+  // ---- LAUUM
+  GemmGen* desc = (GemmGen*)(h->scratch + nn);
+  for (int k = 0; k < nt; ++k) {
+    const int64_t* off = h->zoff + (size_t)k * ZPH;
+    auto L = [&](int ph) { return h->d_zlist + off[ph]; };
+    auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
+    ZTRY(tops_herk_row(h, z, k, s));
+    ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s));
+    ZTRY(tops_trop(h, z, k, L(ZP_L3_LR), N(ZP_L3_LR), 0, L(ZP_L3_D), N(ZP_L3_D), 0, TOP_MUL_T, 1.0, s));
+    // D_k <- D_k^T D_k via the workspace
+    GemmGen g;
+    g.A = h->Dz + (size_t)k * nn; g.B = g.A; g.C = X; g.m = nb; g.n = nb; g.k = nb;
+    g.lda = nb; g.ldb = nb; g.ldc = nb; g.tA = 1; g.tB = 0; g.alpha = 1.0; g.beta = 0.0; g.lower = 0;
+    TLR_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, s));
+    ZTRY(tops_gemm(desc, 1, nb, nb, s));
+    k_copy<<<256, 256, 0, s>>>(X, h->Dz + (size_t)k * nn, (int64_t)nn);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}

@@ -1,0 +1,403 @@
+// Generic batched tile operations (see tileops.h).
+//
+// Update of a target tile by a product of two tiles, alpha op(X) op(Y):
+//   low-rank X, Y:  U_x (V_x^T U_y) V_y^T, kept as the thinner of the two groupings;
+//   dense X:        (op(X) U_y) V_y^T;   dense Y: U_x (op(Y)^T V_x)^T;
+//   dense X and Y:  only into dense targets (the plans close the dense set).
+// Low-rank targets append the product's factors and recompress (one CTA per
+// tile); dense targets get C += P Q^T by batched 64 x 64-block GEMM.
+#include "recompress.cuh"
+#include "tileops.h"
+
+namespace {
+
+struct Opnd {
+  bool dense;
+  const double* A;
+  int tA;
+  const double* U;
+  const double* V;
+  int k;
+};
+
+// tile (p, q), p > q, as an operand, optionally transposed
+__device__ __forceinline__ Opnd operand(const TlrView& v, int p, int q, bool trans) {
+  Opnd o;
+  const int64_t t = dtile_index(p, q);
+  o.dense = v.dslot[t] >= 0;
+  if (o.dense) {
+    o.A = tileA(v, t); o.tA = trans; o.U = o.V = nullptr; o.k = v.nb;
+  } else {
+    o.A = nullptr; o.tA = 0;
+    o.U = trans ? tileV(v, t) : tileU(v, t);
+    o.V = trans ? tileU(v, t) : tileV(v, t);
+    o.k = v.rank[t];
+  }
+  return o;
+}
+
+__device__ __forceinline__ void operands(const TlrView& v, int alg, int a, int b, int k, Opnd* X, Opnd* Y,
+                                         double* alpha) {
+  if (alg == ALG_CHOL) { *X = operand(v, a, k, false); *Y = operand(v, b, k, true); *alpha = -1.0; }
+  else if (alg == ALG_TRTRI) { *X = operand(v, a, k, false); *Y = operand(v, k, b, false); *alpha = 1.0; }
+  else { *X = operand(v, k, a, true); *Y = operand(v, k, b, false); *alpha = 1.0; }
+}
+
+__global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items, double eps,
+                             const double* __restrict__ d_zeta, double zpow, int Kmax, int trunc_cap,
+                             double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  const int2 it = items[blockIdx.x];
+  const int nb = v.nb;
+  const int64_t tt = dtile_index(it.x, it.y);
+  Opnd X, Y;
+  double alpha;
+  operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
+  if (X.k == 0 || Y.k == 0) return;
+  if (X.dense && Y.dense) {
+    if (threadIdx.x == 0) set_status(st, TLR_ERR_STATE, tt);
+    return;
+  }
+  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
+  const int k0 = v.rank[tt];
+  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  double* Ut = tileU(v, tt);
+  double* Vt = tileV(v, tt);
+  for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) { w.Up[e] = Ut[e]; w.Vp[e] = Vt[e]; }
+  double* Un = w.Up + (size_t)k0 * nb;
+  double* Vn = w.Vp + (size_t)k0 * nb;
+  int r;
+  if (!X.dense && !Y.dense) {
+    cta_gemm(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);  // W = V_x^T U_y
+    if (Y.k <= X.k) {
+      cta_gemm(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
+      for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
+      r = Y.k;
+    } else {
+      cta_gemm(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Vn, nb);
+      for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
+      r = X.k;
+    }
+  } else if (X.dense) {
+    cta_gemm(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
+    for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
+    r = Y.k;
+  } else {
+    cta_gemm(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
+    for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
+    r = X.k;
+  }
+  __syncthreads();
+  const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, Ut, Vt, st, tt, sh, shi);
+  if (threadIdx.x == 0) v.rank[tt] = kr;
+}
+
+__global__ void k_upd_d_gen(TlrView v, int alg, int k, const int2* __restrict__ items, GemmGen* __restrict__ desc,
+                            double* __restrict__ ws, size_t ws_elems) {
+  const int2 it = items[blockIdx.x];
+  const int nb = v.nb;
+  const int64_t tt = dtile_index(it.x, it.y);
+  Opnd X, Y;
+  double alpha;
+  operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
+  double* W = ws + (size_t)blockIdx.x * ws_elems;
+  double* T = W + (size_t)v.kcap * v.kcap;
+  GemmGen g;
+  g.C = tileA(v, tt); g.ldc = nb; g.m = nb; g.n = nb; g.alpha = alpha; g.beta = 1.0; g.lower = 0;
+  g.lda = nb; g.ldb = nb;
+  if (X.k == 0 || Y.k == 0) {
+    g.k = 0; g.A = g.B = nullptr; g.tA = g.tB = 0;
+  } else if (X.dense && Y.dense) {
+    g.A = X.A; g.tA = X.tA; g.B = Y.A; g.tB = Y.tA; g.k = nb;
+  } else if (X.dense) {  // (op(X) U_y) V_y^T
+    cta_gemm(nb, Y.k, nb, 1.0, X.A, nb, X.tA, Y.U, nb, 0, 0.0, T, nb);
+    g.A = T; g.tA = 0; g.B = Y.V; g.tB = 1; g.k = Y.k;
+  } else if (Y.dense) {  // U_x (op(Y)^T V_x)^T
+    cta_gemm(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, T, nb);
+    g.A = X.U; g.tA = 0; g.B = T; g.tB = 1; g.k = X.k;
+  } else {
+    cta_gemm(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, W, X.k);
+    if (Y.k <= X.k) {
+      cta_gemm(nb, Y.k, X.k, 1.0, X.U, nb, 0, W, X.k, 0, 0.0, T, nb);
+      g.A = T; g.tA = 0; g.B = Y.V; g.tB = 1; g.k = Y.k;
+    } else {
+      cta_gemm(nb, X.k, Y.k, 1.0, Y.V, nb, 0, W, X.k, 1, 0.0, T, nb);
+      g.A = X.U; g.tA = 0; g.B = T; g.tB = 1; g.k = X.k;
+    }
+  }
+  if (threadIdx.x == 0) desc[blockIdx.x] = g;
+}
+
+__global__ void k_gemm_gen(const GemmGen* __restrict__ desc) {
+  const GemmGen g = desc[blockIdx.y];
+  if (g.k <= 0 && g.beta == 1.0) return;
+  cta_gemm_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
+                  gridDim.x, g.lower);
+}
+
+// X (nb x ncol <= 32 columns, ld nb) <- op(T) X, one CTA
+__device__ void cta_trop32(const double* __restrict__ T, int nb, double* __restrict__ X, int ncol, int op,
+                           double alpha) {
+  __shared__ double Ls[32][33];
+  __shared__ double Xs[32][33];
+  const int nblk = (nb + 31) / 32;
+  if (op == TOP_SOLVE) {
+    for (int rb0 = 0; rb0 < nb; rb0 += 32) {
+      const int w = min(32, nb - rb0);
+      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+        const int r = id & 31, c = id >> 5;
+        Ls[r][c] = (r < w && c < w) ? T[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
+        Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
+      }
+      __syncthreads();
+      if (threadIdx.x < ncol) {
+        const int c = threadIdx.x;
+        for (int r = 0; r < w; ++r) {
+          double s = Xs[r][c];
+          for (int l = 0; l < r; ++l) s -= Ls[r][l] * Xs[l][c];
+          Xs[r][c] = s / Ls[r][r];
+        }
+      }
+      __syncthreads();
+      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+        const int r = id & 31, c = id >> 5;
+        if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
+      }
+      for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
+        double acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+        for (int l = 0; l < w; ++l) {
+          const double lv = T[(size_t)(rb0 + l) * nb + r];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < ncol) X[(size_t)c * nb + r] -= acc[c];
+      }
+      __syncthreads();
+    }
+  } else if (op == TOP_SOLVE_T) {
+    for (int bb = nblk - 1; bb >= 0; --bb) {
+      const int rb0 = bb * 32, w = min(32, nb - rb0);
+      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+        const int r = id & 31, c = id >> 5;
+        Ls[r][c] = (r < w && c < w) ? T[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
+        Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
+      }
+      __syncthreads();
+      if (threadIdx.x < ncol) {  // T_bb^T x = b: backward over rows, (T^T)[r][l] = T[l][r]
+        const int c = threadIdx.x;
+        for (int r = w - 1; r >= 0; --r) {
+          double s = Xs[r][c];
+          for (int l = r + 1; l < w; ++l) s -= Ls[l][r] * Xs[l][c];
+          Xs[r][c] = s / Ls[r][r];
+        }
+      }
+      __syncthreads();
+      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+        const int r = id & 31, c = id >> 5;
+        if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
+      }
+      // rows above: X[a] -= sum_l T[rb0 + l, a] Xs[l]
+      for (int a = threadIdx.x; a < rb0; a += blockDim.x) {
+        double acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+        const double* Tc = T + (size_t)a * nb + rb0;
+        for (int l = 0; l < w; ++l) {
+          const double tv = Tc[l];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[c] = fma(tv, Xs[l][c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < ncol) X[(size_t)c * nb + a] -= acc[c];
+      }
+      __syncthreads();
+    }
+  } else {  // TOP_MUL_T: X <- T^T X, top-down in place (row block a needs rows >= a only)
+    for (int ab = 0; ab < nblk; ++ab) {
+      const int a0 = ab * 32, wa = min(32, nb - a0);
+      // thread (q = row in block, c = column): acc = sum_{r >= a0 + q} T[r, a0 + q] X[r, c]
+      const int q = threadIdx.x & 31, cgrp = threadIdx.x >> 5;  // 8 column groups of 4
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r0 = a0; r0 < nb; r0 += 32) {
+        const int wr = min(32, nb - r0);
+        __syncthreads();
+        for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+          const int r = id & 31, c = id >> 5;
+          Ls[r][c] = (r < wr && c < wa) ? T[(size_t)(a0 + c) * nb + r0 + r] : 0.0;  // Ls[r][q] = T[r0+r, a0+q]
+          Xs[r][c] = (r < wr && c < ncol) ? X[(size_t)c * nb + r0 + r] : 0.0;
+        }
+        __syncthreads();
+        for (int r = 0; r < wr; ++r) {
+          const double tv = (r0 + r >= a0 + q) ? Ls[r][q] : 0.0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = fma(tv, Xs[r][cgrp * 4 + j], acc[j]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = cgrp * 4 + j;
+        if (q < wa && c < ncol) X[(size_t)c * nb + a0 + q] = acc[j];
+      }
+      __syncthreads();
+    }
+  }
+  if (alpha != 1.0) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * ncol; e += blockDim.x) X[(size_t)(e / nb) * nb + (e % nb)] *= alpha;
+    __syncthreads();
+  }
+}
+
+__global__ void k_trop_tiles(TlrView v, int kdiag, const int2* __restrict__ items, int which, int op, double alpha) {
+  const int2 it = items[blockIdx.y];
+  const int64_t t = dtile_index(it.x, it.y);
+  const int nb = v.nb;
+  double* X;
+  int ncols;
+  if (which == 2) { X = tileA(v, t); ncols = nb; }
+  else { X = which == 0 ? tileU(v, t) : tileV(v, t); ncols = v.rank[t]; }
+  const int cb = blockIdx.x * 32;
+  if (cb >= ncols) return;
+  cta_trop32(diagT(v, kdiag), nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
+}
+
+__global__ void k_trop_raw(const double* __restrict__ T, int nb, double* __restrict__ X, int ncols, int op,
+                           double alpha) {
+  const int cb = blockIdx.x * 32;
+  if (cb >= ncols) return;
+  cta_trop32(T, nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
+}
+
+// in-place transpose of listed dense tiles
+__global__ void k_transpose_tiles(TlrView v, const int2* __restrict__ items) {
+  const int2 it = items[blockIdx.y];
+  double* A = tileA(v, dtile_index(it.x, it.y));
+  const int nb = v.nb;
+  const int64_t npair = (int64_t)nb * (nb - 1) / 2;
+  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < npair;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    int a, b;
+    decode_lower(id, &a, &b);  // a > b
+    const double t = A[(size_t)b * nb + a];
+    A[(size_t)b * nb + a] = A[(size_t)a * nb + b];
+    A[(size_t)a * nb + b] = t;
+  }
+}
+
+// LAUUM step: D_n += A_kn^T A_kn, n = 0 .. k-1 (one CTA per n builds the descriptor)
+__global__ void k_herk_prep(TlrView v, int k, GemmGen* __restrict__ desc, double* __restrict__ ws, size_t ws_elems) {
+  const int n = blockIdx.x, nb = v.nb;
+  const int64_t t = dtile_index(k, n);
+  GemmGen g;
+  g.C = diagT(v, n); g.ldc = nb; g.m = nb; g.n = nb; g.alpha = 1.0; g.beta = 1.0; g.lower = 0;
+  g.lda = nb; g.ldb = nb;
+  if (v.dslot[t] >= 0) {
+    g.A = tileA(v, t); g.tA = 1; g.B = g.A; g.tB = 0; g.k = nb;
+  } else {
+    const int kr = v.rank[t];
+    double* G = ws + (size_t)blockIdx.x * ws_elems;
+    double* T = G + (size_t)v.kcap * v.kcap;
+    g.k = kr; g.A = T; g.tA = 0; g.B = tileV(v, t); g.tB = 1;
+    if (kr > 0) {
+      cta_gemm(kr, kr, nb, 1.0, tileU(v, t), nb, 1, tileU(v, t), nb, 0, 0.0, G, kr);  // G = U^T U
+      cta_gemm(nb, kr, kr, 1.0, tileV(v, t), nb, 0, G, kr, 0, 0.0, T, nb);            // T = V G
+    }
+  }
+  if (threadIdx.x == 0) desc[blockIdx.x] = g;
+}
+
+int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
+  size_t avail = h->scratch_elems > reserve ? h->scratch_elems - reserve : 0;
+  size_t c = per_item ? avail / per_item : 65535;
+  if (c > 65535) c = 65535;
+  return (int)c;
+}
+
+}  // namespace
+
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s) {
+  if (count <= 0) return TLR_OK;
+  const int blocks = ((m + 63) / 64) * ((n + 63) / 64);
+  for (int c0 = 0; c0 < count; c0 += 65535) {
+    const int cnt = count - c0 < 65535 ? count - c0 : 65535;
+    k_gemm_gen<<<dim3(blocks, cnt), 256, 0, s>>>(d_desc + c0);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
+                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s) {
+  if (n_dn > 0) {
+    const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
+    int chunk = chunk_of(h, per + (sizeof(GemmGen) + 7) / 8, 8);
+    if (chunk < 1) return TLR_ERR_OOM;
+    for (int64_t q0 = 0; q0 < n_dn; q0 += chunk) {
+      const int cnt = (int)(n_dn - q0 < chunk ? n_dn - q0 : chunk);
+      const size_t desc_elems = ((size_t)cnt * sizeof(GemmGen) + 7) / 8 + 1;
+      GemmGen* desc = (GemmGen*)h->scratch;
+      double* ws = h->scratch + desc_elems;
+      k_upd_d_gen<<<cnt, 256, 0, s>>>(v, alg, k, d_dn + q0, desc, ws, per);
+      TLR_LAUNCH_CHECK();
+      int rc = tops_gemm(desc, cnt, h->nb, h->nb, s);
+      if (rc) return rc;
+    }
+  }
+  if (n_lr > 0) {
+    const size_t ie = tlr_item_elems(h->nb, h->kcap);
+    const int chunk = chunk_of(h, ie, 0);
+    if (chunk < 1) return TLR_ERR_OOM;
+    for (int64_t q0 = 0; q0 < n_lr; q0 += chunk) {
+      const int cnt = (int)(n_lr - q0 < chunk ? n_lr - q0 : chunk);
+      k_upd_lr_gen<<<cnt, TLR_THREADS, 0, s>>>(v, alg, k, d_lr + q0, eps, d_zeta, zpow, 2 * h->kcap,
+                                               h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  return TLR_OK;
+}
+
+int tops_trop(tlr_ctx* h, const TlrView& v, int kdiag, const int2* d_lr, int n_lr, int which, const int2* d_dn,
+              int n_dn, int dense_right, int op, double alpha, cudaStream_t s) {
+  if (n_lr > 0) {
+    k_trop_tiles<<<dim3((h->kcap + 31) / 32, n_lr), 256, 0, s>>>(v, kdiag, d_lr, which, op, alpha);
+    TLR_LAUNCH_CHECK();
+  }
+  if (n_dn > 0) {
+    if (dense_right) {
+      k_transpose_tiles<<<dim3(64, n_dn), 256, 0, s>>>(v, d_dn);
+      TLR_LAUNCH_CHECK();
+    }
+    k_trop_tiles<<<dim3((h->nb + 31) / 32, n_dn), 256, 0, s>>>(v, kdiag, d_dn, 2, op, alpha);
+    TLR_LAUNCH_CHECK();
+    if (dense_right) {
+      k_transpose_tiles<<<dim3(64, n_dn), 256, 0, s>>>(v, d_dn);
+      TLR_LAUNCH_CHECK();
+    }
+  }
+  return TLR_OK;
+}
+
+int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s) {
+  k_trop_raw<<<(ncols + 31) / 32, 256, 0, s>>>(T, nb, X, ncols, op, alpha);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tops_herk_row(tlr_ctx* h, const TlrView& v, int k, cudaStream_t s) {
+  if (k <= 0) return TLR_OK;
+  const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
+  const size_t desc_elems = ((size_t)k * sizeof(GemmGen) + 7) / 8 + 1;
+  if ((size_t)k * per + desc_elems > h->scratch_elems) return TLR_ERR_OOM;
+  GemmGen* desc = (GemmGen*)h->scratch;
+  k_herk_prep<<<k, 256, 0, s>>>(v, k, desc, h->scratch + desc_elems, per);
+  TLR_LAUNCH_CHECK();
+  return tops_gemm(desc, k, h->nb, h->nb, s);
+}

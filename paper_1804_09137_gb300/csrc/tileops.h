@@ -1,0 +1,37 @@
+// Generic batched tile operations on a TlrView (hybrid dense / low-rank tiles),
+// shared by the Cholesky factorization and the inverse (TRTRI, LAUUM).
+#pragma once
+#include "tile.cuh"
+
+// update algorithms: target (a, b) at step k
+#define ALG_CHOL 0   // A_ab -= L_ak L_bk^T
+#define ALG_TRTRI 1  // A_ab += A_ak A_kb
+#define ALG_LAUUM 2  // A_ab += A_ka^T A_kb
+
+// triangular ops X <- alpha op(T) X, T the (lower) diagonal tile
+#define TOP_SOLVE 0   // T^{-1} X
+#define TOP_SOLVE_T 1 // T^{-T} X
+#define TOP_MUL_T 2   // T^T X
+
+struct GemmGen {
+  const double* A;
+  const double* B;
+  double* C;
+  int m, n, k, lda, ldb, ldc, tA, tB;
+  double alpha, beta;
+  int lower;
+};
+
+// low-rank targets (recompressed at tau = eps * zeta^zpow, zeta = *d_zeta or 1) and dense targets
+int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
+                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s);
+// X <- alpha op(T_kdiag) X on listed tiles: low-rank ones on U (which = 0) or V (which = 1), dense ones on A
+// (transposed first and back when dense_right: A <- (alpha op(T) A^T)^T)
+int tops_trop(tlr_ctx* h, const TlrView& v, int kdiag, const int2* d_lr, int n_lr, int which, const int2* d_dn,
+              int n_dn, int dense_right, int op, double alpha, cudaStream_t s);
+// X <- alpha op(T) X for a raw nb x ncols matrix
+int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s);
+// batched general GEMM from a device descriptor array
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s);
+// D_n += A_kn^T A_kn for n = 0 .. k-1 (LAUUM step)
+int tops_herk_row(tlr_ctx* h, const TlrView& v, int k, cudaStream_t s);

@@ -194,9 +194,9 @@ def test_not_spd_reported(T):
 
 
 def test_rank_cap_reported(T):
-    # low-rank tiles allowed up to rank 24 but storage capped at 16: the overflow is reported
-    x, y = inputs.jittered_grid(16)
-    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-12, rank_cap=16, dense_rank=24)
+    # eps-ranks 10..42 (oracle SVD), several in 13..20: low rank allowed above 12 but storage capped at 12
+    x, y = inputs.jittered_grid(24)
+    h = T.Handle(dev(x), dev(y), nb=64, eps=1e-6, rank_cap=12, dense_rank=16)
     h.matern_generate((1.0, 0.3, 1.0))
     h.compress()
     rc, _ = h.status()
@@ -211,3 +211,61 @@ def test_calls_out_of_order(T):
         h.loglik(z)
     with pytest.raises(T.TlrError):
         h.potrf()
+
+
+@pytest.mark.parametrize("theta", [(1.0, 0.1, 0.5), (1.0, 0.3, 1.0), (0.7, 0.15, 1.4)])
+def test_gradient_matches_oracle(T, theta):
+    x, y, z = problem(26, theta, n=650)
+    ll_ref, g_ref = DN.loglik_grad(x, y, z, theta)
+    h = T.Handle(dev(x), dev(y), nb=96, eps=1e-12, rank_cap=96)
+    h.factor(theta)
+    ll, g = h.loglik_grad(dev(z))
+    h.check()
+    ll, g = ll.cpu().numpy()[0], g.cpu().numpy()
+    assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-6 * np.max(np.abs(g_ref)))
+
+
+def test_gradient_dense_mode(T):
+    theta = (1.0, 0.3, 1.0)
+    x, y, z = problem(24, theta, n=560)
+    _, g_ref = DN.loglik_grad(x, y, z, theta)
+    h = T.Handle(dev(x), dev(y), nb=80, eps=-1.0)
+    h.factor(theta)
+    _, g = h.loglik_grad(dev(z))
+    h.check()
+    np.testing.assert_allclose(g.cpu().numpy(), g_ref, rtol=1e-8, atol=1e-8 * np.max(np.abs(g_ref)))
+
+
+def test_gradient_sigma2_identity_at_tlr_eps(T):
+    # Sigma = sigma2 R: dl/dsigma2 = (q - n) / (2 sigma2) holds at any size
+    theta = (1.4, 0.3, 1.0)
+    x, y = inputs.jittered_grid(40)
+    h = T.Handle(dev(x), dev(y), nb=200, eps=1e-8)
+    h.factor(theta)
+    z = h.sample(dev(inputs.standard_normal(len(x))))
+    out = h.loglik(z).cpu().numpy()
+    _, g = h.loglik_grad(z)
+    h.check()
+    want = (out[2] - len(x)) / (2 * theta[0])
+    assert abs(g.cpu().numpy()[0] - want) <= 1e-6 * abs(want) + 1e-6
+
+
+def test_gradient_finite_differences_of_gpu_loglik(T):
+    theta = np.array([1.0, 0.2, 0.8])
+    x, y, z = problem(30, tuple(theta), n=880)
+    h = T.Handle(dev(x), dev(y), nb=128, eps=1e-12, rank_cap=128)
+    zt = dev(z)
+    h.factor(theta)
+    _, g = h.loglik_grad(zt)
+    g = g.cpu().numpy()
+    for p in range(3):
+        hp = 1e-6 * theta[p]
+        vals = []
+        for sgn in (1, -1):
+            th = theta.copy()
+            th[p] += sgn * hp
+            h.factor(th)
+            vals.append(h.loglik(zt).cpu().numpy()[0])
+        fd = (vals[0] - vals[1]) / (2 * hp)
+        assert abs(g[p] - fd) <= 1e-5 * max(abs(fd), 1.0), (p, g[p], fd)
