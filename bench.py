@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Benchmark of one Matérn log-likelihood + gradient evaluation in TLR form.
+
+Workload (the n = 90,000 configuration): 300 x 300 jittered grid on [0,1]^2,
+theta = (sigma2, beta, nu) = (1, 0.3, 1.0), tile size nb = 900, absolute
+threshold eps = 1e-7, float64.  One step is the whole path on one batch:
+Matérn generation, compression of the off-diagonal tiles, TLR Cholesky,
+log-determinant and solves (eq. 1), the adjoint gradient (TLR inverse and the
+fused regenerate-and-reduce pass) and kriging of 100 held-out points (eq. 4)
+on the same factor.  z is a draw from the model, z = L e with L the TLR
+factor (synthesised before timing).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead
+(dense float64 likelihood + gradient on a bounded sample, scaled by n^3).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "loglik+grad evals/s at n=90k: TLR vs dense FP64, 1 GB300, rel err≤1e-6"
+UNIT = "evals/s"
+THETA = (1.0, 0.3, 1.0)
+# float64 peak of the GB300 derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22500.json")
+KERNEL_SOURCES = ["tileops.cu", "recompress.cuh", "tile.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1804_09137_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
+    p.add_argument("--side", type=int, default=300)
+    p.add_argument("--nb", type=int, default=900)
+    p.add_argument("--eps", type=float, default=1e-7)
+    p.add_argument("--rank-cap", type=int, default=256)
+    p.add_argument("--dense-side", type=int, default=150, help="grid side of the dense FP64 comparator run")
+    p.add_argument("--no-dense", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-side", type=int, default=40, help="grid side of the CPU oracle sample")
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def log(*a):
+    print("[bench]", *a, file=sys.stderr, flush=True)
+
+
+def dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(side):
+    """Seconds of one dense CPU-oracle likelihood+gradient evaluation at n = side^2."""
+    from oracle import dense as DN
+    from paper_1804_09137_gb300 import inputs
+
+    x, y = inputs.jittered_grid(side)
+    z = DN.sample(x, y, THETA, inputs.standard_normal(len(x)))
+    t = time.perf_counter()
+    DN.loglik_grad(x, y, z, THETA)
+    return time.perf_counter() - t, len(x)
+
+
+def run_reference(a):
+    world, rank, _ = dist()
+    if rank != 0:
+        return
+    n_full = a.side * a.side
+    times = []
+    for i in range(a.warmup + a.steps):
+        dt, ns = cpu_oracle_sample(a.cpu_side)
+        if i >= a.warmup:
+            times.append(dt)
+    scale = (n_full / ns) ** 3
+    t_full = statistics.mean(times) * scale
+    val = 1.0 / t_full
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"matern_n{n_full}", "n": n_full},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"dense float64 oracle loglik+grad at n={ns} ({a.cpu_side}^2 grid), "
+                                       f"mean of {a.steps} runs {statistics.mean(times):.3f} s, scaled by "
+                                       f"(n/{ns})^3 to n={n_full}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+
+    world, rank, local = dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+
+        tdist.init_process_group("nccl")
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_1804_09137_gb300 import inputs
+    from paper_1804_09137_gb300 import tlr as T
+
+    dev = torch.device("cuda", local)
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(a.side)
+    n = len(x)
+    obs, held = inputs.holdout(n, 100)
+    xo, yo = t64(x[obs]), t64(y[obs])
+    xh, yh = t64(x[held]), t64(y[held])
+    h = T.Handle(xo, yo, nb=a.nb, eps=a.eps, rank_cap=a.rank_cap)
+    # synthetic measurements z = L e from the factor itself (not timed): a draw from the TLR model
+    h.factor(THETA)
+    z = h.sample(t64(inputs.standard_normal(len(obs))))
+    h.check()
+    ll = torch.empty(1, dtype=torch.float64, device=dev)
+    grad = torch.empty(3, dtype=torch.float64, device=dev)
+    pred = torch.empty(len(held), dtype=torch.float64, device=dev)
+
+    def step(zz):
+        h.matern_generate(THETA)
+        h.compress()
+        h.potrf()
+        h.loglik_grad(zz, ll, grad)
+        h.predict(zz, xh, yh, pred)
+
+    log("setup done", f"n={len(obs)}")
+    for i in range(a.warmup):
+        t0 = time.perf_counter()
+        step(z)
+        torch.cuda.synchronize()
+        log(f"warmup {i}: {time.perf_counter() - t0:.2f} s")
+    h.check()
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    barrier()
+    T.profile(True)
+    l0 = T.launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step(z)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = T.launch_count() - l0
+    prof = T.profile_read()
+    T.profile(False)
+    ms = e0.elapsed_time(e1) / a.steps
+    h.check()
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world / (ms / 1e3)
+    log(f"timed: {ms:.1f} ms/step, profile {prof}")
+
+    # ---- end to end: pinned host z in, (l, grad) out, every step
+    z_h = z.cpu().pin_memory()
+    out_h = torch.empty(4, dtype=torch.float64).pin_memory()
+    out_d = torch.empty(4, dtype=torch.float64, device=dev)
+    z_d = torch.empty_like(z)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        z_d.copy_(z_h, non_blocking=True)
+        step(z_d)
+        out_d[0:1].copy_(ll)
+        out_d[1:4].copy_(grad)
+        out_h.copy_(out_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / a.steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    log(f"e2e: {e2e_s:.2f} s/step")
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(z_h.numel() * 8),
+           "d2h_bytes_per_step": int(out_h.numel() * 8)}
+
+    result = out_h.numpy().copy()
+    ranks = h.rank_stats()
+    counts = h.tile_counts()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+        return
+
+    # ---- roofline of the dominant kernel (low-rank update with recompression)
+    achieved = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else None
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("source_sha") == kernel_hash():
+            traffic = tr.get("dram_bytes_per_launch")
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
+            "kernel": "k_upd_lr_gen", "launches": prof["launches"], "kernel_ms_per_step": prof["ms"] / a.steps,
+            "peak_source": "float64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured "
+                           "1.19 TFLOP/s)"}
+
+    # ---- dense float64 GPU comparator (every tile dense), scaled by n^3
+    dense = None
+    if not a.no_dense:
+        xd, yd = inputs.jittered_grid(a.dense_side)
+        nd = len(xd)
+        hd = T.Handle(t64(xd), t64(yd), nb=a.nb, eps=-1.0)
+        zd = t64(inputs.standard_normal(nd))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hd.factor(THETA)
+        hd.loglik_grad(zd)
+        torch.cuda.synchronize()
+        td = time.perf_counter() - t0
+        hd.check()
+        hd.close()
+        scale = (n / nd) ** 3
+        dense = {"value": 1.0 / (td * scale), "unit": UNIT, "measured_n": nd, "measured_s": td,
+                 "scaled_to_n": n, "scaling": "n^3", "tlr_speedup": value / (1.0 / (td * scale))}
+
+    cpu = None
+    if not a.no_cpu and world == 1:
+        dt, ns = cpu_oracle_sample(a.cpu_side)
+        scale = (n / ns) ** 3
+        cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"dense float64 oracle loglik+grad at n={ns} ({a.cpu_side}^2 grid) took {dt:.3f} s, "
+                         f"scaled by (n/{ns})^3 to n={n}"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (jittered grid, z drawn from the model)",
+            "config": {"workload": f"matern_tlr_n{len(obs)}_nb{a.nb}_eps{a.eps:g}_theta1-0.3-1.0",
+                       "n": len(obs), "nb": a.nb, "eps": a.eps, "rank_cap": a.rank_cap, "theta": list(THETA),
+                       "kriging_points": len(held), "l2": "inputs larger than L2 (TLR factor > 1 GB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "dense_fp64_gpu": dense,
+            "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,
+                       "tiles": counts}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -53,7 +53,10 @@ typedef struct {
  * the points before tiling, 0 = keep the caller's order; dense_rank: an
  * off-diagonal tile whose eps-rank exceeds it is stored and updated dense
  * (0 = max(16, nb/16)); tiles are also made dense where a dense x dense
- * product would land on them during the factorization. */
+ * product would land on them during the factorization; inv_scale: the
+ * gradient's inverse Sigma^{-1} truncates its tiles at inv_scale * eps *
+ * zeta^(1/2) (L^{-1}) and inv_scale * eps * zeta (Sigma^{-1}), zeta = the
+ * largest 1 / L_aa^2 (0 = 0.1). */
 typedef struct {
   int nb;
   double eps;
@@ -61,6 +64,7 @@ typedef struct {
   int truncate_at_cap;
   int order;
   int dense_rank;
+  double inv_scale;
 } tlr_opts;
 
 enum {
@@ -147,6 +151,28 @@ int tlr_tile_counts(tlr_handle h, int64_t* n_lowrank, int64_t* n_dense);
 /* perm[s] = caller index of the s-th point in the handle's sorted order
  * (device buffer of n int32).  Synchronises `stream`. */
 int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream);
+
+/* Diagnostics (no counterpart in the paper). */
+
+/* Rank statistics of the low-rank tiles of the inverse Sigma^{-1} built by the
+ * last tlr_loglik_grad, and its number of dense off-diagonal tiles.
+ * Synchronises. */
+int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* n_dense);
+
+/* Total kernel launches issued by the library in this process. */
+int tlr_launch_count(int64_t* count);
+
+/* enable != 0: from now on time every launch of the low-rank update kernel
+ * (the TLR GEMM with recompression, the dominant kernel) with CUDA events on
+ * its stream and accumulate its algorithmic float64 flops on the device
+ * (Householder QR, core product, Jacobi rotations as executed, applying Q,
+ * forming the product); enable == 0 stops.  Either call resets the counters
+ * and synchronises the device. */
+int tlr_profile(int enable);
+
+/* Launches timed, their summed device time (ms) and flops since tlr_profile.
+ * Synchronises the device. */
+int tlr_profile_read(int64_t* launches, double* ms, double* flops);
 
 #ifdef __cplusplus
 }

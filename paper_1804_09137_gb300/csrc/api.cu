@@ -14,6 +14,33 @@
 #include "common.cuh"
 
 
+long long g_tlr_launches = 0;
+TlrProfile g_tlr_prof = {0, nullptr, 0, 0.0};
+
+namespace {
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev;  // recorded (start, stop) pairs
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev_free;
+cudaEvent_t g_ev_open = nullptr;
+}  // namespace
+
+void tlr_prof_begin(cudaStream_t s) {
+  cudaEvent_t a, b;
+  if (!g_ev_free.empty()) {
+    a = g_ev_free.back().first;
+    b = g_ev_free.back().second;
+    g_ev_free.pop_back();
+  } else {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  cudaEventRecord(a, s);
+  g_ev.push_back({a, b});
+}
+
+void tlr_prof_end(cudaStream_t s) {
+  if (!g_ev.empty()) cudaEventRecord(g_ev.back().second, s);
+}
+
 namespace {
 
 // digamma by upward recurrence to x >= 10 and the asymptotic series
@@ -406,6 +433,61 @@ int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   TLR_CUDA_TRY(cudaMemcpyAsync(perm, h->perm, h->n * sizeof(int), cudaMemcpyDeviceToDevice, s));
   TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  return TLR_OK;
+}
+
+int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* n_dense) {
+  if (!h) return -1;
+  if (!h->rankz || !h->kindz) return TLR_ERR_STATE;
+  TLR_CUDA_TRY(cudaStreamSynchronize(h->last_stream));
+  std::vector<int> r(std::max<int64_t>(h->ntiles, 1), 0);
+  if (h->ntiles > 0)
+    TLR_CUDA_TRY(cudaMemcpy(r.data(), h->rankz, h->ntiles * sizeof(int), cudaMemcpyDeviceToHost));
+  int mn = INT32_MAX, mx = 0;
+  double sum = 0;
+  int64_t nlr = 0;
+  for (int64_t t = 0; t < h->ntiles; ++t) {
+    if (h->kindz[t]) continue;
+    mn = std::min(mn, r[t]); mx = std::max(mx, r[t]); sum += r[t]; ++nlr;
+  }
+  if (nlr == 0) mn = 0;
+  if (kmin) *kmin = mn;
+  if (kmax) *kmax = mx;
+  if (kmean) *kmean = nlr > 0 ? sum / nlr : 0.0;
+  if (n_dense) *n_dense = h->ndensez;
+  return TLR_OK;
+}
+
+int tlr_launch_count(int64_t* count) {
+  if (!count) return -1;
+  *count = g_tlr_launches;
+  return TLR_OK;
+}
+
+int tlr_profile(int enable) {
+  if (!g_tlr_prof.d_flops) {
+    if (cudaMalloc((void**)&g_tlr_prof.d_flops, sizeof(double)) != cudaSuccess) return TLR_ERR_OOM;
+  }
+  TLR_CUDA_TRY(cudaDeviceSynchronize());
+  TLR_CUDA_TRY(cudaMemset(g_tlr_prof.d_flops, 0, sizeof(double)));
+  for (auto& e : g_ev) g_ev_free.push_back(e);
+  g_ev.clear();
+  g_tlr_prof.enabled = enable ? 1 : 0;
+  return TLR_OK;
+}
+
+int tlr_profile_read(int64_t* launches, double* ms, double* flops) {
+  TLR_CUDA_TRY(cudaDeviceSynchronize());
+  double tot = 0.0;
+  for (auto& e : g_ev) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) tot += t;
+  }
+  double fl = 0.0;
+  if (g_tlr_prof.d_flops) TLR_CUDA_TRY(cudaMemcpy(&fl, g_tlr_prof.d_flops, sizeof(double), cudaMemcpyDeviceToHost));
+  if (launches) *launches = (int64_t)g_ev.size();
+  if (ms) *ms = tot;
+  if (flops) *flops = fl;
   return TLR_OK;
 }
 

@@ -41,7 +41,9 @@
 #define ZP_L2_D 7
 #define ZP_L3_LR 8
 #define ZP_L3_D 9
-#define ZPH 10
+#define ZP_T2_DD 10
+#define ZP_L2_DD 11
+#define ZPH 12
 
 #define ST_CODE 0
 #define ST_INFO 1
@@ -118,8 +120,10 @@ struct tlr_ctx {
     }                                                                        \
   } while (0)
 
+extern long long g_tlr_launches;  // kernel launches issued by the library
 #define TLR_LAUNCH_CHECK()                                                   \
   do {                                                                       \
+    ++g_tlr_launches;                                                        \
     cudaError_t e_ = cudaGetLastError();                                     \
     if (e_ != cudaSuccess) {                                                 \
       fprintf(stderr, "tlr: launch failed: %s (%s:%d)\n",                   \
@@ -229,6 +233,18 @@ __device__ __forceinline__ double cov_pts(const double* __restrict__ tab, const 
   const double dx = x[p] - x[q], dy = y[p] - y[q];
   return matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy));
 }
+
+// profiling of the low-rank update kernel (the dominant one): per-launch CUDA
+// events and a device-side count of its algorithmic float64 flops
+struct TlrProfile {
+  int enabled;
+  double* d_flops;     // device accumulator
+  long long launches;
+  double ms;
+};
+extern TlrProfile g_tlr_prof;
+void tlr_prof_begin(cudaStream_t s);
+void tlr_prof_end(cudaStream_t s);
 
 // ------------------------------------------------------------ host helpers
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);

@@ -22,98 +22,34 @@
 namespace {
 
 // ------------------------------------------------------------- compression
+struct GenEntry {  // entries of Sigma_ij generated from the Matérn table
+  const double* tab;
+  MaternParams mp;
+  const double* x;
+  const double* y;
+  int64_t n, pi0, pj0;
+  __device__ __forceinline__ double operator()(int a, int b) const {
+    return cov_pts(tab, mp, x, y, n, pi0 + a, pj0 + b);
+  }
+};
+
 __global__ void k_aca_compress(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
                                const double* __restrict__ y, int64_t n, TlrView v, int64_t t0, double eps,
                                int aca_max, int Kmax, int trunc_cap, double* __restrict__ ws, size_t item_elems,
                                long long* __restrict__ st) {
   extern __shared__ double dsm[];
-  const int nb = v.nb;
-  double* row = dsm;
-  double* col = dsm + nb;
-  int* used = (int*)(dsm + 2 * nb);
   __shared__ double sh[TLR_THREADS / 32 + 2];
   __shared__ int shi[TLR_THREADS / 32 + 2];
+  const int nb = v.nb;
   const int64_t t = t0 + blockIdx.x;
   int ti, tj;
   decode_lower(t, &ti, &tj);
   ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
   const int64_t pi0 = (int64_t)ti * nb, pj0 = (int64_t)tj * nb;
   const int mi = (int)min((int64_t)nb, n - pi0), mj = (int)min((int64_t)nb, n - pj0);
-  for (int a = threadIdx.x; a < nb; a += blockDim.x) used[a] = (a >= mi);
-  const double tol = eps * 0.125;
-  int istar = 0, k = 0, nsmall = 0, conv = 0;
-  __syncthreads();
-  while (true) {
-    if (k >= aca_max) break;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      double val = 0.0;
-      if (b < mj) {
-        val = cov_pts(tab, mp, x, y, n, pi0 + istar, pj0 + b);
-        for (int l = 0; l < k; ++l) val = fma(-w.Up[(size_t)l * nb + istar], w.Vp[(size_t)l * nb + b], val);
-      }
-      row[b] = val;
-    }
-    if (threadIdx.x == 0) used[istar] = 1;
-    double av = -1.0, rmax;
-    int ai = 0x7fffffff;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const double a = fabs(row[b]);
-      if (a > av) { av = a; ai = b; }
-    }
-    const int jstar = block_argmax(av, ai, sh, shi, &rmax);
-    if (!(rmax > 1e-3 * tol)) {  // residual row (numerically) zero: sample another row
-      if (++nsmall >= 3) { conv = 1; break; }
-      if (threadIdx.x == 0) {
-        int nxt = -1;
-        for (int s2 = 1; s2 <= nb; ++s2) {
-          const int cand = (int)(((int64_t)istar + (int64_t)97 * s2) % nb);
-          if (!used[cand]) { nxt = cand; break; }
-        }
-        shi[0] = nxt;
-      }
-      __syncthreads();
-      const int nxt = shi[0];
-      __syncthreads();
-      if (nxt < 0) { conv = 1; break; }
-      istar = nxt;
-      continue;
-    }
-    const double delta = row[jstar];
-    double pu = 0.0, pv = 0.0;
-    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
-      double val = 0.0;
-      if (a < mi) {
-        val = cov_pts(tab, mp, x, y, n, pi0 + a, pj0 + jstar);
-        for (int l = 0; l < k; ++l) val = fma(-w.Vp[(size_t)l * nb + jstar], w.Up[(size_t)l * nb + a], val);
-      }
-      col[a] = val;
-      w.Up[(size_t)k * nb + a] = val;
-      const double rv = row[a] / delta;
-      w.Vp[(size_t)k * nb + a] = rv;
-      pu = fma(val, val, pu);
-      pv = fma(rv, rv, pv);
-    }
-    const double nu2 = block_sum(pu, sh);
-    const double nv2 = block_sum(pv, sh);
-    ++k;
-    if (sqrt(nu2 * nv2) <= tol) {
-      if (++nsmall >= 2) { conv = 1; break; }
-    } else {
-      nsmall = 0;
-    }
-    av = -1.0;
-    ai = 0x7fffffff;
-    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
-      if (!used[a]) {
-        const double val = fabs(col[a]);
-        if (val > av) { av = val; ai = a; }
-      }
-    }
-    double cm;
-    const int nxt = block_argmax(av, ai, sh, shi, &cm);
-    if (cm < 0.0) { conv = 1; break; }  // every row used: the cross approximation is exact
-    istar = nxt;
-  }
+  GenEntry ge{tab, mp, x, y, n, pi0, pj0};
+  int conv = 0;
+  const int k = cta_aca(ge, nb, mi, mj, eps * 0.125, aca_max, w, dsm, sh, shi, &conv);
   if (!conv) {  // not compressible within aca_max terms: stored dense
     if (threadIdx.x == 0) v.rank[t] = -1;
     return;

@@ -14,7 +14,8 @@
 // Low-rank targets are recompressed at tau_M = eps sqrt(zeta) (TRTRI) and
 // tau_Z = eps zeta (LAUUM), zeta = max_a 1 / L_aa^2 ~ the scale of Z's
 // diagonal, so that the truncation is relative to the size of M and Z as eps
-// is to Sigma.  The dense set is closed under both algorithms' fill.
+// is to Sigma.  Z keeps the factor's dense tiles; a dense x dense product that
+// lands on a low-rank tile is formed by GEMM and recompressed.
 #include <stdlib.h>
 #include <string.h>
 
@@ -110,16 +111,10 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   char* K = h->kindz;
   for (int64_t t = 0; t < T; ++t) K[t] = h->kind ? h->kind[t] : 0;
   auto kd = [&](int p, int q) -> char& { return K[tile_index(p, q)]; };
-  for (int k = 0; k < nt; ++k)  // TRTRI fill: A_ij += A_ik A_kj
-    for (int i = k + 1; i < nt; ++i)
-      if (kd(i, k))
-        for (int j = 0; j < k; ++j)
-          if (kd(k, j)) kd(i, j) = 1;
-  for (int k = 0; k < nt; ++k)  // LAUUM fill: A_mn += A_km^T A_kn
-    for (int m = 0; m < k; ++m)
-      if (kd(k, m))
-        for (int n2 = 0; n2 < m; ++n2)
-          if (kd(k, n2)) kd(m, n2) = 1;
+  // No fill closure: the inverse of a banded triangular matrix is full, so the
+  // closure would make every tile dense although the far tiles of L^{-1} and
+  // Sigma^{-1} are numerically low rank.  A dense x dense product that lands on
+  // a low-rank tile is materialised and recompressed instead (phases *_DD).
   std::vector<int> slot(std::max<int64_t>(T, 1), -1);
   int nd = 0;
   for (int64_t t = 0; t < T; ++t)
@@ -146,16 +141,24 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
         case ZP_T1_LR: case ZP_T1_D:
           for (int i = k + 1; i < nt; ++i) if (kd(i, k) == want) L.push_back(make_int2(i, k));
           break;
-        case ZP_T2_LR: case ZP_T2_D:
+        case ZP_T2_LR: case ZP_T2_D: case ZP_T2_DD:
           for (int i = k + 1; i < nt; ++i)
-            for (int j = 0; j < k; ++j) if (kd(i, j) == want) L.push_back(make_int2(i, j));
+            for (int j = 0; j < k; ++j) {
+              const bool dd = kd(i, k) && kd(k, j);
+              if (ph == ZP_T2_D ? kd(i, j) == 1 : (kd(i, j) == 0 && dd == (ph == ZP_T2_DD)))
+                L.push_back(make_int2(i, j));
+            }
           break;
         case ZP_T3_LR: case ZP_T3_D: case ZP_L3_LR: case ZP_L3_D:
           for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
           break;
-        case ZP_L2_LR: case ZP_L2_D:
+        case ZP_L2_LR: case ZP_L2_D: case ZP_L2_DD:
           for (int m = 1; m < k; ++m)
-            for (int n2 = 0; n2 < m; ++n2) if (kd(m, n2) == want) L.push_back(make_int2(m, n2));
+            for (int n2 = 0; n2 < m; ++n2) {
+              const bool dd = kd(k, m) && kd(k, n2);
+              if (ph == ZP_L2_D ? kd(m, n2) == 1 : (kd(m, n2) == 0 && dd == (ph == ZP_L2_DD)))
+                L.push_back(make_int2(m, n2));
+            }
           break;
       }
     }
@@ -237,7 +240,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
       TLR_LAUNCH_CHECK();
     }
   }
-  const double eps = h->opts.eps > 0 ? h->opts.eps : 0.0;
+  const double eps = (h->opts.eps > 0 ? h->opts.eps : 0.0) * (h->opts.inv_scale > 0 ? h->opts.inv_scale : 0.1);
   double* X = h->scratch;  // nb x nb workspace for the diagonal tiles
   // ---- TRTRI
   for (int k = 0; k < nt; ++k) {
@@ -246,6 +249,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
     ZTRY(tops_trop(h, z, k, L(ZP_T1_LR), N(ZP_T1_LR), 1, L(ZP_T1_D), N(ZP_T1_D), 1, TOP_SOLVE_T, -1.0, s));
     ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s));
+    ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), N(ZP_T2_DD), eps, d_zeta, 0.5, s));
     ZTRY(tops_trop(h, z, k, L(ZP_T3_LR), N(ZP_T3_LR), 0, L(ZP_T3_D), N(ZP_T3_D), 0, TOP_SOLVE, 1.0, s));
     k_eye<<<256, 256, 0, s>>>(X, nb);
     TLR_LAUNCH_CHECK();
@@ -261,6 +265,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
     ZTRY(tops_herk_row(h, z, k, s));
     ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s));
+    ZTRY(tops_update_dd(h, z, ALG_LAUUM, k, L(ZP_L2_DD), N(ZP_L2_DD), eps, d_zeta, 1.0, s));
     ZTRY(tops_trop(h, z, k, L(ZP_L3_LR), N(ZP_L3_LR), 0, L(ZP_L3_D), N(ZP_L3_D), 0, TOP_MUL_T, 1.0, s));
     // D_k <- D_k^T D_k via the workspace
     GemmGen g;

@@ -97,12 +97,13 @@ __device__ __forceinline__ void rr_pair(int K2, int rr, int pi, int* p, int* q) 
 }
 
 // one-sided Jacobi: M (K x K, ld K) <- M Y with orthogonal columns, Y (K x K) accumulated
-__device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K, int* sh_flag) {
+__device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K, int* sh_flag, double* flops) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) Y[e] = ((e % K) == (e / K)) ? 1.0 : 0.0;
   __syncthreads();
   if (K < 2) return;
   const int K2 = K + (K & 1);
+  double fl = 0.0;  // per-warp count, lane 0 holds it
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
     __syncthreads();
@@ -124,7 +125,9 @@ __device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
+        fl += 6.0 * K;
         if (al > 0.0 && be > 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          fl += 12.0 * K;
           const double zeta = (be - al) / (2.0 * ga);
           const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -150,12 +153,14 @@ __device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K
     if (*sh_flag == 0) break;
     __syncthreads();
   }
+  if (lane == 0 && flops) atomicAdd(flops, fl);
 }
 
 // Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
 // singular values > eps.  Returns k (same in all threads).
 __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, double* Uo,
-                              double* Vo, long long* st, long long info, double* sh, int* shi) {
+                              double* Vo, long long* st, long long info, double* sh, int* shi,
+                              double* flops = nullptr) {
   if (K == 0) return 0;
   cta_geqr2(w.Up, nb, nb, K, w.tu, sh);
   cta_geqr2(w.Vp, nb, nb, K, w.tv, sh);
@@ -169,7 +174,10 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     w.M[(size_t)b * Ke + a] = s;
   }
   __syncthreads();
-  cta_jacobi(w.M, w.Y, Ke, shi);
+  __shared__ double jfl;
+  if (threadIdx.x == 0) jfl = 0.0;
+  __syncthreads();
+  cta_jacobi(w.M, w.Y, Ke, shi, flops ? &jfl : nullptr);
   // singular values = column norms of M
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int l = warp; l < Ke; l += nw) {
@@ -211,6 +219,108 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   cta_apply_q(w.Up, nb, nb, Ke, w.tu, Uo, nb, k);
   cta_apply_q(w.Vp, nb, nb, Ke, w.tv, Vo, nb, k);
   __syncthreads();
+  if (flops && threadIdx.x == 0) {
+    // Householder QR of two nb x K factors, triangular core product, column norms,
+    // applying both Q to k columns, plus the Jacobi sweeps as executed
+    const double m = nb, KK = K, Kq = Ke;
+    const double qr = 2.0 * (2.0 * m * KK * Kq - (KK + m) * Kq * Kq + 2.0 * Kq * Kq * Kq / 3.0);
+    const double core = 2.0 * Kq * Kq * (KK - 2.0 * Kq / 3.0);
+    const double apply = 2.0 * k * (4.0 * m * Kq - 2.0 * Kq * Kq);
+    atomicAdd(flops, qr + core + 2.0 * Kq * Kq + apply + jfl);
+  }
+  return k;
+}
+
+
+// Adaptive cross approximation with partial pivoting of an mi x mj block (rows
+// and columns beyond are zero) whose entries come from E(a, b): each step takes
+// the residual row at the pivot row, its largest entry as pivot column, the
+// residual column there, and the next pivot row where that column is largest
+// among unused rows.  Stops (conv = 1) after two successive rank-one terms with
+// ||u|| ||v|| <= tol, when the residual rows are zero, or when every row is used;
+// conv = 0 when aca_max terms did not suffice.  Factors go to w.Up / w.Vp.
+// Shared memory: dsm >= 2 nb doubles + nb ints.
+template <class E>
+__device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int aca_max, const ItemWs& w,
+                       double* dsm, double* sh, int* shi, int* conv_out) {
+  double* row = dsm;
+  double* col = dsm + nb;
+  int* used = (int*)(dsm + 2 * nb);
+  for (int a = threadIdx.x; a < nb; a += blockDim.x) used[a] = (a >= mi);
+  int istar = 0, k = 0, nsmall = 0, conv = 0;
+  __syncthreads();
+  while (true) {
+    if (k >= aca_max) break;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      double val = 0.0;
+      if (b < mj) {
+        val = entry(istar, b);
+        for (int l = 0; l < k; ++l) val = fma(-w.Up[(size_t)l * nb + istar], w.Vp[(size_t)l * nb + b], val);
+      }
+      row[b] = val;
+    }
+    if (threadIdx.x == 0) used[istar] = 1;
+    double av = -1.0, rmax;
+    int ai = 0x7fffffff;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double a = fabs(row[b]);
+      if (a > av) { av = a; ai = b; }
+    }
+    const int jstar = block_argmax(av, ai, sh, shi, &rmax);
+    if (!(rmax > 1e-3 * tol)) {  // residual row (numerically) zero: sample another row
+      if (++nsmall >= 3) { conv = 1; break; }
+      if (threadIdx.x == 0) {
+        int nxt = -1;
+        for (int s2 = 1; s2 <= nb; ++s2) {
+          const int cand = (int)(((int64_t)istar + (int64_t)97 * s2) % nb);
+          if (!used[cand]) { nxt = cand; break; }
+        }
+        shi[0] = nxt;
+      }
+      __syncthreads();
+      const int nxt = shi[0];
+      __syncthreads();
+      if (nxt < 0) { conv = 1; break; }
+      istar = nxt;
+      continue;
+    }
+    const double delta = row[jstar];
+    double pu = 0.0, pv = 0.0;
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      double val = 0.0;
+      if (a < mi) {
+        val = entry(a, jstar);
+        for (int l = 0; l < k; ++l) val = fma(-w.Vp[(size_t)l * nb + jstar], w.Up[(size_t)l * nb + a], val);
+      }
+      col[a] = val;
+      w.Up[(size_t)k * nb + a] = val;
+      const double rv = row[a] / delta;
+      w.Vp[(size_t)k * nb + a] = rv;
+      pu = fma(val, val, pu);
+      pv = fma(rv, rv, pv);
+    }
+    const double nu2 = block_sum(pu, sh);
+    const double nv2 = block_sum(pv, sh);
+    ++k;
+    if (sqrt(nu2 * nv2) <= tol) {
+      if (++nsmall >= 2) { conv = 1; break; }
+    } else {
+      nsmall = 0;
+    }
+    av = -1.0;
+    ai = 0x7fffffff;
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+      if (!used[a]) {
+        const double val = fabs(col[a]);
+        if (val > av) { av = val; ai = a; }
+      }
+    }
+    double cm;
+    const int nxt = block_argmax(av, ai, sh, shi, &cm);
+    if (cm < 0.0) { conv = 1; break; }  // every row used: the cross approximation is exact
+    istar = nxt;
+  }
+  *conv_out = conv;
   return k;
 }
 

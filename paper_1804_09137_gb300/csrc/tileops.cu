@@ -45,7 +45,8 @@ __device__ __forceinline__ void operands(const TlrView& v, int alg, int a, int b
 
 __global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items, double eps,
                              const double* __restrict__ d_zeta, double zpow, int Kmax, int trunc_cap,
-                             double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
+                             double* __restrict__ ws, size_t item_elems, long long* __restrict__ st,
+                             double* __restrict__ flops) {
   __shared__ double sh[TLR_THREADS / 32 + 2];
   __shared__ int shi[TLR_THREADS / 32 + 2];
   const int2 it = items[blockIdx.x];
@@ -68,7 +69,9 @@ __global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__
   double* Un = w.Up + (size_t)k0 * nb;
   double* Vn = w.Vp + (size_t)k0 * nb;
   int r;
+  double pf;  // product flops
   if (!X.dense && !Y.dense) {
+    pf = 2.0 * nb * X.k * Y.k * 2.0;
     cta_gemm(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);  // W = V_x^T U_y
     if (Y.k <= X.k) {
       cta_gemm(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
@@ -80,16 +83,19 @@ __global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__
       r = X.k;
     }
   } else if (X.dense) {
+    pf = 2.0 * nb * nb * Y.k;
     cta_gemm(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
     r = Y.k;
   } else {
+    pf = 2.0 * nb * nb * X.k;
     cta_gemm(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
     r = X.k;
   }
   __syncthreads();
-  const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, Ut, Vt, st, tt, sh, shi);
+  if (flops && threadIdx.x == 0) atomicAdd(flops, pf);
+  const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, Ut, Vt, st, tt, sh, shi, flops);
   if (threadIdx.x == 0) v.rank[tt] = kr;
 }
 
@@ -313,6 +319,54 @@ __global__ void k_herk_prep(TlrView v, int k, GemmGen* __restrict__ desc, double
   if (threadIdx.x == 0) desc[blockIdx.x] = g;
 }
 
+struct DenseEntry {
+  const double* A;
+  int nb;
+  __device__ __forceinline__ double operator()(int a, int b) const { return A[(size_t)b * nb + a]; }
+};
+
+// low-rank target hit by a dense x dense product: descriptors that materialise
+// buf = alpha op(X) op(Y) (d1) and then buf += U_t V_t^T (d2)
+__global__ void k_dd_prep(TlrView v, int alg, int k, const int2* __restrict__ items, int cnt, GemmGen* __restrict__ d1,
+                          GemmGen* __restrict__ d2, double* __restrict__ bufs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const int2 it = items[q];
+  const int nb = v.nb;
+  const int64_t tt = dtile_index(it.x, it.y);
+  Opnd X, Y;
+  double alpha;
+  operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
+  double* buf = bufs + (size_t)q * nb * nb;
+  GemmGen g;
+  g.A = X.A; g.tA = X.tA; g.B = Y.A; g.tB = Y.tA; g.C = buf; g.m = nb; g.n = nb; g.k = nb;
+  g.lda = nb; g.ldb = nb; g.ldc = nb; g.alpha = alpha; g.beta = 0.0; g.lower = 0;
+  d1[q] = g;
+  g.A = tileU(v, tt); g.tA = 0; g.B = tileV(v, tt); g.tB = 1; g.k = v.rank[tt]; g.alpha = 1.0; g.beta = 1.0;
+  d2[q] = g;
+}
+
+// compress the materialised target (ACA on stored entries, then eps-truncated SVD)
+__global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const double* __restrict__ bufs, double eps,
+                              const double* __restrict__ d_zeta, double zpow, int aca_max, int Kmax, int trunc_cap,
+                              double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
+  extern __shared__ double dsm[];
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  const int2 it = items[blockIdx.x];
+  const int nb = v.nb;
+  const int64_t tt = dtile_index(it.x, it.y);
+  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
+  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  DenseEntry de{bufs + (size_t)blockIdx.x * nb * nb, nb};
+  int conv = 0;
+  const int k = cta_aca(de, nb, nb, nb, tau * 0.125, aca_max, w, dsm, sh, shi, &conv);
+  if (!conv && !trunc_cap && threadIdx.x == 0) set_status(st, TLR_ERR_RANK_CAP, tt);
+  __syncthreads();
+  const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, tileU(v, tt), tileV(v, tt), st, tt, sh, shi);
+  if (threadIdx.x == 0) v.rank[tt] = kr;
+}
+
 int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
   size_t avail = h->scratch_elems > reserve ? h->scratch_elems - reserve : 0;
   size_t c = per_item ? avail / per_item : 65535;
@@ -356,10 +410,44 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     if (chunk < 1) return TLR_ERR_OOM;
     for (int64_t q0 = 0; q0 < n_lr; q0 += chunk) {
       const int cnt = (int)(n_lr - q0 < chunk ? n_lr - q0 : chunk);
+      if (g_tlr_prof.enabled) tlr_prof_begin(s);
       k_upd_lr_gen<<<cnt, TLR_THREADS, 0, s>>>(v, alg, k, d_lr + q0, eps, d_zeta, zpow, 2 * h->kcap,
-                                               h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
+                                               h->opts.truncate_at_cap, h->scratch, ie, h->d_stat,
+                                               g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
       TLR_LAUNCH_CHECK();
+      if (g_tlr_prof.enabled) tlr_prof_end(s);
     }
+  }
+  return TLR_OK;
+}
+
+int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
+                   const double* d_zeta, double zpow, cudaStream_t s) {
+  if (n_dd <= 0) return TLR_OK;
+  const size_t nn = (size_t)h->nb * h->nb;
+  const size_t ie = tlr_item_elems(h->nb, h->kcap);
+  const size_t gd = (sizeof(GemmGen) + 7) / 8;
+  const int chunk = chunk_of(h, nn + ie + 2 * gd, 16);
+  if (chunk < 1) return TLR_ERR_OOM;
+  const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
+  if (smem > 48 * 1024)
+    if (cudaFuncSetAttribute(k_dd_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return TLR_ERR_CUDA;
+  for (int64_t q0 = 0; q0 < n_dd; q0 += chunk) {
+    const int cnt = (int)(n_dd - q0 < chunk ? n_dd - q0 : chunk);
+    GemmGen* d1 = (GemmGen*)h->scratch;
+    GemmGen* d2 = (GemmGen*)(h->scratch + (size_t)cnt * gd + 1);
+    double* bufs = h->scratch + 2 * (size_t)cnt * gd + 2;
+    double* ws = bufs + (size_t)cnt * nn;
+    k_dd_prep<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dd + q0, cnt, d1, d2, bufs);
+    TLR_LAUNCH_CHECK();
+    int rc = tops_gemm(d1, cnt, h->nb, h->nb, s);
+    if (rc) return rc;
+    rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
+    if (rc) return rc;
+    k_dd_compress<<<cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, 2 * h->kcap, 2 * h->kcap,
+                                                 h->opts.truncate_at_cap, ws, ie, h->d_stat);
+    TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
 }

@@ -25,6 +25,9 @@ struct GemmGen {
 // low-rank targets (recompressed at tau = eps * zeta^zpow, zeta = *d_zeta or 1) and dense targets
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
                 int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s);
+// low-rank targets whose two sources are both dense (materialise, ACA, recompress)
+int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
+                   const double* d_zeta, double zpow, cudaStream_t s);
 // X <- alpha op(T_kdiag) X on listed tiles: low-rank ones on U (which = 0) or V (which = 1), dense ones on A
 // (transposed first and back when dense_right: A <- (alpha op(T) A^T)^T)
 int tops_trop(tlr_ctx* h, const TlrView& v, int kdiag, const int2* d_lr, int n_lr, int which, const int2* d_dn,

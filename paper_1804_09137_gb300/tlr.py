@@ -21,7 +21,7 @@ ERR_NAMES = {1: "not SPD", 2: "rank cap exceeded", 3: "out of memory", 4: "CUDA 
 
 class TlrOpts(C.Structure):
     _fields_ = [("nb", C.c_int), ("eps", C.c_double), ("rank_cap", C.c_int), ("truncate_at_cap", C.c_int),
-                ("order", C.c_int), ("dense_rank", C.c_int)]
+                ("order", C.c_int), ("dense_rank", C.c_int), ("inv_scale", C.c_double)]
 
 
 class TlrTheta(C.Structure):
@@ -40,7 +40,8 @@ _lib = None
 
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
-           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts"]
+           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats",
+           "tlr_profile_read"]
 
 
 def lib():
@@ -67,6 +68,10 @@ def lib():
     L.tlr_get_tile.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     L.tlr_get_perm.argtypes = [vp, vp, vp]
     L.tlr_tile_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.tlr_launch_count.argtypes = [C.POINTER(i64)]
+    L.tlr_inverse_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
+    L.tlr_profile.argtypes = [C.c_int]
+    L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -92,10 +97,10 @@ class Handle:
     """Owns one tlr_handle (tile storage on the current CUDA device)."""
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, nb: int, eps: float = 1e-9, rank_cap: int = 0,
-                 truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0):
+                 truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0, inv_scale: float = 0.0):
         L = lib()
         self._opts = TlrOpts(int(nb), float(eps), int(rank_cap), int(bool(truncate_at_cap)), int(bool(order)),
-                             int(dense_rank))
+                             int(dense_rank), float(inv_scale))
         h = C.c_void_p()
         _check("tlr_create", L.tlr_create(int(x.numel()), _ptr(x), _ptr(y), C.byref(self._opts), _stream(),
                                           C.byref(h)))
@@ -184,6 +189,12 @@ class Handle:
         _check("tlr_tile_counts", lib().tlr_tile_counts(self._h, C.byref(a), C.byref(b)))
         return {"lowrank": a.value, "dense": b.value}
 
+    def inverse_stats(self):
+        kmin, kmax, kmean, nd = C.c_int(), C.c_int(), C.c_double(), C.c_int64()
+        _check("tlr_inverse_stats", lib().tlr_inverse_stats(self._h, C.byref(kmin), C.byref(kmean), C.byref(kmax),
+                                                            C.byref(nd)))
+        return {"kmin": kmin.value, "kmean": kmean.value, "kmax": kmax.value, "dense": nd.value}
+
     def get_perm(self):
         p = torch.zeros(self.n, dtype=torch.int32, device=self.dev)
         _check("tlr_get_perm", lib().tlr_get_perm(self._h, C.c_void_p(p.data_ptr()), _stream()))
@@ -194,3 +205,19 @@ class Handle:
         _check("tlr_rank_stats", lib().tlr_rank_stats(self._h, C.byref(kmin), C.byref(kmean), C.byref(kmax),
                                                       C.byref(nbytes)))
         return {"kmin": kmin.value, "kmean": kmean.value, "kmax": kmax.value, "bytes": nbytes.value}
+
+
+def launch_count() -> int:
+    c = C.c_int64()
+    _check("tlr_launch_count", lib().tlr_launch_count(C.byref(c)))
+    return c.value
+
+
+def profile(enable: bool):
+    _check("tlr_profile", lib().tlr_profile(int(bool(enable))))
+
+
+def profile_read():
+    n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
+    _check("tlr_profile_read", lib().tlr_profile_read(C.byref(n), C.byref(ms), C.byref(fl)))
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value}

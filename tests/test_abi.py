@@ -45,10 +45,10 @@ def test_invalid_arguments_rejected_before_device_work(lib):
     from paper_1804_09137_gb300.tlr import TlrOpts
 
     h = C.c_void_p()
-    opts = TlrOpts(64, 1e-9, 0, 0, 1, 0)
+    opts = TlrOpts(64, 1e-9, 0, 0, 1, 0, 0.0)
     assert lib.tlr_create(0, None, None, C.byref(opts), None, C.byref(h)) == -1
     assert lib.tlr_create(10, None, None, C.byref(opts), None, C.byref(h)) == -2
-    bad = TlrOpts(0, 1e-9, 0, 0, 1, 0)
+    bad = TlrOpts(0, 1e-9, 0, 0, 1, 0, 0.0)
     one = C.c_double(0.0)
     assert lib.tlr_create(10, C.byref(one), C.byref(one), C.byref(bad), None, C.byref(h)) == -4
     assert lib.tlr_destroy(None) == -1
