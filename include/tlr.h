@@ -159,6 +159,13 @@ int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream);
  * Synchronises. */
 int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t* n_dense);
 
+/* While profiling is enabled (tlr_profile), device time of each phase of the
+ * path (generate, compress, chol.*, trtri.*, lauum.*, solves, grad_fused,
+ * update.*) is recorded with CUDA events.  Writes a JSON object
+ * {"phase": [ms, count], ...} into buf (len bytes, host memory).
+ * Synchronises the device. */
+int tlr_profile_phases(char* buf, int64_t len);
+
 /* Total kernel launches issued by the library in this process. */
 int tlr_launch_count(int64_t* count);
 

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -39,6 +40,31 @@ void tlr_prof_begin(cudaStream_t s) {
 
 void tlr_prof_end(cudaStream_t s) {
   if (!g_ev.empty()) cudaEventRecord(g_ev.back().second, s);
+}
+
+namespace {
+struct PhaseRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::vector<PhaseRec> g_ph;
+std::vector<int> g_ph_open;
+}  // namespace
+
+void tlr_phase_begin(const char* name, cudaStream_t s) {
+  if (!g_tlr_prof.enabled) return;
+  PhaseRec r{name, nullptr, nullptr};
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, s);
+  g_ph.push_back(r);
+  g_ph_open.push_back((int)g_ph.size() - 1);
+}
+
+void tlr_phase_end(cudaStream_t s) {
+  if (!g_tlr_prof.enabled || g_ph_open.empty()) return;
+  cudaEventRecord(g_ph[g_ph_open.back()].b, s);
+  g_ph_open.pop_back();
 }
 
 namespace {
@@ -245,8 +271,11 @@ int tlr_matern_generate(tlr_handle h, tlr_theta th, tlr_stream_t stream) {
   h->mp.cnu = 1.0 / (pow(2.0, th.nu - 1.0) * tgamma(th.nu));
   h->mp.psi = host_digamma(th.nu);
   TLR_CUDA_TRY(cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s));
-  TRY(tlr_build_table(h, s));
-  TRY(tlr_gen_diag(h, s));
+  {
+    PhaseScope ps("generate", s);
+    TRY(tlr_build_table(h, s));
+    TRY(tlr_gen_diag(h, s));
+  }
   if (h->dense) {
     TRY(tlr_plan(h, s));  // every off-diagonal tile dense, generated by the plan
     h->state = 2;
@@ -264,8 +293,14 @@ int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream) {
   h->last_stream = s;
   if (h->dense) return TLR_OK;
   h->opts.eps = eps;
-  if (h->ntiles > 0) TRY(tlr_compress_tiles(h, eps, s));
-  TRY(tlr_plan(h, s));
+  {
+    PhaseScope ps("compress", s);
+    if (h->ntiles > 0) TRY(tlr_compress_tiles(h, eps, s));
+  }
+  {
+    PhaseScope ps("plan", s);
+    TRY(tlr_plan(h, s));
+  }
   h->state = 2;
   return TLR_OK;
 }
@@ -340,6 +375,7 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
   hx[m] = bx[0]; hy[m] = by[0]; hx[m + 1] = bx[1]; hy[m + 1] = by[1];
   if (set_table_range(h, bbox_diag(hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
   double* a = h->d_vec;
+  PhaseScope ps("predict", s);
   TRY(tlr_permute_in(h, z_obs, a, s));
   TRY(tlr_fwd_solve(h, a, s));
   TRY(tlr_bwd_solve(h, a, s));
@@ -458,6 +494,30 @@ int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t
   return TLR_OK;
 }
 
+int tlr_profile_phases(char* buf, int64_t len) {
+  if (!buf || len <= 0) return -1;
+  TLR_CUDA_TRY(cudaDeviceSynchronize());
+  std::vector<std::pair<std::string, std::pair<double, int>>> acc;
+  for (auto& r : g_ph) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    bool found = false;
+    for (auto& e : acc)
+      if (e.first == r.name) { e.second.first += t; e.second.second += 1; found = true; }
+    if (!found) acc.push_back({r.name, {t, 1}});
+  }
+  std::string out = "{";
+  for (size_t i = 0; i < acc.size(); ++i) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "%s\"%s\": [%.3f, %d]", i ? ", " : "", acc[i].first.c_str(), acc[i].second.first,
+             acc[i].second.second);
+    out += tmp;
+  }
+  out += "}";
+  snprintf(buf, (size_t)len, "%s", out.c_str());
+  return TLR_OK;
+}
+
 int tlr_launch_count(int64_t* count) {
   if (!count) return -1;
   *count = g_tlr_launches;
@@ -472,6 +532,9 @@ int tlr_profile(int enable) {
   TLR_CUDA_TRY(cudaMemset(g_tlr_prof.d_flops, 0, sizeof(double)));
   for (auto& e : g_ev) g_ev_free.push_back(e);
   g_ev.clear();
+  for (auto& r : g_ph) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  g_ph.clear();
+  g_ph_open.clear();
   g_tlr_prof.enabled = enable ? 1 : 0;
   return TLR_OK;
 }
@@ -585,8 +648,13 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
 }
 
 namespace {
-__global__ void k_grad_finish(const double* __restrict__ ll3, double* __restrict__ d_ll) {
-  if (threadIdx.x == 0) d_ll[0] = ll3[0];
+// l out; dl/dsigma2 = (q - n) / (2 sigma2) since dSigma/dsigma2 = Sigma / sigma2
+__global__ void k_grad_finish(const double* __restrict__ ll3, double* __restrict__ d_ll, double* __restrict__ g3,
+                              int64_t n, double sigma2) {
+  if (threadIdx.x == 0) {
+    d_ll[0] = ll3[0];
+    g3[0] = (ll3[2] - (double)n) / (2.0 * sigma2);
+  }
 }
 }  // namespace
 
@@ -601,14 +669,20 @@ extern "C" int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, doub
   double* w = h->d_vec;              // L^{-1} z
   double* a = h->d_vec + h->npad;    // Sigma^{-1} z
   double* ll3 = h->d_red + 2 * h->nt;  // (l, log|Sigma|, quad)
-  TRY(tlr_permute_in(h, z, w, s));
-  TRY(tlr_fwd_solve(h, w, s));
-  TRY(tlr_reduce_loglik(h, w, ll3, s));
-  TLR_CUDA_TRY(cudaMemcpyAsync(a, w, h->npad * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  TRY(tlr_bwd_solve(h, a, s));
+  {
+    PhaseScope ps("solves", s);
+    TRY(tlr_permute_in(h, z, w, s));
+    TRY(tlr_fwd_solve(h, w, s));
+    TRY(tlr_reduce_loglik(h, w, ll3, s));
+    TLR_CUDA_TRY(cudaMemcpyAsync(a, w, h->npad * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(tlr_bwd_solve(h, a, s));
+  }
   TRY(tlr_inverse(h, s));
-  TRY(tlr_grad_fused(h, a, d_grad3, s));
-  k_grad_finish<<<1, 32, 0, s>>>(ll3, d_ll);
+  {
+    PhaseScope ps("grad_fused", s);
+    TRY(tlr_grad_fused(h, a, d_grad3, s));
+  }
+  k_grad_finish<<<1, 32, 0, s>>>(ll3, d_ll, d_grad3, h->n, h->mp.sigma2);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }

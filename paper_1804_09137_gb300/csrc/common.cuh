@@ -245,6 +245,14 @@ struct TlrProfile {
 extern TlrProfile g_tlr_prof;
 void tlr_prof_begin(cudaStream_t s);
 void tlr_prof_end(cudaStream_t s);
+// per-phase device time (events around each phase when profiling is enabled)
+void tlr_phase_begin(const char* name, cudaStream_t s);
+void tlr_phase_end(cudaStream_t s);
+struct PhaseScope {
+  cudaStream_t s;
+  PhaseScope(const char* name, cudaStream_t st) : s(st) { tlr_phase_begin(name, s); }
+  ~PhaseScope() { tlr_phase_end(s); }
+};
 
 // ------------------------------------------------------------ host helpers
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);

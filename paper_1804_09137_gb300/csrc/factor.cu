@@ -303,12 +303,25 @@ static int launch_updates(tlr_ctx* h, int k, cudaStream_t s) {
 int tlr_factor(tlr_ctx* h, cudaStream_t s) {
   const int nt = h->nt, nb = h->nb;
   for (int k = 0; k < nt; ++k) {
-    int rc = tlr_potrf_tile(h, h->D + (size_t)k * nb * nb, nb, nb, (int64_t)k * nb, s);
+    int rc;
+    {
+      PhaseScope ps("chol.potrf", s);
+      rc = tlr_potrf_tile(h, h->D + (size_t)k * nb * nb, nb, nb, (int64_t)k * nb, s);
+    }
     if (rc) return rc;
     if (k == nt - 1) break;
-    if ((rc = launch_trsm(h, k, s))) return rc;
-    if ((rc = launch_syrk(h, k, s))) return rc;
-    if ((rc = launch_updates(h, k, s))) return rc;
+    {
+      PhaseScope ps("chol.trsm", s);
+      if ((rc = launch_trsm(h, k, s))) return rc;
+    }
+    {
+      PhaseScope ps("chol.syrk", s);
+      if ((rc = launch_syrk(h, k, s))) return rc;
+    }
+    {
+      PhaseScope ps("chol.update", s);
+      if ((rc = launch_updates(h, k, s))) return rc;
+    }
   }
   return TLR_OK;
 }

@@ -1,8 +1,9 @@
 // Gradient of eq. 1 in theta (not in the paper), from a = Sigma^{-1} z and the
 // TLR inverse Z:
 //   dl/dtheta_p = 1/2 a^T dSigma_p a - 1/2 tr(Z dSigma_p)
-//               = sum_{a > b} (a_a a_b - Z_ab) dC_p(r_ab) + 1/2 sum_a (a_a^2 - Z_aa) dC_p(0)
-// with dC_sigma2 = C / sigma2 (1 at r = 0) and dC_beta(0) = dC_nu(0) = 0.
+//               = sum_{a > b} (a_a a_b - Z_ab) dC_p(r_ab)      for p = beta, nu
+// (dC_beta(0) = dC_nu(0) = 0).  For sigma2, dSigma = Sigma / sigma2 exactly, so
+// dl/dsigma2 = (q - n) / (2 sigma2) with q = z^T Sigma^{-1} z (no trace needed).
 // One pass over the strictly lower triangle regenerates the three derivative
 // entries from the Matérn table (dSigma is never stored) and reads Z's tile:
 // dense tiles directly, low-rank tiles as U V^T formed 64 x 64 at a time in
@@ -54,7 +55,7 @@ __global__ void k_grad_fused(TlrView z, const double* __restrict__ tab, const Ma
   const int J = (int)(pair - (int64_t)I * (I + 1) / 2);
   const int bi = blockIdx.x % mb, bj = blockIdx.x / mb;
   const int r0 = bi * 64, c0 = bj * 64;
-  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  double g1 = 0.0, g2 = 0.0;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool skip = (I == J && r0 + 63 < c0) || ((int64_t)I * nb + r0 >= n) || ((int64_t)J * nb + c0 >= n);
   if (!skip) {
@@ -84,35 +85,26 @@ __global__ void k_grad_fused(TlrView z, const double* __restrict__ tab, const Ma
         if (b >= nb || pb >= n) continue;
         if (I == J && b > a) continue;
         const double zab = Zd ? Zd[(size_t)b * nb + a] : acc[i][j];
-        if (I == J && a == b) {  // diagonal: only the sigma2 derivative is nonzero at r = 0
-          g0 += 0.5 * (wa * wa - zab) * mp.sigma2;  // scaled back by 1 / sigma2 below
-          continue;
-        }
+        if (I == J && a == b) continue;  // dC_beta(0) = dC_nu(0) = 0
         const double dx = xa - x[pb], dy = ya - y[pb];
         const double r = sqrt(dx * dx + dy * dy);
         const double w = wa * al[pb] - zab;
         if (r > 0.0) {
           double t;
           const int jt = tab_locate(r, mp.e_lo, &t);
-          if (jt >= 0 && jt < TAB_NINT) {
-            g0 = fma(w, tab_poly(tab + (size_t)jt * TAB_NC, t), g0);
+          if (jt >= 0 && jt < TAB_NINT) {  // below the table the derivatives vanish
             g1 = fma(w, tab_poly(tab + (size_t)(TAB_NINT + jt) * TAB_NC, t), g1);
             g2 = fma(w, tab_poly(tab + (size_t)(2 * TAB_NINT + jt) * TAB_NC, t), g2);
-          } else if (jt < 0) {
-            g0 += w * mp.sigma2;  // r below the table: C -> sigma2, derivatives -> 0
           }
-        } else {
-          g0 += w * mp.sigma2;    // coincident points
         }
       }
     }
   }
-  g0 = block_sum(g0, sh);
   g1 = block_sum(g1, sh);
   g2 = block_sum(g2, sh);
   if (threadIdx.x == 0) {
     const size_t id = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-    part[3 * id] = g0 / mp.sigma2;  // table function 0 is C; dC/dsigma2 = C / sigma2
+    part[3 * id] = 0.0;
     part[3 * id + 1] = g1;
     part[3 * id + 2] = g2;
   }

@@ -16,6 +16,7 @@
 // diagonal, so that the truncation is relative to the size of M and Z as eps
 // is to Sigma.  Z keeps the factor's dense tiles; a dense x dense product that
 // lands on a low-rank tile is formed by GEMM and recompressed.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -109,7 +110,16 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   h->kindz = (char*)calloc(std::max<int64_t>(T, 1), 1);
   if (!h->kindz) return TLR_ERR_OOM;
   char* K = h->kindz;
-  for (int64_t t = 0; t < T; ++t) K[t] = h->kind ? h->kind[t] : 0;
+  // Z keeps the factor's dense tiles; a low-rank factor tile whose rank exceeds
+  // zdense_rank is also made dense in Z (inverse ranks run several times higher)
+  std::vector<int> rk(std::max<int64_t>(T, 1), 0);
+  if (T > 0) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(rk.data(), h->rank, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  int zr = h->dense_rank;
+  if (const char* e = getenv("TLR_ZDENSE_RANK")) zr = atoi(e);
+  for (int64_t t = 0; t < T; ++t) K[t] = (h->kind ? h->kind[t] : 0) || (zr > 0 && rk[t] > zr);
   auto kd = [&](int p, int q) -> char& { return K[tile_index(p, q)]; };
   // No fill closure: the inverse of a banded triangular matrix is full, so the
   // closure would make every tile dense although the far tiles of L^{-1} and
@@ -164,6 +174,15 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     }
   }
   off[(size_t)nt * ZPH] = (int64_t)L.size();
+  if (getenv("TLR_VERBOSE")) {
+    int64_t cnt[ZPH] = {0};
+    for (int k = 0; k < nt; ++k)
+      for (int ph = 0; ph < ZPH; ++ph) cnt[ph] += off[(size_t)k * ZPH + ph + 1] - off[(size_t)k * ZPH + ph];
+    fprintf(stderr, "tlr inverse plan: dense %d; items T1 %lld/%lld T2 %lld/%lld/dd %lld T3 %lld/%lld L2 %lld/%lld/dd %lld L3 %lld/%lld\n",
+            nd, (long long)cnt[ZP_T1_LR], (long long)cnt[ZP_T1_D], (long long)cnt[ZP_T2_LR], (long long)cnt[ZP_T2_D],
+            (long long)cnt[ZP_T2_DD], (long long)cnt[ZP_T3_LR], (long long)cnt[ZP_T3_D], (long long)cnt[ZP_L2_LR],
+            (long long)cnt[ZP_L2_D], (long long)cnt[ZP_L2_DD], (long long)cnt[ZP_L3_LR], (long long)cnt[ZP_L3_D]);
+  }
   const int64_t len = std::max<int64_t>((int64_t)L.size(), 1);
   if (len > h->zlist_cap) {
     if (h->d_zlist) cudaFree(h->d_zlist);
@@ -221,6 +240,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   const size_t nn = (size_t)nb * nb;
   // zeta lives in the last reduction slot
   double* d_zeta = h->d_red + h->red_len - 1;
+  PhaseScope ps_all("inverse", s);
   k_zeta<<<1, TLR_THREADS, 0, s>>>(h->D, nb, nt, d_zeta);
   TLR_LAUNCH_CHECK();
   k_copy<<<1024, 256, 0, s>>>(h->D, h->Dz, (int64_t)nt * nn);
@@ -247,10 +267,15 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
     auto L = [&](int ph) { return h->d_zlist + off[ph]; };
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
-    ZTRY(tops_trop(h, z, k, L(ZP_T1_LR), N(ZP_T1_LR), 1, L(ZP_T1_D), N(ZP_T1_D), 1, TOP_SOLVE_T, -1.0, s));
-    ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s));
-    ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), N(ZP_T2_DD), eps, d_zeta, 0.5, s));
-    ZTRY(tops_trop(h, z, k, L(ZP_T3_LR), N(ZP_T3_LR), 0, L(ZP_T3_D), N(ZP_T3_D), 0, TOP_SOLVE, 1.0, s));
+    { PhaseScope ps("trtri.col", s);
+      ZTRY(tops_trop(h, z, k, L(ZP_T1_LR), N(ZP_T1_LR), 1, L(ZP_T1_D), N(ZP_T1_D), 1, TOP_SOLVE_T, -1.0, s)); }
+    { PhaseScope ps("trtri.update", s);
+      ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s)); }
+    { PhaseScope ps("trtri.update_dd", s);
+      ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), N(ZP_T2_DD), eps, d_zeta, 0.5, s)); }
+    { PhaseScope ps("trtri.row", s);
+      ZTRY(tops_trop(h, z, k, L(ZP_T3_LR), N(ZP_T3_LR), 0, L(ZP_T3_D), N(ZP_T3_D), 0, TOP_SOLVE, 1.0, s)); }
+    PhaseScope ps_d("trtri.diag", s);
     k_eye<<<256, 256, 0, s>>>(X, nb);
     TLR_LAUNCH_CHECK();
     ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, X, nb, TOP_SOLVE, 1.0, s));
@@ -263,10 +288,14 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
     auto L = [&](int ph) { return h->d_zlist + off[ph]; };
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
-    ZTRY(tops_herk_row(h, z, k, s));
-    ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s));
-    ZTRY(tops_update_dd(h, z, ALG_LAUUM, k, L(ZP_L2_DD), N(ZP_L2_DD), eps, d_zeta, 1.0, s));
-    ZTRY(tops_trop(h, z, k, L(ZP_L3_LR), N(ZP_L3_LR), 0, L(ZP_L3_D), N(ZP_L3_D), 0, TOP_MUL_T, 1.0, s));
+    { PhaseScope ps("lauum.herk", s); ZTRY(tops_herk_row(h, z, k, s)); }
+    { PhaseScope ps("lauum.update", s);
+      ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s)); }
+    { PhaseScope ps("lauum.update_dd", s);
+      ZTRY(tops_update_dd(h, z, ALG_LAUUM, k, L(ZP_L2_DD), N(ZP_L2_DD), eps, d_zeta, 1.0, s)); }
+    { PhaseScope ps("lauum.row", s);
+      ZTRY(tops_trop(h, z, k, L(ZP_L3_LR), N(ZP_L3_LR), 0, L(ZP_L3_D), N(ZP_L3_D), 0, TOP_MUL_T, 1.0, s)); }
+    PhaseScope ps_d("lauum.diag", s);
     // D_k <- D_k^T D_k via the workspace
     GemmGen g;
     g.A = h->Dz + (size_t)k * nn; g.B = g.A; g.C = X; g.m = nb; g.n = nb; g.k = nb;

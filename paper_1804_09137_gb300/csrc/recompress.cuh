@@ -174,48 +174,103 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     w.M[(size_t)b * Ke + a] = s;
   }
   __syncthreads();
-  __shared__ double jfl;
-  if (threadIdx.x == 0) jfl = 0.0;
-  __syncthreads();
-  cta_jacobi(w.M, w.Y, Ke, shi, flops ? &jfl : nullptr);
-  // singular values = column norms of M
+  // column-pivoted Householder QR of M, stopped at the first step whose trailing
+  // block has Frobenius norm <= eps (then ||M - Q_k R_k P^T||_2 <= eps)
+  double* nrm = w.s;               // partial column norms^2 (rows >= step)
+  double* tm = w.Y;                // reflector taus of M
+  int* perm = (int*)(w.Y + Ke);    // column permutation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = warp; l < Ke; l += nw) {
-    double s = 0.0;
-    for (int r = lane; r < Ke; r += 32) s = fma(w.M[(size_t)l * Ke + r], w.M[(size_t)l * Ke + r], s);
-    s = warp_sum(s);
-    if (lane == 0) w.s[l] = sqrt(s);
+  for (int j = warp; j < Ke; j += nw) {
+    double q = 0.0;
+    for (int r = lane; r < Ke; r += 32) q = fma(w.M[(size_t)j * Ke + r], w.M[(size_t)j * Ke + r], q);
+    q = warp_sum(q);
+    if (lane == 0) { nrm[j] = q; perm[j] = j; }
   }
   __syncthreads();
-  // rank of each kept value in descending order; count kept
-  int cnt_local = 0;
-  for (int l = threadIdx.x; l < Ke; l += blockDim.x) cnt_local += (w.s[l] > eps);
-  const int kept = (int)block_sum((double)cnt_local, sh);
-  int k = kept;
+  const double eps2 = eps * eps;
+  int k = 0;
+  double fl = 2.0 * Ke * Ke * (K - 2.0 * Ke / 3.0) + 2.0 * Ke * Ke;
+  for (int c = 0; c < Ke; ++c) {
+    double part = 0.0, av = -1.0;
+    int ai = 0x7fffffff;
+    for (int j = c + threadIdx.x; j < Ke; j += blockDim.x) {
+      part += nrm[j];
+      if (nrm[j] > av) { av = nrm[j]; ai = j; }
+    }
+    const double trail = block_sum(part, sh);
+    if (trail <= eps2) break;
+    const int piv = block_argmax(av, ai, sh, shi, nullptr);
+    if (piv != c) {  // swap columns c and piv
+      for (int r = threadIdx.x; r < Ke; r += blockDim.x) {
+        const double t = w.M[(size_t)c * Ke + r];
+        w.M[(size_t)c * Ke + r] = w.M[(size_t)piv * Ke + r];
+        w.M[(size_t)piv * Ke + r] = t;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double tn = nrm[c]; nrm[c] = nrm[piv]; nrm[piv] = tn;
+        const int tp = perm[c]; perm[c] = perm[piv]; perm[piv] = tp;
+      }
+    }
+    __syncthreads();
+    // reflector of column c (rows c..Ke-1); sigma = sum of squares below the diagonal
+    double* a = w.M + (size_t)c * Ke;
+    const double alpha = a[c];
+    double ps = 0.0;
+    for (int r = c + 1 + threadIdx.x; r < Ke; r += blockDim.x) ps = fma(a[r], a[r], ps);
+    const double sig = block_sum(ps, sh);
+    double beta = alpha, tc = 0.0, scal = 1.0;
+    if (sig > 0.0) {
+      beta = -copysign(sqrt(alpha * alpha + sig), alpha);
+      tc = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    if (sig > 0.0)
+      for (int r = c + 1 + threadIdx.x; r < Ke; r += blockDim.x) a[r] *= scal;
+    __syncthreads();
+    if (threadIdx.x == 0) { a[c] = beta; tm[c] = tc; }
+    // trailing columns: apply the reflector, recompute the partial norms (rows > c) exactly
+    for (int j = c + 1 + warp; j < Ke; j += nw) {
+      double* b = w.M + (size_t)j * Ke;
+      double d = (lane == 0) ? b[c] : 0.0;
+      if (tc != 0.0) {
+        for (int r = c + 1 + lane; r < Ke; r += 32) d = fma(a[r], b[r], d);
+        d = warp_sum(d) * tc;
+        if (lane == 0) b[c] -= d;
+      }
+      double q = 0.0;
+      for (int r = c + 1 + lane; r < Ke; r += 32) {
+        const double v = (tc != 0.0) ? fma(-d, a[r], b[r]) : b[r];
+        b[r] = v;
+        q = fma(v, v, q);
+      }
+      q = warp_sum(q);
+      if (lane == 0) nrm[j] = q;
+    }
+    fl += 6.0 * (Ke - c) * (Ke - c);
+    k = c + 1;
+    __syncthreads();
+  }
   if (k > kcap) {
     if (!trunc_cap) set_status(st, TLR_ERR_RANK_CAP, info);
     k = kcap;
   }
-  // output columns: position of l among kept values sorted by (s desc, l asc)
+  // U block = Q_M[:, :k] (Ke x k): apply the k reflectors of M to [I_k; 0]
   for (int j = 0; j < k; ++j)
-    for (int r = threadIdx.x; r < nb; r += blockDim.x) { Uo[(size_t)j * nb + r] = 0.0; Vo[(size_t)j * nb + r] = 0.0; }
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) {
+      Uo[(size_t)j * nb + r] = (r == j) ? 1.0 : 0.0;
+      Vo[(size_t)j * nb + r] = 0.0;
+    }
   __syncthreads();
-  for (int l = threadIdx.x; l < Ke; l += blockDim.x) {
-    const double sl = w.s[l];
-    if (!(sl > eps)) continue;
-    int pos = 0;
-    for (int l2 = 0; l2 < Ke; ++l2) {
-      const double s2 = w.s[l2];
-      pos += (s2 > sl) || (s2 == sl && l2 < l);
-    }
-    if (pos < k) {
-      for (int r = 0; r < Ke; ++r) {
-        Uo[(size_t)pos * nb + r] = w.M[(size_t)l * Ke + r];
-        Vo[(size_t)pos * nb + r] = w.Y[(size_t)l * Ke + r];
-      }
-    }
+  cta_apply_q(w.M, Ke, Ke, k, tm, Uo, nb, k);
+  // V block = P R_k^T (Ke x k): row perm[jj] gets R[:k, jj]
+  for (int e = threadIdx.x; e < Ke * k; e += blockDim.x) {
+    const int jj = e % Ke, c = e / Ke;
+    Vo[(size_t)c * nb + perm[jj]] = (jj >= c) ? w.M[(size_t)jj * Ke + c] : 0.0;
   }
   __syncthreads();
+  if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
   cta_apply_q(w.Up, nb, nb, Ke, w.tu, Uo, nb, k);
   cta_apply_q(w.Vp, nb, nb, Ke, w.tv, Vo, nb, k);
   __syncthreads();
@@ -223,10 +278,10 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     // Householder QR of two nb x K factors, triangular core product, column norms,
     // applying both Q to k columns, plus the Jacobi sweeps as executed
     const double m = nb, KK = K, Kq = Ke;
+    (void)KK;
     const double qr = 2.0 * (2.0 * m * KK * Kq - (KK + m) * Kq * Kq + 2.0 * Kq * Kq * Kq / 3.0);
-    const double core = 2.0 * Kq * Kq * (KK - 2.0 * Kq / 3.0);
     const double apply = 2.0 * k * (4.0 * m * Kq - 2.0 * Kq * Kq);
-    atomicAdd(flops, qr + core + 2.0 * Kq * Kq + apply + jfl);
+    atomicAdd(flops, qr + apply);
   }
   return k;
 }

@@ -99,45 +99,63 @@ __global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__
   if (threadIdx.x == 0) v.rank[tt] = kr;
 }
 
-__global__ void k_upd_d_gen(TlrView v, int alg, int k, const int2* __restrict__ items, GemmGen* __restrict__ desc,
-                            double* __restrict__ ws, size_t ws_elems) {
-  const int2 it = items[blockIdx.x];
+// dense target C += alpha op(X) op(Y) as three batched GEMM stages per item:
+//   stage 0: W = V_x^T U_y (LR x LR) or T = op(X) U_y (dense X) or T = op(Y)^T V_x (dense Y)
+//   stage 1: T = U_x W or T = V_y W^T (LR x LR only)
+//   stage 2: C += alpha T V_y^T, alpha U_x T^T or alpha op(X) op(Y)
+// an unused stage has k = 0 and beta = 1 (no-op)
+__global__ void k_upd_d_desc(TlrView v, int alg, int k, const int2* __restrict__ items, int cnt,
+                             GemmGen* __restrict__ d0, GemmGen* __restrict__ d1, GemmGen* __restrict__ d2,
+                             double* __restrict__ ws, size_t ws_elems) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const int2 it = items[q];
   const int nb = v.nb;
   const int64_t tt = dtile_index(it.x, it.y);
   Opnd X, Y;
   double alpha;
   operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
-  double* W = ws + (size_t)blockIdx.x * ws_elems;
+  double* W = ws + (size_t)q * ws_elems;
   double* T = W + (size_t)v.kcap * v.kcap;
-  GemmGen g;
-  g.C = tileA(v, tt); g.ldc = nb; g.m = nb; g.n = nb; g.alpha = alpha; g.beta = 1.0; g.lower = 0;
-  g.lda = nb; g.ldb = nb;
+  GemmGen nop;
+  nop.A = nop.B = nullptr; nop.C = T; nop.m = nop.n = 0; nop.k = 0; nop.lda = nop.ldb = nop.ldc = nb;
+  nop.tA = nop.tB = 0; nop.alpha = 0.0; nop.beta = 1.0; nop.lower = 0;
+  GemmGen g0 = nop, g1 = nop, g2 = nop;
+  g2.C = tileA(v, tt); g2.ldc = nb; g2.m = nb; g2.n = nb; g2.alpha = alpha; g2.beta = 1.0;
+  g2.lda = nb; g2.ldb = nb;
+  auto mk = [&](GemmGen& g, int m, int n, int kk, const double* A, int lda, int tA, const double* B, int ldb, int tB,
+                double* C, int ldc) {
+    g.m = m; g.n = n; g.k = kk; g.A = A; g.lda = lda; g.tA = tA; g.B = B; g.ldb = ldb; g.tB = tB; g.C = C;
+    g.ldc = ldc; g.alpha = 1.0; g.beta = 0.0; g.lower = 0;
+  };
   if (X.k == 0 || Y.k == 0) {
-    g.k = 0; g.A = g.B = nullptr; g.tA = g.tB = 0;
+    g2.k = 0;
   } else if (X.dense && Y.dense) {
-    g.A = X.A; g.tA = X.tA; g.B = Y.A; g.tB = Y.tA; g.k = nb;
-  } else if (X.dense) {  // (op(X) U_y) V_y^T
-    cta_gemm(nb, Y.k, nb, 1.0, X.A, nb, X.tA, Y.U, nb, 0, 0.0, T, nb);
-    g.A = T; g.tA = 0; g.B = Y.V; g.tB = 1; g.k = Y.k;
-  } else if (Y.dense) {  // U_x (op(Y)^T V_x)^T
-    cta_gemm(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, T, nb);
-    g.A = X.U; g.tA = 0; g.B = T; g.tB = 1; g.k = X.k;
+    g2.A = X.A; g2.tA = X.tA; g2.B = Y.A; g2.tB = Y.tA; g2.k = nb;
+  } else if (X.dense) {
+    mk(g0, nb, Y.k, nb, X.A, nb, X.tA, Y.U, nb, 0, T, nb);
+    g2.A = T; g2.tA = 0; g2.B = Y.V; g2.tB = 1; g2.k = Y.k;
+  } else if (Y.dense) {
+    mk(g0, nb, X.k, nb, Y.A, nb, !Y.tA, X.V, nb, 0, T, nb);
+    g2.A = X.U; g2.tA = 0; g2.B = T; g2.tB = 1; g2.k = X.k;
   } else {
-    cta_gemm(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, W, X.k);
+    mk(g0, X.k, Y.k, nb, X.V, nb, 1, Y.U, nb, 0, W, X.k);
     if (Y.k <= X.k) {
-      cta_gemm(nb, Y.k, X.k, 1.0, X.U, nb, 0, W, X.k, 0, 0.0, T, nb);
-      g.A = T; g.tA = 0; g.B = Y.V; g.tB = 1; g.k = Y.k;
+      mk(g1, nb, Y.k, X.k, X.U, nb, 0, W, X.k, 0, T, nb);
+      g2.A = T; g2.tA = 0; g2.B = Y.V; g2.tB = 1; g2.k = Y.k;
     } else {
-      cta_gemm(nb, X.k, Y.k, 1.0, Y.V, nb, 0, W, X.k, 1, 0.0, T, nb);
-      g.A = X.U; g.tA = 0; g.B = T; g.tB = 1; g.k = X.k;
+      mk(g1, nb, X.k, Y.k, Y.V, nb, 0, W, X.k, 1, T, nb);
+      g2.A = X.U; g2.tA = 0; g2.B = T; g2.tB = 1; g2.k = X.k;
     }
   }
-  if (threadIdx.x == 0) desc[blockIdx.x] = g;
+  d0[q] = g0;
+  d1[q] = g1;
+  d2[q] = g2;
 }
 
 __global__ void k_gemm_gen(const GemmGen* __restrict__ desc) {
   const GemmGen g = desc[blockIdx.y];
-  if (g.k <= 0 && g.beta == 1.0) return;
+  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0) return;
   cta_gemm_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
                   gridDim.x, g.lower);
 }
@@ -390,21 +408,29 @@ int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s) {
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
                 int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s) {
   if (n_dn > 0) {
+    PhaseScope ps("update.dense_target", s);
     const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
-    int chunk = chunk_of(h, per + (sizeof(GemmGen) + 7) / 8, 8);
+    const size_t gd = (sizeof(GemmGen) + 7) / 8;
+    int chunk = chunk_of(h, per + 3 * gd, 16);
     if (chunk < 1) return TLR_ERR_OOM;
     for (int64_t q0 = 0; q0 < n_dn; q0 += chunk) {
       const int cnt = (int)(n_dn - q0 < chunk ? n_dn - q0 : chunk);
-      const size_t desc_elems = ((size_t)cnt * sizeof(GemmGen) + 7) / 8 + 1;
-      GemmGen* desc = (GemmGen*)h->scratch;
-      double* ws = h->scratch + desc_elems;
-      k_upd_d_gen<<<cnt, 256, 0, s>>>(v, alg, k, d_dn + q0, desc, ws, per);
+      GemmGen* d0 = (GemmGen*)h->scratch;
+      GemmGen* d1 = (GemmGen*)(h->scratch + (size_t)cnt * gd + 1);
+      GemmGen* d2 = (GemmGen*)(h->scratch + 2 * ((size_t)cnt * gd + 1));
+      double* ws = h->scratch + 3 * ((size_t)cnt * gd + 1);
+      k_upd_d_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dn + q0, cnt, d0, d1, d2, ws, per);
       TLR_LAUNCH_CHECK();
-      int rc = tops_gemm(desc, cnt, h->nb, h->nb, s);
+      int rc = tops_gemm(d0, cnt, h->nb, h->kcap > h->nb ? h->nb : h->kcap, s);
+      if (rc) return rc;
+      rc = tops_gemm(d1, cnt, h->nb, h->kcap > h->nb ? h->nb : h->kcap, s);
+      if (rc) return rc;
+      rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
       if (rc) return rc;
     }
   }
   if (n_lr > 0) {
+    PhaseScope ps("update.lowrank_target", s);
     const size_t ie = tlr_item_elems(h->nb, h->kcap);
     const int chunk = chunk_of(h, ie, 0);
     if (chunk < 1) return TLR_ERR_OOM;

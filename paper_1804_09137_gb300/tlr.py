@@ -40,7 +40,7 @@ _lib = None
 
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
-           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats",
+           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases",
            "tlr_profile_read"]
 
 
@@ -71,6 +71,7 @@ def lib():
     L.tlr_launch_count.argtypes = [C.POINTER(i64)]
     L.tlr_inverse_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
     L.tlr_profile.argtypes = [C.c_int]
+    L.tlr_profile_phases.argtypes = [C.c_char_p, i64]
     L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
@@ -221,3 +222,11 @@ def profile_read():
     n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
     _check("tlr_profile_read", lib().tlr_profile_read(C.byref(n), C.byref(ms), C.byref(fl)))
     return {"launches": n.value, "ms": ms.value, "flops": fl.value}
+
+
+def profile_phases() -> dict:
+    import json
+
+    buf = C.create_string_buffer(1 << 16)
+    _check("tlr_profile_phases", lib().tlr_profile_phases(buf, len(buf)))
+    return json.loads(buf.value.decode())
