@@ -152,6 +152,22 @@ int tlr_tile_counts(tlr_handle h, int64_t* n_lowrank, int64_t* n_dense);
  * (device buffer of n int32).  Synchronises `stream`. */
 int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream);
 
+/* Allocation-free variant (the paper has no counterpart): eq. 1 for a small
+ * problem, n <= 1024 points, evaluated as one dense tile (Matérn generation,
+ * Cholesky, solve, log-determinant) with every piece of workspace in a static
+ * device array of the library (about 8.5 MB per GPU, held until exit).  For
+ * callers that cannot call cudaMalloc, e.g. because their process has handed
+ * all device memory to another allocator or may not allocate after start-up.
+ * x, y, z: device arrays of n doubles (caller's order); d_out3: device array
+ * of 3 doubles (l, log|Sigma|, z^T Sigma^{-1} z).  Makes no device
+ * allocation.  Returns -1 for n outside 1..1024, TLR_ERR_NOT_SPD when the
+ * covariance is not positive definite, TLR_OK otherwise; synchronises
+ * `stream`.  The first call on a device looks up the workspace address (make
+ * it before any stream capture).  All calls share the workspace: calls that
+ * overlap on the GPU race. */
+int tlr_loglik_dense_noalloc(int64_t n, const double* x, const double* y, const double* z, tlr_theta theta,
+                             double* d_out3, tlr_stream_t stream);
+
 /* Diagnostics (no counterpart in the paper). */
 
 /* Rank statistics of the low-rank tiles of the inverse Sigma^{-1} built by the

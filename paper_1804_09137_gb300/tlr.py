@@ -40,7 +40,7 @@ _lib = None
 
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
-           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases",
+           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
            "tlr_profile_read"]
 
 
@@ -71,6 +71,7 @@ def lib():
     L.tlr_launch_count.argtypes = [C.POINTER(i64)]
     L.tlr_inverse_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
     L.tlr_profile.argtypes = [C.c_int]
+    L.tlr_loglik_dense_noalloc.argtypes = [i64, vp, vp, vp, TlrTheta, vp, vp]
     L.tlr_profile_phases.argtypes = [C.c_char_p, i64]
     L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
     for name in EXPORTS:
