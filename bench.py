@@ -117,6 +117,23 @@ def dist():
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Largest value over the ranks (the slowest replica sets the job time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as tdist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ms_per_step_max: float, world: int) -> float:
+    """Whole-job evaluations per second: every replica completes one evaluation per step."""
+    return world / (ms_per_step_max / 1e3)
+
+
 def cpu_oracle_sample(side):
     """Seconds of one dense CPU-oracle likelihood+gradient evaluation at n = side^2."""
     from oracle import dense as DN
@@ -227,11 +244,8 @@ def main():
     T.profile(False)
     ms = e0.elapsed_time(e1) / a.steps
     h.check()
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world / (ms / 1e3)
+    ms = reduce_max(ms, world, dev)
+    value = replica_throughput(ms, world)
     log(f"timed: {ms:.1f} ms/step, profile {prof}")
 
     # ---- end to end: pinned host z in, (l, grad) out, every step
@@ -250,12 +264,9 @@ def main():
         torch.cuda.current_stream().synchronize()
     barrier()
     e2e_s = (time.perf_counter() - t0) / a.steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = reduce_max(e2e_s, world, dev)
     log(f"e2e: {e2e_s:.2f} s/step")
-    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(z_h.numel() * 8),
+    e2e = {"value": replica_throughput(e2e_s * 1e3, world), "unit": UNIT, "h2d_bytes_per_step": int(z_h.numel() * 8),
            "d2h_bytes_per_step": int(out_h.numel() * 8)}
 
     result = out_h.numpy().copy()
