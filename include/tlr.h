@@ -52,7 +52,7 @@ typedef struct {
  * 1 = keep the rank_cap largest terms; order: 1 = Morton (Z-curve) ordering of
  * the points before tiling, 0 = keep the caller's order; dense_rank: an
  * off-diagonal tile whose eps-rank exceeds it is stored and updated dense
- * (0 = max(16, nb/16)); tiles are also made dense where a dense x dense
+ * (0 = max(16, nb/9)); tiles are also made dense where a dense x dense
  * product would land on them during the factorization; inv_scale: the
  * gradient's inverse Sigma^{-1} truncates its tiles at inv_scale * eps *
  * zeta^(1/2) (L^{-1}) and inv_scale * eps * zeta (Sigma^{-1}), zeta = the
@@ -74,7 +74,8 @@ enum {
   TLR_ERR_OOM = 3,      /* cudaMalloc failed */
   TLR_ERR_CUDA = 4,     /* a CUDA launch or runtime call failed */
   TLR_ERR_TIMEOUT = 5,  /* a device-side wait gave up */
-  TLR_ERR_STATE = 6     /* call out of order (e.g. tlr_loglik before tlr_potrf) */
+  TLR_ERR_STATE = 6,    /* call out of order (e.g. tlr_loglik before tlr_potrf) */
+  TLR_ERR_NUMERIC = 7   /* a non-finite value met in a low-rank recompression (tile index in info) */
 };
 
 /* Create a handle for n points (x[i], y[i]) (device pointers, length n).

@@ -183,7 +183,7 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   h->dense = opts->eps < 0;
   int kc = opts->rank_cap > 0 ? opts->rank_cap : std::max(1, h->nb / 2);
   h->kcap = h->dense ? 1 : std::min(kc, h->nb);
-  h->dense_rank = opts->dense_rank > 0 ? opts->dense_rank : std::max(16, h->nb / 16);
+  h->dense_rank = opts->dense_rank > 0 ? opts->dense_rank : std::max(16, h->nb / 9);
   if (h->dense_rank > 2 * h->kcap - 8) h->dense_rank = std::max(1, 2 * h->kcap - 8);
 
   std::vector<int> perm(n);

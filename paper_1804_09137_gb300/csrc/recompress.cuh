@@ -6,19 +6,24 @@
 // pair ordering, keep the singular values > eps, apply both orthogonal factors
 // back.  One CTA of 256 threads per tile; workspace in global memory (L2).
 #pragma once
+#include "df.cuh"
 #include "tile.cuh"
 
 namespace {
 
 struct ItemWs {  // per-item workspace layout (doubles)
-  double* Up;    // nb x Kmax
+  double* Up;    // nb x Kmax (float64 input; double-float after the QR starts)
   double* Vp;    // nb x Kmax
+  dfloat* Uq;    // nb x Kmax double-float output buffers
+  dfloat* Vq;
   double* W;     // kcap x kcap
   double* M;     // Kmax x Kmax
   double* Y;     // Kmax x Kmax
   double* tu;    // Kmax
   double* tv;    // Kmax
   double* s;     // Kmax
+  int* eu;       // Kmax column scale exponents of Up
+  int* ev;       // Kmax column scale exponents of Vp
 };
 
 __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int slot, int nb, int Kmax, int kcap) {
@@ -26,12 +31,16 @@ __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int s
   double* p = base + (size_t)slot * item_elems;
   w.Up = p; p += (size_t)nb * Kmax;
   w.Vp = p; p += (size_t)nb * Kmax;
+  w.Uq = (dfloat*)p; p += (size_t)nb * Kmax;
+  w.Vq = (dfloat*)p; p += (size_t)nb * Kmax;
   w.W = p; p += (size_t)kcap * kcap;
   w.M = p; p += (size_t)Kmax * Kmax;
   w.Y = p; p += (size_t)Kmax * Kmax;
   w.tu = p; p += Kmax;
   w.tv = p; p += Kmax;
-  w.s = p;
+  w.s = p; p += Kmax;
+  w.eu = (int*)p;
+  w.ev = w.eu + Kmax;
   return w;
 }
 
@@ -84,6 +93,66 @@ __device__ void cta_apply_q(const double* __restrict__ A, int lda, int m, int K,
       d = warp_sum(d) * tc;
       if (lane == 0) b[c] -= d;
       for (int r = c + 1 + lane; r < m; r += 32) b[r] = fma(-d, v[r], b[r]);
+    }
+  }
+}
+
+// Householder QR in place in double-float storage A (m x K, ld lda): R on and
+// above the diagonal, reflector v below it (v0 = 1), tau[c] in float64.  The
+// scalars of each reflector are formed in float64 from double-float sums.
+__device__ void cta_geqr2_df(dfloat* __restrict__ A, int lda, int m, int K, double* __restrict__ tau, double* sh) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nref = K < m ? K : m;
+  for (int c = 0; c < nref; ++c) {
+    dfloat* a = A + (size_t)c * lda;
+    float ps = 0.f, pc = 0.f;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) df_dot_add(ps, pc, a[r], a[r]);
+    const double sig = block_sum((double)ps + (double)pc, sh);
+    const double alpha = df_to(a[c]);
+    double beta = alpha, tc = 0.0, scal = 1.0;
+    if (sig > 0.0) {
+      beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+      tc = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    const dfloat scd = df_from(scal);
+    if (sig > 0.0)
+      for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) a[r] = df_mul(a[r], scd);
+    __syncthreads();
+    if (threadIdx.x == 0) { a[c] = df_from(beta); tau[c] = tc; }
+    if (tc != 0.0) {
+      for (int j = c + 1 + warp; j < K; j += nw) {
+        dfloat* b = A + (size_t)j * lda;
+        float s = 0.f, e = 0.f;
+        for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, a[r], b[r]);
+        double d = warp_sum((double)s + (double)e);
+        d = (d + df_to(b[c])) * tc;
+        const dfloat dd = df_from(d);
+        if (lane == 0) b[c] = df_from(df_to(b[c]) - d);
+        for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], dd, a[r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B <- Q B (double-float), Q = H_0 ... H_{K-1} from cta_geqr2_df; warp per column
+__device__ void cta_apply_q_df(const dfloat* __restrict__ A, int lda, int m, int K, const double* __restrict__ tau,
+                               dfloat* __restrict__ B, int ldb, int ncol) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < ncol; j += nw) {
+    dfloat* b = B + (size_t)j * ldb;
+    for (int c = K - 1; c >= 0; --c) {
+      const double tc = tau[c];
+      if (tc == 0.0) continue;
+      const dfloat* v = A + (size_t)c * lda;
+      float s = 0.f, e = 0.f;
+      for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, v[r], b[r]);
+      double d = warp_sum((double)s + (double)e);
+      d = (d + df_to(b[c])) * tc;
+      const dfloat dd = df_from(d);
+      if (lane == 0) b[c] = df_from(df_to(b[c]) - d);
+      for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], dd, v[r]);
     }
   }
 }
@@ -162,18 +231,50 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
                               double* Vo, long long* st, long long info, double* sh, int* shi,
                               double* flops = nullptr) {
   if (K == 0) return 0;
-  cta_geqr2(w.Up, nb, nb, K, w.tu, sh);
-  cta_geqr2(w.Vp, nb, nb, K, w.tv, sh);
+  dfloat* Ud = (dfloat*)w.Up;
+  dfloat* Vd = (dfloat*)w.Vp;
+  // scale every column by a power of two so that its largest entry is in [1, 2):
+  // Q is unchanged, R's columns are scaled back below, and the squares formed in
+  // double-float stay far inside the float32 exponent range
+  const int warp0 = threadIdx.x >> 5, lane0 = threadIdx.x & 31, nw0 = blockDim.x >> 5;
+  for (int j = warp0; j < 2 * K; j += nw0) {
+    const double* col = (j < K ? w.Up : w.Vp) + (size_t)(j % K) * nb;
+    double mx = 0.0;
+    for (int r = lane0; r < nb; r += 32) mx = fmax(mx, fabs(col[r]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane0 == 0) {
+      const int ex = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
+      if (j < K) w.eu[j] = ex; else w.ev[j - K] = ex;
+    }
+  }
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < (size_t)nb * K; e += blockDim.x) {
+    const int j = (int)(e / nb);
+    Ud[e] = df_from(ldexp(w.Up[e], -w.eu[j]));
+    Vd[e] = df_from(ldexp(w.Vp[e], -w.ev[j]));
+  }
+  __syncthreads();
+  cta_geqr2_df(Ud, nb, nb, K, w.tu, sh);
+  cta_geqr2_df(Vd, nb, nb, K, w.tv, sh);
   const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
   // M = R_u R_v^T (Ke x Ke)
   for (int e = threadIdx.x; e < Ke * Ke; e += blockDim.x) {
     const int a = e % Ke, b = e / Ke;
     const int c0 = a > b ? a : b;
     double s = 0.0;
-    for (int c = c0; c < K; ++c) s = fma(w.Up[(size_t)c * nb + a], w.Vp[(size_t)c * nb + b], s);
+    for (int c = c0; c < K; ++c)
+      s = fma(df_to(Ud[(size_t)c * nb + a]), ldexp(df_to(Vd[(size_t)c * nb + b]), w.eu[c] + w.ev[c]), s);
     w.M[(size_t)b * Ke + a] = s;
   }
   __syncthreads();
+  {  // a non-finite core means the inputs were not finite: report, keep rank 0
+    int bad = 0;
+    for (int e = threadIdx.x; e < Ke * Ke; e += blockDim.x) bad |= !isfinite(w.M[e]);
+    if (block_sum((double)bad, sh) > 0.0) {
+      if (threadIdx.x == 0) set_status(st, TLR_ERR_NUMERIC, info);
+      return 0;
+    }
+  }
   // column-pivoted Householder QR of M, stopped at the first step whose trailing
   // block has Frobenius norm <= eps (then ||M - Q_k R_k P^T||_2 <= eps)
   double* nrm = w.s;               // partial column norms^2 (rows >= step)
@@ -200,6 +301,10 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     const double trail = block_sum(part, sh);
     if (trail <= eps2) break;
     const int piv = block_argmax(av, ai, sh, shi, nullptr);
+    if (piv < c || piv >= Ke) {  // no valid pivot (non-finite norms): stop here
+      if (threadIdx.x == 0) set_status(st, TLR_ERR_NUMERIC, info);
+      break;
+    }
     if (piv != c) {  // swap columns c and piv
       for (int r = threadIdx.x; r < Ke; r += blockDim.x) {
         const double t = w.M[(size_t)c * Ke + r];
@@ -260,19 +365,26 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   for (int j = 0; j < k; ++j)
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {
       Uo[(size_t)j * nb + r] = (r == j) ? 1.0 : 0.0;
-      Vo[(size_t)j * nb + r] = 0.0;
+      w.Vq[(size_t)j * nb + r] = make_float2(0.f, 0.f);
     }
   __syncthreads();
   cta_apply_q(w.M, Ke, Ke, k, tm, Uo, nb, k);
+  __syncthreads();  // Uo columns were written warp by warp; they are read across warps below
   // V block = P R_k^T (Ke x k): row perm[jj] gets R[:k, jj]
   for (int e = threadIdx.x; e < Ke * k; e += blockDim.x) {
     const int jj = e % Ke, c = e / Ke;
-    Vo[(size_t)c * nb + perm[jj]] = (jj >= c) ? w.M[(size_t)jj * Ke + c] : 0.0;
+    w.Vq[(size_t)c * nb + perm[jj]] = df_from((jj >= c) ? w.M[(size_t)jj * Ke + c] : 0.0);
   }
+  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from(Uo[e]);
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
-  cta_apply_q(w.Up, nb, nb, Ke, w.tu, Uo, nb, k);
-  cta_apply_q(w.Vp, nb, nb, Ke, w.tv, Vo, nb, k);
+  cta_apply_q_df(Ud, nb, nb, Ke, w.tu, w.Uq, nb, k);
+  cta_apply_q_df(Vd, nb, nb, Ke, w.tv, w.Vq, nb, k);
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) {
+    Uo[e] = df_to(w.Uq[e]);
+    Vo[e] = df_to(w.Vq[e]);
+  }
   __syncthreads();
   if (flops && threadIdx.x == 0) {
     // Householder QR of two nb x K factors, triangular core product, column norms,
@@ -322,6 +434,7 @@ __device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int a
       if (a > av) { av = a; ai = b; }
     }
     const int jstar = block_argmax(av, ai, sh, shi, &rmax);
+    if (jstar < 0 || jstar >= nb) { conv = 0; break; }  // non-finite row
     if (!(rmax > 1e-3 * tol)) {  // residual row (numerically) zero: sample another row
       if (++nsmall >= 3) { conv = 1; break; }
       if (threadIdx.x == 0) {
@@ -373,6 +486,7 @@ __device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int a
     double cm;
     const int nxt = block_argmax(av, ai, sh, shi, &cm);
     if (cm < 0.0) { conv = 1; break; }  // every row used: the cross approximation is exact
+    if (nxt < 0 || nxt >= nb) { conv = 0; break; }  // non-finite column
     istar = nxt;
   }
   *conv_out = conv;

@@ -14,9 +14,10 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtlr.so")
 
-TLR_OK, TLR_ERR_NOT_SPD, TLR_ERR_RANK_CAP, TLR_ERR_OOM, TLR_ERR_CUDA, TLR_ERR_TIMEOUT, TLR_ERR_STATE = range(7)
+TLR_OK, TLR_ERR_NOT_SPD, TLR_ERR_RANK_CAP, TLR_ERR_OOM, TLR_ERR_CUDA, TLR_ERR_TIMEOUT, TLR_ERR_STATE, \
+    TLR_ERR_NUMERIC = range(8)
 ERR_NAMES = {1: "not SPD", 2: "rank cap exceeded", 3: "out of memory", 4: "CUDA error", 5: "device wait timed out",
-             6: "call out of order"}
+             6: "call out of order", 7: "non-finite value in a recompression"}
 
 
 class TlrOpts(C.Structure):
