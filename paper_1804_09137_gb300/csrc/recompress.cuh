@@ -103,33 +103,42 @@ __device__ void cta_apply_q(const double* __restrict__ A, int lda, int m, int K,
 __device__ void cta_geqr2_df(dfloat* __restrict__ A, int lda, int m, int K, double* __restrict__ tau, double* sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nref = K < m ? K : m;
+  __shared__ dfloat sc_tau, sc_scal;
+  __shared__ int sc_on;
   for (int c = 0; c < nref; ++c) {
     dfloat* a = A + (size_t)c * lda;
     float ps = 0.f, pc = 0.f;
     for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) df_dot_add(ps, pc, a[r], a[r]);
     const double sig = block_sum((double)ps + (double)pc, sh);
-    const double alpha = df_to(a[c]);
-    double beta = alpha, tc = 0.0, scal = 1.0;
-    if (sig > 0.0) {
-      beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-      tc = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
+    if (threadIdx.x == 0) {  // the reflector's scalars, once per column, in float64
+      const double alpha = df_to(a[c]);
+      double beta = alpha, tc = 0.0, scal = 1.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tc = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      sc_on = sig > 0.0;
+      sc_tau = df_from(tc);
+      sc_scal = df_from(scal);
+      tau[c] = tc;
+      a[c] = df_from(beta);
     }
-    const dfloat scd = df_from(scal);
-    if (sig > 0.0)
+    __syncthreads();
+    const int on = sc_on;
+    const dfloat tcd = sc_tau, scd = sc_scal;
+    if (on)
       for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) a[r] = df_mul(a[r], scd);
     __syncthreads();
-    if (threadIdx.x == 0) { a[c] = df_from(beta); tau[c] = tc; }
-    if (tc != 0.0) {
+    if (on) {
       for (int j = c + 1 + warp; j < K; j += nw) {
         dfloat* b = A + (size_t)j * lda;
         float s = 0.f, e = 0.f;
         for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, a[r], b[r]);
-        double d = warp_sum((double)s + (double)e);
-        d = (d + df_to(b[c])) * tc;
-        const dfloat dd = df_from(d);
-        if (lane == 0) b[c] = df_from(df_to(b[c]) - d);
-        for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], dd, a[r]);
+        const dfloat bc = b[c];
+        const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), tcd);
+        if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
+        for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], d, a[r]);
       }
     }
     __syncthreads();
@@ -145,16 +154,85 @@ __device__ void cta_apply_q_df(const dfloat* __restrict__ A, int lda, int m, int
     for (int c = K - 1; c >= 0; --c) {
       const double tc = tau[c];
       if (tc == 0.0) continue;
+      const dfloat tcd = df_from_scaled(tc, 0);
       const dfloat* v = A + (size_t)c * lda;
       float s = 0.f, e = 0.f;
       for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, v[r], b[r]);
-      double d = warp_sum((double)s + (double)e);
-      d = (d + df_to(b[c])) * tc;
-      const dfloat dd = df_from(d);
-      if (lane == 0) b[c] = df_from(df_to(b[c]) - d);
-      for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], dd, v[r]);
+      const dfloat bc = b[c];
+      const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), tcd);
+      if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
+      for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], d, v[r]);
     }
   }
+}
+
+// C[0:m, 0:n] = beta C + alpha op(A) op(B) like cta_gemm_blocks, with the
+// products accumulated in double-float (Dot2) on the float32 pipe; inputs are
+// split to double-float as they are staged in shared memory.
+__device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double alpha, const double* __restrict__ A,
+                                                   int lda, int tA, const double* __restrict__ B, int ldb, int tB,
+                                                   double beta, double* __restrict__ C, int ldc, int blk0,
+                                                   int nblk_step, int lower_only) {
+  __shared__ dfloat As[16][64 + 1];
+  __shared__ dfloat Bs[16][64 + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int mb = (m + 63) / 64, nbk = (n + 63) / 64;
+  for (int blk = blk0; blk < mb * nbk; blk += nblk_step) {
+    const int bi = blk % mb, bj = blk / mb;
+    const int r0 = bi * 64, c0 = bj * 64;
+    if (lower_only && r0 + 63 < c0) continue;
+    float as[4][4], ae[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { as[i][j] = 0.f; ae[i][j] = 0.f; }
+    for (int k0 = 0; k0 < k; k0 += 16) {
+      __syncthreads();
+      for (int id = threadIdx.x; id < 64 * 16; id += 256) {
+        int a, kk;
+        if (!tA) { a = id & 63; kk = id >> 6; } else { kk = id & 15; a = id >> 4; }
+        const int ra = r0 + a, kc = k0 + kk;
+        double v = 0.0;
+        if (ra < m && kc < k) v = tA ? A[(size_t)ra * lda + kc] : A[(size_t)kc * lda + ra];
+        As[kk][a] = df_from_scaled(v, 0);
+        if (!tB) { kk = id & 15; a = id >> 4; } else { a = id & 63; kk = id >> 6; }
+        const int cb = c0 + a, kc2 = k0 + kk;
+        double wv = 0.0;
+        if (cb < n && kc2 < k) wv = tB ? B[(size_t)kc2 * ldb + cb] : B[(size_t)cb * ldb + kc2];
+        Bs[kk][a] = df_from_scaled(wv, 0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 16; ++kk) {
+        dfloat av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_dot_add(as[i][j], ae[i][j], av[i], bv[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+        if (r < m && c < n && (!lower_only || r >= c)) {
+          double* cp = C + (size_t)c * ldc + r;
+          const double v = df_to_scaled(df_norm(as[i][j], ae[i][j]), 0);
+          *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * v;
+        }
+      }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cta_gemm_df(int m, int n, int k, double alpha, const double* A, int lda, int tA,
+                                            const double* B, int ldb, int tB, double beta, double* C, int ldc) {
+  cta_gemm_df_blocks(m, n, k, alpha, A, lda, tA, B, ldb, tB, beta, C, ldc, 0, 1, 0);
 }
 
 // round-robin pairing: round rr of K2-1, pair pi of K2/2
@@ -250,20 +328,27 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)nb * K; e += blockDim.x) {
     const int j = (int)(e / nb);
-    Ud[e] = df_from(ldexp(w.Up[e], -w.eu[j]));
-    Vd[e] = df_from(ldexp(w.Vp[e], -w.ev[j]));
+    Ud[e] = df_from_scaled(w.Up[e], -w.eu[j]);
+    Vd[e] = df_from_scaled(w.Vp[e], -w.ev[j]);
   }
   __syncthreads();
   cta_geqr2_df(Ud, nb, nb, K, w.tu, sh);
   cta_geqr2_df(Vd, nb, nb, K, w.tv, sh);
   const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
-  // M = R_u R_v^T (Ke x Ke)
+  // R_u, R_v unscaled to float64 (Ke x K each, upper trapezoid) in the output buffers, then M = R_u R_v^T
+  double* Ru = (double*)w.Uq;
+  double* Rv = (double*)w.Vq;
+  for (int e = threadIdx.x; e < Ke * K; e += blockDim.x) {
+    const int a = e % Ke, c = e / Ke;
+    Ru[e] = (a <= c) ? df_to_scaled(Ud[(size_t)c * nb + a], w.eu[c]) : 0.0;
+    Rv[e] = (a <= c) ? df_to_scaled(Vd[(size_t)c * nb + a], w.ev[c]) : 0.0;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < Ke * Ke; e += blockDim.x) {
     const int a = e % Ke, b = e / Ke;
     const int c0 = a > b ? a : b;
     double s = 0.0;
-    for (int c = c0; c < K; ++c)
-      s = fma(df_to(Ud[(size_t)c * nb + a]), ldexp(df_to(Vd[(size_t)c * nb + b]), w.eu[c] + w.ev[c]), s);
+    for (int c = c0; c < K; ++c) s = fma(Ru[(size_t)c * Ke + a], Rv[(size_t)c * Ke + b], s);
     w.M[(size_t)b * Ke + a] = s;
   }
   __syncthreads();
@@ -375,15 +460,15 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     const int jj = e % Ke, c = e / Ke;
     w.Vq[(size_t)c * nb + perm[jj]] = df_from((jj >= c) ? w.M[(size_t)jj * Ke + c] : 0.0);
   }
-  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from(Uo[e]);
+  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from_scaled(Uo[e], 0);
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
   cta_apply_q_df(Ud, nb, nb, Ke, w.tu, w.Uq, nb, k);
   cta_apply_q_df(Vd, nb, nb, Ke, w.tv, w.Vq, nb, k);
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) {
-    Uo[e] = df_to(w.Uq[e]);
-    Vo[e] = df_to(w.Vq[e]);
+    Uo[e] = df_to_scaled(w.Uq[e], 0);
+    Vo[e] = df_to_scaled(w.Vq[e], 0);
   }
   __syncthreads();
   if (flops && threadIdx.x == 0) {

@@ -72,24 +72,24 @@ __global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__
   double pf;  // product flops
   if (!X.dense && !Y.dense) {
     pf = 2.0 * nb * X.k * Y.k * 2.0;
-    cta_gemm(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);  // W = V_x^T U_y
+    cta_gemm_df(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);  // W = V_x^T U_y
     if (Y.k <= X.k) {
-      cta_gemm(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
+      cta_gemm_df(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
       for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
       r = Y.k;
     } else {
-      cta_gemm(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Vn, nb);
+      cta_gemm_df(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Vn, nb);
       for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
       r = X.k;
     }
   } else if (X.dense) {
     pf = 2.0 * nb * nb * Y.k;
-    cta_gemm(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
+    cta_gemm_df(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
     r = Y.k;
   } else {
     pf = 2.0 * nb * nb * X.k;
-    cta_gemm(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
+    cta_gemm_df(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
     r = X.k;
   }
@@ -156,8 +156,8 @@ __global__ void k_upd_d_desc(TlrView v, int alg, int k, const int2* __restrict__
 __global__ void k_gemm_gen(const GemmGen* __restrict__ desc) {
   const GemmGen g = desc[blockIdx.y];
   if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0) return;
-  cta_gemm_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
-                  gridDim.x, g.lower);
+  cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
+                     gridDim.x, g.lower);
 }
 
 // X (nb x ncol <= 32 columns, ld nb) <- op(T) X, one CTA
