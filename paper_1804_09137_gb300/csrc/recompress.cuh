@@ -97,6 +97,39 @@ __device__ void cta_apply_q(const double* __restrict__ A, int lda, int m, int K,
   }
 }
 
+// sum_{r = r0 + lane, step 32} a[r] b[r] over r < m as a double-float, four
+// independent Dot2 accumulators so that several loads are in flight per lane
+__device__ __forceinline__ dfloat df_col_dot(const dfloat* __restrict__ a, const dfloat* __restrict__ b, int r0,
+                                             int m, int lane) {
+  float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f, s2 = 0.f, e2 = 0.f, s3 = 0.f, e3 = 0.f;
+  int r = r0 + lane;
+  for (; r + 96 < m; r += 128) {
+    const dfloat a0 = a[r], b0 = b[r], a1 = a[r + 32], b1 = b[r + 32];
+    const dfloat a2 = a[r + 64], b2 = b[r + 64], a3 = a[r + 96], b3 = b[r + 96];
+    df_dot_add(s0, e0, a0, b0);
+    df_dot_add(s1, e1, a1, b1);
+    df_dot_add(s2, e2, a2, b2);
+    df_dot_add(s3, e3, a3, b3);
+  }
+  for (; r < m; r += 32) df_dot_add(s0, e0, a[r], b[r]);
+  return df_add(df_add(df_norm(s0, e0), df_norm(s1, e1)), df_add(df_norm(s2, e2), df_norm(s3, e3)));
+}
+
+// b[r] -= d a[r] for r = r0 + lane, step 32, r < m
+__device__ __forceinline__ void df_col_axpy(dfloat* __restrict__ b, dfloat d, const dfloat* __restrict__ a, int r0,
+                                            int m, int lane) {
+  int r = r0 + lane;
+  for (; r + 96 < m; r += 128) {
+    const dfloat a0 = a[r], b0 = b[r], a1 = a[r + 32], b1 = b[r + 32];
+    const dfloat a2 = a[r + 64], b2 = b[r + 64], a3 = a[r + 96], b3 = b[r + 96];
+    b[r] = df_sub_prod(b0, d, a0);
+    b[r + 32] = df_sub_prod(b1, d, a1);
+    b[r + 64] = df_sub_prod(b2, d, a2);
+    b[r + 96] = df_sub_prod(b3, d, a3);
+  }
+  for (; r < m; r += 32) b[r] = df_sub_prod(b[r], d, a[r]);
+}
+
 // Householder QR in place in double-float storage A (m x K, ld lda): R on and
 // above the diagonal, reflector v below it (v0 = 1), tau[c] in float64.  The
 // scalars of each reflector are formed in float64 from double-float sums.
@@ -133,12 +166,10 @@ __device__ void cta_geqr2_df(dfloat* __restrict__ A, int lda, int m, int K, doub
     if (on) {
       for (int j = c + 1 + warp; j < K; j += nw) {
         dfloat* b = A + (size_t)j * lda;
-        float s = 0.f, e = 0.f;
-        for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, a[r], b[r]);
         const dfloat bc = b[c];
-        const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), tcd);
+        const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(a, b, c + 1, m, lane)), bc), tcd);
         if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
-        for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], d, a[r]);
+        df_col_axpy(b, d, a, c + 1, m, lane);
       }
     }
     __syncthreads();
@@ -156,12 +187,10 @@ __device__ void cta_apply_q_df(const dfloat* __restrict__ A, int lda, int m, int
       if (tc == 0.0) continue;
       const dfloat tcd = df_from_scaled(tc, 0);
       const dfloat* v = A + (size_t)c * lda;
-      float s = 0.f, e = 0.f;
-      for (int r = c + 1 + lane; r < m; r += 32) df_dot_add(s, e, v[r], b[r]);
       const dfloat bc = b[c];
-      const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), tcd);
+      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(v, b, c + 1, m, lane)), bc), tcd);
       if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
-      for (int r = c + 1 + lane; r < m; r += 32) b[r] = df_sub_prod(b[r], d, v[r]);
+      df_col_axpy(b, d, v, c + 1, m, lane);
     }
   }
 }

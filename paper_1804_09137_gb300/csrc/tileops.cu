@@ -43,7 +43,7 @@ __device__ __forceinline__ void operands(const TlrView& v, int alg, int a, int b
   else { *X = operand(v, k, a, true); *Y = operand(v, k, b, false); *alpha = 1.0; }
 }
 
-__global__ void k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items, double eps,
+__global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items, double eps,
                              const double* __restrict__ d_zeta, double zpow, int Kmax, int trunc_cap,
                              double* __restrict__ ws, size_t item_elems, long long* __restrict__ st,
                              double* __restrict__ flops) {
