@@ -121,6 +121,21 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
 /* Synthetic measurements of Sec. VIII-D: z = L e on the factored handle. */
 int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream);
 
+/* Independent regions (exact likelihood of many unrelated problems, e.g. the
+ * regions of a large field, Sec. VII-VIII): l and dl/dtheta of R problems.
+ * n, x, y, z, theta, opts are host arrays of length R; x[r], y[r], z[r] are
+ * device arrays of n[r] doubles; opts[r] may differ per region (tile size,
+ * threshold; eps < 0 is dense).  d_ll (device, R doubles) and d_grad (device,
+ * 3R doubles, sigma2/beta/nu per region) receive the results; status (host,
+ * R ints) each region's TLR status.  nworkers host threads (0 = 8), each with
+ * its own stream, take regions in turn and keep one handle per tile size,
+ * allocated once at the capacity of the largest region using it and rebound
+ * to each region's points.  Returns when every region is done; `stream` is
+ * ordered after the work.  Returns the first worker failure, else TLR_OK. */
+int tlr_loglik_grad_batched(int R, const int64_t* n, const double* const* x, const double* const* y,
+                            const double* const* z, const tlr_theta* theta, const tlr_opts* opts, double* d_ll,
+                            double* d_grad, int* status, int nworkers, tlr_stream_t stream);
+
 /* Synchronise the handle's last stream and report the first device-side
  * failure (TLR_OK if none); *info gets the failing column for
  * TLR_ERR_NOT_SPD, the offending tile index for TLR_ERR_RANK_CAP. */

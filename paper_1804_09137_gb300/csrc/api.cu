@@ -15,12 +15,12 @@
 #include "common.cuh"
 
 
-long long g_tlr_launches = 0;
-TlrProfile g_tlr_prof = {0, nullptr, 0, 0.0};
+std::atomic<long long> g_tlr_launches{0};
+thread_local TlrProfile g_tlr_prof = {0, nullptr, 0, 0.0};
 
 namespace {
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev;  // recorded (start, stop) pairs
-std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev_free;
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev;  // recorded (start, stop) pairs
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev_free;
 cudaEvent_t g_ev_open = nullptr;
 }  // namespace
 
@@ -47,8 +47,8 @@ struct PhaseRec {
   const char* name;
   cudaEvent_t a, b;
 };
-std::vector<PhaseRec> g_ph;
-std::vector<int> g_ph_open;
+thread_local std::vector<PhaseRec> g_ph;
+thread_local std::vector<int> g_ph_open;
 }  // namespace
 
 void tlr_phase_begin(const char* name, cudaStream_t s) {
@@ -146,6 +146,36 @@ void free_ctx(tlr_ctx* h) {
   delete h;
 }
 
+// (Re)bind a handle to n <= cap_n points: Morton order, sorted padded
+// coordinates, table range; resets the pipeline state.  Synchronises s.
+int bind_points(tlr_ctx* h, int64_t n, const std::vector<double>& hx, const std::vector<double>& hy, cudaStream_t s) {
+  if (n > h->cap_n) return -1;
+  h->n = n;
+  h->nt = (int)((n + h->nb - 1) / h->nb);
+  h->npad = (int64_t)h->nt * h->nb;
+  h->ntiles = (int64_t)h->nt * (h->nt - 1) / 2;
+  std::vector<int> perm(n);
+  if (h->opts.order) perm = morton_order(hx, hy);
+  else std::iota(perm.begin(), perm.end(), 0);
+  std::vector<double> sx(h->npad, 0.0), sy(h->npad, 0.0);
+  for (int64_t s2 = 0; s2 < n; ++s2) { sx[s2] = hx[perm[s2]]; sy[s2] = hy[perm[s2]]; }
+  h->mp.e_lo = 0;
+  h->tab_valid = 0;
+  set_table_range(h, bbox_diag(hx.data(), hy.data(), n));
+  h->state = 0;
+  h->zplan_valid = 0;
+  cudaError_t e1 = cudaMemcpyAsync(h->x, sx.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaError_t e2 = cudaMemcpyAsync(h->y, sy.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaError_t e3 = cudaMemcpyAsync(h->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
+  cudaError_t e4 = cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s);
+  cudaError_t e5 = cudaMemsetAsync(h->rank, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
+  if (e5 == cudaSuccess) e5 = cudaMemsetAsync(h->dslot, 0xff, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
+  cudaError_t e6 = cudaStreamSynchronize(s);
+  if (e1 || e2 || e3 || e4 || e5 || e6) return TLR_ERR_CUDA;
+  h->last_stream = s;
+  return TLR_OK;
+}
+
 #define TRY(x)                 \
   do {                         \
     int rc_ = (x);             \
@@ -153,6 +183,60 @@ void free_ctx(tlr_ctx* h) {
   } while (0)
 
 }  // namespace
+
+// Allocate a handle with capacity for cap points (not yet bound to points).
+int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
+  tlr_ctx* h = new tlr_ctx();
+  memset(h, 0, sizeof(*h));
+  h->opts = *opts;
+  h->nb = opts->nb;
+  h->cap_n = n;
+  h->cap_nt = (int)((n + h->nb - 1) / h->nb);
+  h->cap_ntiles = (int64_t)h->cap_nt * (h->cap_nt - 1) / 2;
+  h->dense = opts->eps < 0;
+  int kc = opts->rank_cap > 0 ? opts->rank_cap : std::max(1, h->nb / 2);
+  h->kcap = h->dense ? 1 : std::min(kc, h->nb);
+  h->dense_rank = opts->dense_rank > 0 ? opts->dense_rank : std::max(16, h->nb / 9);
+  if (h->dense_rank > 2 * h->kcap - 8) h->dense_rank = std::max(1, 2 * h->kcap - 8);
+
+  const size_t nb = h->nb;
+  const size_t slot = nb * (size_t)h->kcap;
+  const int64_t cnp = (int64_t)h->cap_nt * h->nb, ct = h->cap_ntiles;
+  int rc = TLR_OK;
+  rc |= dmalloc(&h->x, cnp);
+  rc |= dmalloc(&h->y, cnp);
+  rc |= dmalloc(&h->perm, n);
+  rc |= dmalloc(&h->D, (size_t)h->cap_nt * nb * nb);
+  rc |= dmalloc(&h->U, h->dense ? 1 : (size_t)ct * slot);
+  rc |= dmalloc(&h->V, h->dense ? 1 : (size_t)ct * slot);
+  rc |= dmalloc(&h->rank, ct);
+  rc |= dmalloc(&h->dslot, ct);
+  rc |= dmalloc(&h->tab, TAB_ELEMS);
+  rc |= dmalloc(&h->d_stat, 4);
+  rc |= dmalloc(&h->d_vec, 4 * (size_t)cnp);
+  h->red_len = 2 * h->cap_nt + 64;
+  rc |= dmalloc(&h->d_red, h->red_len);
+  // workspace: low-rank update items, SYRK items, table nodes, gradient partials
+  const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap);
+  const int64_t max_items = std::max<int64_t>(ct, 1);
+  const int64_t chunk = std::min<int64_t>(max_items, 912);
+  size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
+  ws = std::max(ws, (size_t)std::min<int64_t>(max_items, 912) * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
+  ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->cap_nt * (h->cap_nt + 1) / 2 + 16));
+  // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
+  const size_t mb = (nb + 63) / 64;
+  ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->cap_nt * (h->cap_nt + 1) / 2 + 1024));
+  ws = std::max(ws, 2 * nb * nb + 4096);
+  h->scratch_elems = ws;
+  rc |= dmalloc(&h->scratch, ws);
+  if (rc != TLR_OK) {
+    free_ctx(h);
+    return TLR_ERR_OOM;
+  }
+  *out = h;
+  return TLR_OK;
+}
+
 
 extern "C" {
 
@@ -172,74 +256,14 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   for (int64_t i = 0; i < n; ++i)
     if (!(hx[i] == hx[i]) || !(hy[i] == hy[i])) return -2;  // NaN location
 
-  tlr_ctx* h = new tlr_ctx();
-  memset(h, 0, sizeof(*h));
-  h->opts = *opts;
-  h->n = n;
-  h->nb = opts->nb;
-  h->nt = (int)((n + h->nb - 1) / h->nb);
-  h->npad = (int64_t)h->nt * h->nb;
-  h->ntiles = (int64_t)h->nt * (h->nt - 1) / 2;
-  h->dense = opts->eps < 0;
-  int kc = opts->rank_cap > 0 ? opts->rank_cap : std::max(1, h->nb / 2);
-  h->kcap = h->dense ? 1 : std::min(kc, h->nb);
-  h->dense_rank = opts->dense_rank > 0 ? opts->dense_rank : std::max(16, h->nb / 9);
-  if (h->dense_rank > 2 * h->kcap - 8) h->dense_rank = std::max(1, 2 * h->kcap - 8);
-
-  std::vector<int> perm(n);
-  if (opts->order) perm = morton_order(hx, hy);
-  else std::iota(perm.begin(), perm.end(), 0);
-  std::vector<double> sx(h->npad, 0.0), sy(h->npad, 0.0);
-  for (int64_t s2 = 0; s2 < n; ++s2) { sx[s2] = hx[perm[s2]]; sy[s2] = hy[perm[s2]]; }
-  h->mp.e_lo = 0;
-  h->tab_valid = 0;
-  set_table_range(h, bbox_diag(hx.data(), hy.data(), n));
-
-  const size_t nb = h->nb;
-  const size_t slot = nb * (size_t)h->kcap;
-  int rc = TLR_OK;
-  rc |= dmalloc(&h->x, h->npad);
-  rc |= dmalloc(&h->y, h->npad);
-  rc |= dmalloc(&h->perm, n);
-  rc |= dmalloc(&h->D, (size_t)h->nt * nb * nb);
-  rc |= dmalloc(&h->U, h->dense ? 1 : (size_t)h->ntiles * slot);
-  rc |= dmalloc(&h->V, h->dense ? 1 : (size_t)h->ntiles * slot);
-  rc |= dmalloc(&h->rank, h->ntiles);
-  rc |= dmalloc(&h->dslot, h->ntiles);
-  rc |= dmalloc(&h->tab, TAB_ELEMS);
-  rc |= dmalloc(&h->d_stat, 4);
-  rc |= dmalloc(&h->d_vec, 4 * (size_t)h->npad);
-  h->red_len = 2 * h->nt + 64;
-  rc |= dmalloc(&h->d_red, h->red_len);
-  // workspace: low-rank update items, SYRK items, table nodes, gradient partials
-  const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap);
-  const int64_t max_items = std::max<int64_t>(h->ntiles, 1);
-  const int64_t chunk = std::min<int64_t>(max_items, 912);
-  size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
-  ws = std::max(ws, (size_t)std::min<int64_t>(max_items, 912) * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
-  ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->nt * (h->nt + 1) / 2 + 16));
-  // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
-  const size_t mb = (nb + 63) / 64;
-  ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->nt * (h->nt + 1) / 2 + 1024));
-  ws = std::max(ws, 2 * nb * nb + 4096);
-  h->scratch_elems = ws;
-  rc |= dmalloc(&h->scratch, ws);
+  tlr_ctx* h = nullptr;
+  int rc = tlr_alloc(n, opts, &h);
+  if (rc != TLR_OK) return rc;
+  rc = bind_points(h, n, hx, hy, s);
   if (rc != TLR_OK) {
     free_ctx(h);
-    return TLR_ERR_OOM;
+    return rc;
   }
-  cudaError_t e1 = cudaMemcpyAsync(h->x, sx.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
-  cudaError_t e2 = cudaMemcpyAsync(h->y, sy.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
-  cudaError_t e3 = cudaMemcpyAsync(h->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
-  cudaError_t e4 = cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s);
-  cudaError_t e5 = cudaMemsetAsync(h->rank, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
-  if (e5 == cudaSuccess) e5 = cudaMemsetAsync(h->dslot, 0xff, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s);
-  cudaError_t e6 = cudaStreamSynchronize(s);
-  if (e1 || e2 || e3 || e4 || e5 || e6) {
-    free_ctx(h);
-    return TLR_ERR_CUDA;
-  }
-  h->last_stream = s;
   *out = h;
   return TLR_OK;
 }
@@ -520,7 +544,7 @@ int tlr_profile_phases(char* buf, int64_t len) {
 
 int tlr_launch_count(int64_t* count) {
   if (!count) return -1;
-  *count = g_tlr_launches;
+  *count = g_tlr_launches.load();
   return TLR_OK;
 }
 
@@ -556,6 +580,17 @@ int tlr_profile_read(int64_t* launches, double* ms, double* flops) {
 
 }  // extern "C"
 
+
+int tlr_rebind(tlr_ctx* h, int64_t n, const double* x, const double* y, cudaStream_t s) {
+  if (n <= 0 || n > h->cap_n) return -1;
+  std::vector<double> hx(n), hy(n);
+  TLR_CUDA_TRY(cudaMemcpyAsync(hx.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(hy.data(), y, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int64_t i = 0; i < n; ++i)
+    if (!(hx[i] == hx[i]) || !(hy[i] == hy[i])) return -2;
+  return bind_points(h, n, hx, hy, s);
+}
 
 // Host plan of one factorization: tile kinds (dense above dense_rank or where
 // fill-in from two dense tiles lands), dense-pool slots, per-step item lists.

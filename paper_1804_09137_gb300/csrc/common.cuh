@@ -59,6 +59,9 @@ struct tlr_ctx {
   int64_t n, npad;
   int nb, nt;
   int64_t ntiles;  // strictly lower tiles nt(nt-1)/2
+  int64_t cap_n;   // allocation capacity (points); a handle can be rebound to n <= cap_n
+  int cap_nt;
+  int64_t cap_ntiles;
   tlr_opts opts;
   int dense;       // eps < 0: every off-diagonal tile dense
   int kcap;        // rank capacity of a low-rank tile
@@ -120,7 +123,8 @@ struct tlr_ctx {
     }                                                                        \
   } while (0)
 
-extern long long g_tlr_launches;  // kernel launches issued by the library
+#include <atomic>
+extern std::atomic<long long> g_tlr_launches;  // kernel launches issued by the library
 #define TLR_LAUNCH_CHECK()                                                   \
   do {                                                                       \
     ++g_tlr_launches;                                                        \
@@ -242,7 +246,7 @@ struct TlrProfile {
   long long launches;
   double ms;
 };
-extern TlrProfile g_tlr_prof;
+extern thread_local TlrProfile g_tlr_prof;  // per host thread
 void tlr_prof_begin(cudaStream_t s);
 void tlr_prof_end(cudaStream_t s);
 // per-phase device time (events around each phase when profiling is enabled)
@@ -261,6 +265,8 @@ int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t
 int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s);
 int tlr_factor(tlr_ctx* h, cudaStream_t s);
 int tlr_plan(tlr_ctx* h, cudaStream_t s);
+int tlr_rebind(tlr_ctx* h, int64_t n, const double* x, const double* y, cudaStream_t s);
+int tlr_alloc(int64_t cap_n, const tlr_opts* opts, tlr_ctx** out);
 size_t tlr_item_elems(int nb, int kcap);
 int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s);
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);

@@ -212,8 +212,8 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
 static int ensure_z(tlr_ctx* h) {
   if (h->Dz) return TLR_OK;
   const size_t nb = h->nb, slot = nb * h->kcap;
-  const size_t T = std::max<int64_t>(h->ntiles, 1);
-  bool ok = cudaMalloc((void**)&h->Dz, (size_t)h->nt * nb * nb * sizeof(double)) == cudaSuccess;
+  const size_t T = std::max<int64_t>(h->cap_ntiles, 1);
+  bool ok = cudaMalloc((void**)&h->Dz, (size_t)h->cap_nt * nb * nb * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&h->Uz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&h->Vz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&h->rankz, T * sizeof(int)) == cudaSuccess;

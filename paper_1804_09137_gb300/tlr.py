@@ -42,6 +42,7 @@ _lib = None
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
            "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
+           "tlr_loglik_grad_batched",
            "tlr_profile_read"]
 
 
@@ -72,6 +73,9 @@ def lib():
     L.tlr_launch_count.argtypes = [C.POINTER(i64)]
     L.tlr_inverse_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
     L.tlr_profile.argtypes = [C.c_int]
+    L.tlr_loglik_grad_batched.argtypes = [C.c_int, C.POINTER(i64), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                          C.POINTER(TlrTheta), C.POINTER(TlrOpts), vp, vp, C.POINTER(C.c_int),
+                                          C.c_int, vp]
     L.tlr_loglik_dense_noalloc.argtypes = [i64, vp, vp, vp, TlrTheta, vp, vp]
     L.tlr_profile_phases.argtypes = [C.c_char_p, i64]
     L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
@@ -232,3 +236,23 @@ def profile_phases() -> dict:
     buf = C.create_string_buffer(1 << 16)
     _check("tlr_profile_phases", lib().tlr_profile_phases(buf, len(buf)))
     return json.loads(buf.value.decode())
+
+
+def loglik_grad_batched(xs, ys, zs, thetas, opts, nworkers: int = 8):
+    """l and dl/dtheta of independent regions (lists of float64 CUDA tensors, thetas, TlrOpts).
+
+    Returns (ll (R,), grad (R, 3), status list)."""
+    R = len(xs)
+    dev = xs[0].device
+    n = (C.c_int64 * R)(*[int(t.numel()) for t in xs])
+    px = (C.c_void_p * R)(*[_ptr(t).value for t in xs])
+    py = (C.c_void_p * R)(*[_ptr(t).value for t in ys])
+    pz = (C.c_void_p * R)(*[_ptr(t).value for t in zs])
+    th = (TlrTheta * R)(*[TlrTheta(*[float(v) for v in t]) for t in thetas])
+    op = (TlrOpts * R)(*opts)
+    ll = torch.empty(R, dtype=torch.float64, device=dev)
+    grad = torch.empty(R, 3, dtype=torch.float64, device=dev)
+    st = (C.c_int * R)()
+    _check("tlr_loglik_grad_batched", lib().tlr_loglik_grad_batched(R, n, px, py, pz, th, op, _ptr(ll), _ptr(grad),
+                                                                    st, int(nworkers), _stream()))
+    return ll, grad, list(st)
