@@ -111,14 +111,14 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   if (!h->kindz) return TLR_ERR_OOM;
   char* K = h->kindz;
   // Z keeps the factor's dense tiles; a low-rank factor tile whose rank exceeds
-  // zdense_rank is also made dense in Z (inverse ranks run several times higher)
+  // 2/5 of dense_rank is also made dense in Z (inverse ranks run about 3.5 times
+  // the factor's, and the update of a dense tile is a parallel GEMM)
   std::vector<int> rk(std::max<int64_t>(T, 1), 0);
   if (T > 0) {
     TLR_CUDA_TRY(cudaMemcpyAsync(rk.data(), h->rank, T * sizeof(int), cudaMemcpyDeviceToHost, s));
     TLR_CUDA_TRY(cudaStreamSynchronize(s));
   }
-  int zr = h->dense_rank;
-  if (const char* e = getenv("TLR_ZDENSE_RANK")) zr = atoi(e);
+  const int zr = std::max(16, (2 * h->dense_rank) / 5);
   for (int64_t t = 0; t < T; ++t) K[t] = (h->kind ? h->kind[t] : 0) || (zr > 0 && rk[t] > zr);
   auto kd = [&](int p, int q) -> char& { return K[tile_index(p, q)]; };
   // No fill closure: the inverse of a banded triangular matrix is full, so the
