@@ -11,11 +11,14 @@
 //   2. A_mn <- A_mn + A_km^T A_kn              n < m < k
 //   3. A_kn <- A_kk^T A_kn                     n < k  (low rank: U <- M_kk^T U)
 //   4. A_kk <- A_kk^T A_kk
-// Low-rank targets are recompressed at tau_M = eps sqrt(zeta) (TRTRI) and
-// tau_Z = eps zeta (LAUUM), zeta = max_a 1 / L_aa^2 ~ the scale of Z's
-// diagonal, so that the truncation is relative to the size of M and Z as eps
-// is to Sigma.  Z keeps the factor's dense tiles; a dense x dense product that
-// lands on a low-rank tile is formed by GEMM and recompressed.
+// TRTRI keeps L^{-1} in tile low-rank form (its tiles are sources of later
+// products) and recompresses at tau_M = eps sqrt(zeta), zeta = max_a 1 / L_aa^2
+// (the scale of L^{-1} squared), so the truncation is relative to the size of
+// L^{-1} as eps is to Sigma; a dense x dense product landing on a low-rank tile
+// is formed by GEMM and recompressed.  Sigma^{-1}'s tiles are never sources:
+// only the gradient pass reads them, so LAUUM accumulates every off-diagonal
+// tile densely (no truncation): a row of L^{-1} is expanded to dense right
+// after its last use as a source.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -23,6 +26,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "recompress.cuh"
 #include "tileops.h"
 
 namespace {
@@ -83,6 +87,23 @@ __global__ void k_copy_to_z(TlrView f, TlrView z, int64_t ntiles) {
   }
 }
 
+// tiles (r, n), n < r, still low rank: A = U V^T into their own dense slot (slot = tile index)
+__global__ void k_expand_row(TlrView z, int r) {
+  const int n = blockIdx.y;
+  const int64_t t = dtile_index(r, n);
+  if (z.dslot[t] >= 0) return;
+  const int nb = z.nb;
+  cta_gemm_df_blocks(nb, nb, z.rank[t], 1.0, tileU(z, t), nb, 0, tileV(z, t), nb, 1, 0.0,
+                     z.dpool + (size_t)t * nb * nb, nb, blockIdx.x, gridDim.x, 0);
+}
+
+__global__ void k_mark_row_dense(TlrView z, int r) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= r) return;
+  const int64_t t = dtile_index(r, n);
+  z.dslot[t] = (int)t;
+}
+
 __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     b[e] = a[e];
@@ -125,15 +146,17 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   // closure would make every tile dense although the far tiles of L^{-1} and
   // Sigma^{-1} are numerically low rank.  A dense x dense product that lands on
   // a low-rank tile is materialised and recompressed instead (phases *_DD).
+  // every tile owns dense slot t: L^{-1}'s dense tiles use it during TRTRI, and
+  // every tile of Sigma^{-1} is accumulated densely there during LAUUM
   std::vector<int> slot(std::max<int64_t>(T, 1), -1);
   int nd = 0;
   for (int64_t t = 0; t < T; ++t)
-    if (K[t]) slot[t] = nd++;
-  if (nd > h->dcapz) {
+    if (K[t]) { slot[t] = (int)t; ++nd; }
+  if (T > h->dcapz) {
     if (h->dpoolz) cudaFree(h->dpoolz);
     h->dpoolz = nullptr;
     h->dcapz = 0;
-    const int want = nd + nd / 8 + 1;
+    const int want = (int)std::max<int64_t>(T, 1);
     if (cudaMalloc((void**)&h->dpoolz, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return TLR_ERR_OOM;
@@ -162,13 +185,11 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
         case ZP_T3_LR: case ZP_T3_D: case ZP_L3_LR: case ZP_L3_D:
           for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
           break;
-        case ZP_L2_LR: case ZP_L2_D: case ZP_L2_DD:
+        case ZP_L2_D:  // LAUUM targets are dense (their rows were expanded before)
           for (int m = 1; m < k; ++m)
-            for (int n2 = 0; n2 < m; ++n2) {
-              const bool dd = kd(k, m) && kd(k, n2);
-              if (ph == ZP_L2_D ? kd(m, n2) == 1 : (kd(m, n2) == 0 && dd == (ph == ZP_L2_DD)))
-                L.push_back(make_int2(m, n2));
-            }
+            for (int n2 = 0; n2 < m; ++n2) L.push_back(make_int2(m, n2));
+          break;
+        case ZP_L2_LR: case ZP_L2_DD:
           break;
       }
     }
@@ -284,10 +305,22 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   }
   // ---- LAUUM
   GemmGen* desc = (GemmGen*)(h->scratch + nn);
+  const int mb = (nb + 63) / 64;
+  auto expand_row = [&](int r) -> int {
+    if (r < 1) return TLR_OK;
+    k_expand_row<<<dim3(mb * mb, r), 256, 0, s>>>(z, r);
+    TLR_LAUNCH_CHECK();
+    k_mark_row_dense<<<(r + 127) / 128, 128, 0, s>>>(z, r);
+    TLR_LAUNCH_CHECK();
+    return TLR_OK;
+  };
   for (int k = 0; k < nt; ++k) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
     auto L = [&](int ph) { return h->d_zlist + off[ph]; };
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
+    // row k-1 was a source for the last time in step k-1: from now on its tiles are
+    // dense targets of Sigma^{-1}
+    { PhaseScope ps("lauum.expand", s); ZTRY(expand_row(k - 1)); }
     { PhaseScope ps("lauum.herk", s); ZTRY(tops_herk_row(h, z, k, s)); }
     { PhaseScope ps("lauum.update", s);
       ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s)); }
@@ -305,5 +338,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     k_copy<<<256, 256, 0, s>>>(X, h->Dz + (size_t)k * nn, (int64_t)nn);
     TLR_LAUNCH_CHECK();
   }
+  { PhaseScope ps("lauum.expand", s); ZTRY(expand_row(nt - 1)); }
+  h->zplan_valid = 0;  // the device tile kinds of Z changed: the next inverse re-plans
   return TLR_OK;
 }
