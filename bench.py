@@ -53,8 +53,9 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
-    p.add_argument("--workload", default="n90k", choices=["n90k", "regions"],
-                   help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent regions")
+    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k"],
+                   help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent "
+                        "regions; n40k: TLR vs dense likelihood at n = 40,000 and kriging of 10% held out")
     p.add_argument("--regions", type=int, default=512)
     p.add_argument("--workers", type=int, default=8)
     p.add_argument("--side", type=int, default=300)
@@ -230,8 +231,70 @@ def run_regions(a):
     print(json.dumps(line), flush=True)
 
 
+def run_n40k(a):
+    """200 x 200 jittered grid, theta = (1, 0.1, 0.5), nb = 800, eps = 1e-9, rank cap 200; 10% held out.
+
+    One likelihood evaluation on the 36,000 observed points in TLR form and in dense float64 (same library,
+    every tile dense), their relative difference, and the kriging MSE of the 4,000 held-out values (the
+    paper's Sec. VIII-D1 reports an average MSE of 0.036 at beta = 0.1 for 100 held-out of 40K points)."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_1804_09137_gb300 import inputs
+    from paper_1804_09137_gb300 import tlr as T
+
+    theta = (1.0, 0.1, 0.5)
+    dev = torch.device("cuda")
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(200)
+    n = len(x)
+    # z at all 40,000 points from a tight factor (eps = 1e-12), then 10% held out
+    hs = T.Handle(t64(x), t64(y), nb=800, eps=1e-12, rank_cap=400)
+    hs.factor(theta)
+    z = hs.sample(t64(inputs.standard_normal(n)))
+    hs.check()
+    hs.close()
+    obs, held = inputs.holdout(n, n // 10)
+    zo = z[torch.as_tensor(obs, device=dev)].contiguous()
+    zh = z[torch.as_tensor(held, device=dev)].contiguous()
+    res = {}
+    for name, eps, cap in (("tlr", 1e-9, 200), ("dense", -1.0, 0)):
+        h = T.Handle(t64(x[obs]), t64(y[obs]), nb=800, eps=eps, rank_cap=cap)
+        for _ in range(2 if name == "tlr" else 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.factor(theta)
+            out = h.loglik(zo)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        h.check()
+        pred = h.predict(zo, t64(x[held]), t64(y[held]))
+        mse = float(((pred - zh) ** 2).mean().item())
+        res[name] = {"loglik": float(out[0].item()), "seconds": secs, "mse": mse,
+                     "ranks": h.rank_stats() if name == "tlr" else None}
+        log(name, res[name])
+        h.close()
+    rel = abs(res["tlr"]["loglik"] - res["dense"]["loglik"]) / abs(res["dense"]["loglik"])
+    line = {"metric": "loglik evals/s at n=36k (40k grid, 10% held out): TLR eps=1e-9 vs dense FP64",
+            "value": 1.0 / res["tlr"]["seconds"], "unit": "evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": res["tlr"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "matern_n40000_nb800_eps1e-9_cap200_theta1-0.1-0.5", "n_obs": len(obs),
+                       "n_held_out": len(held)},
+            "dense_fp64_gpu": {"value": 1.0 / res["dense"]["seconds"], "unit": "evals/s",
+                               "seconds": res["dense"]["seconds"]},
+            "tlr_rel_err_vs_dense": rel, "kriging_mse": {"tlr": res["tlr"]["mse"], "dense": res["dense"]["mse"],
+                                                        "paper_average_beta_0.1": 0.036},
+            "result": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
+    if a.workload == "n40k" and a.impl != "reference":
+        return run_n40k(a)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "regions":

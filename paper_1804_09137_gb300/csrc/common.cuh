@@ -99,6 +99,7 @@ struct tlr_ctx {
   int zplan_valid;
   double* tab;     // Matérn table (TAB_ELEMS)
   MaternParams mp;
+  double* dinv;    // nb x nb: explicit inverse (or transform) of the current diagonal tile
   double* scratch; // batched-kernel workspace
   size_t scratch_elems;
   size_t item_elems;  // workspace per low-rank update item

@@ -73,100 +73,6 @@ __global__ void k_gen_dense_list(const double* __restrict__ tab, const MaternPar
   }
 }
 
-// ------------------------------------------------------------------- TRSM
-// low rank: V_ik <- L_kk^{-1} V_ik, items (i, k); 32 columns per CTA
-__global__ void k_trsm_lr(TlrView v, const int2* __restrict__ items) {
-  const int2 it = items[blockIdx.y];
-  const int64_t t = dtile_index(it.x, it.y);
-  const int kr = v.rank[t];
-  const int cb = blockIdx.x * 32;
-  if (cb >= kr) return;
-  const int nb = v.nb;
-  const int ncol = min(32, kr - cb);
-  const double* L = diagT(v, it.y);
-  double* X = tileV(v, t) + (size_t)cb * nb;
-  __shared__ double Ls[32][33];
-  __shared__ double Xs[32][33];
-  for (int rb0 = 0; rb0 < nb; rb0 += 32) {
-    const int w = min(32, nb - rb0);
-    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-      const int r = id & 31, c = id >> 5;
-      Ls[r][c] = (r < w && c < w) ? L[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
-      Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < ncol) {
-      const int c = threadIdx.x;
-      for (int r = 0; r < w; ++r) {
-        double s = Xs[r][c];
-        for (int l = 0; l < r; ++l) s -= Ls[r][l] * Xs[l][c];
-        Xs[r][c] = s / Ls[r][r];
-      }
-    }
-    __syncthreads();
-    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-      const int r = id & 31, c = id >> 5;
-      if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
-    }
-    for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
-      double acc[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-      for (int l = 0; l < w; ++l) {
-        const double lv = L[(size_t)(rb0 + l) * nb + r];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < ncol) X[(size_t)c * nb + r] -= acc[c];
-    }
-    __syncthreads();
-  }
-}
-
-// dense: A_ik <- A_ik L_kk^{-T}, columns c0 .. c0+w of every row (row per thread)
-__global__ void k_trsm_d_panel(TlrView v, const int2* __restrict__ items, int c0, int w) {
-  __shared__ double Ls[32][33];
-  const int2 it = items[blockIdx.y];
-  const int nb = v.nb;
-  const double* L = diagT(v, it.y);
-  double* A = tileA(v, dtile_index(it.x, it.y));
-  for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-    const int r = id & 31, c = id >> 5;
-    Ls[r][c] = (r < w && c < w) ? L[(size_t)(c0 + c) * nb + c0 + r] : 0.0;
-  }
-  __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nb) return;
-  double xr[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) xr[c] = (c < w) ? A[(size_t)(c0 + c) * nb + r] : 0.0;
-#pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    if (c < w) {
-      double s = xr[c];
-#pragma unroll
-      for (int l = 0; l < 32; ++l)
-        if (l < c) s -= xr[l] * Ls[c][l];
-      xr[c] = s / Ls[c][c];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c < w) A[(size_t)(c0 + c) * nb + r] = xr[c];
-}
-
-// dense: A_ik[:, c1:] -= A_ik[:, c0:c1] L_kk[c1:, c0:c1]^T
-__global__ void k_trsm_d_trail(TlrView v, const int2* __restrict__ items, int c0, int w) {
-  const int2 it = items[blockIdx.y];
-  const int nb = v.nb, c1 = c0 + w;
-  const double* L = diagT(v, it.y);
-  double* A = tileA(v, dtile_index(it.x, it.y));
-  cta_gemm_blocks(nb, nb - c1, w, -1.0, A + (size_t)c0 * nb, nb, 0, L + (size_t)c0 * nb + c1, nb, 1, 1.0,
-                  A + (size_t)c1 * nb, nb, blockIdx.x, gridDim.x, 0);
-}
-
 // ----------------------------------------------------------------- SYRK
 // descriptor of D_i -= L_ik L_ik^T for i = i0 + blockIdx.x (one CTA per i)
 __global__ void k_syrk_prep(TlrView v, int k, int i0, GemmDesc* __restrict__ desc, double* __restrict__ ws,
@@ -247,31 +153,25 @@ int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t
   return TLR_OK;
 }
 
+// L_ik = A_ik L_kk^{-T}: low rank V <- L_kk^{-1} V, dense A <- A L_kk^{-T}, by GEMM with the explicit L_kk^{-1}
+__global__ void k_eye_f(double* __restrict__ X, int nb) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
+       e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = ((e % nb) == (e / nb)) ? 1.0 : 0.0;
+}
+
 static int launch_trsm(tlr_ctx* h, int k, cudaStream_t s) {
   const TlrView v = view_of(h);
   const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
   const int nlr = (int)(off[PH_TRSM_LR + 1] - off[PH_TRSM_LR]);
-  if (nlr > 0) {
-    dim3 grid((h->kcap + 31) / 32, nlr);
-    k_trsm_lr<<<grid, 256, 0, s>>>(v, h->d_list + off[PH_TRSM_LR]);
-    TLR_LAUNCH_CHECK();
-  }
   const int nd = (int)(off[PH_TRSM_D + 1] - off[PH_TRSM_D]);
-  if (nd > 0) {
-    const int2* it = h->d_list + off[PH_TRSM_D];
-    for (int c0 = 0; c0 < h->nb; c0 += 32) {
-      const int w = h->nb - c0 < 32 ? h->nb - c0 : 32;
-      k_trsm_d_panel<<<dim3((h->nb + 127) / 128, nd), 128, 0, s>>>(v, it, c0, w);
-      TLR_LAUNCH_CHECK();
-      const int c1 = c0 + w;
-      if (c1 < h->nb) {
-        const int mb = (h->nb + 63) / 64, nbk = (h->nb - c1 + 63) / 64;
-        k_trsm_d_trail<<<dim3(mb * nbk, nd), 256, 0, s>>>(v, it, c0, w);
-        TLR_LAUNCH_CHECK();
-      }
-    }
-  }
-  return TLR_OK;
+  if (nlr + nd == 0) return TLR_OK;
+  k_eye_f<<<256, 256, 0, s>>>(h->dinv, h->nb);
+  TLR_LAUNCH_CHECK();
+  int rc = tops_trop_raw(h->D + (size_t)k * h->nb * h->nb, h->nb, h->dinv, h->nb, TOP_SOLVE, 1.0, s);
+  if (rc) return rc;
+  return tops_trmul(h, v, h->dinv, 0, h->d_list + off[PH_TRSM_LR], nlr, 1, 1, h->d_list + off[PH_TRSM_D], nd, 1, 1.0,
+                    s);
 }
 
 static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {

@@ -288,19 +288,21 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
     auto L = [&](int ph) { return h->d_zlist + off[ph]; };
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
-    { PhaseScope ps("trtri.col", s);
-      ZTRY(tops_trop(h, z, k, L(ZP_T1_LR), N(ZP_T1_LR), 1, L(ZP_T1_D), N(ZP_T1_D), 1, TOP_SOLVE_T, -1.0, s)); }
+    double* Mi = h->dinv;  // L_kk^{-1}, applied by GEMM in steps 1 and 3, stored in step 4
+    { PhaseScope ps("trtri.diag", s);
+      k_eye<<<256, 256, 0, s>>>(Mi, nb);
+      TLR_LAUNCH_CHECK();
+      ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, Mi, nb, TOP_SOLVE, 1.0, s)); }
+    { PhaseScope ps("trtri.col", s);  // A_ik <- -A_ik L_kk^{-1}: V <- -L_kk^{-T} V
+      ZTRY(tops_trmul(h, z, Mi, 1, L(ZP_T1_LR), N(ZP_T1_LR), 1, 0, L(ZP_T1_D), N(ZP_T1_D), 1, -1.0, s)); }
     { PhaseScope ps("trtri.update", s);
       ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s)); }
     { PhaseScope ps("trtri.update_dd", s);
       ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), N(ZP_T2_DD), eps, d_zeta, 0.5, s)); }
-    { PhaseScope ps("trtri.row", s);
-      ZTRY(tops_trop(h, z, k, L(ZP_T3_LR), N(ZP_T3_LR), 0, L(ZP_T3_D), N(ZP_T3_D), 0, TOP_SOLVE, 1.0, s)); }
-    PhaseScope ps_d("trtri.diag", s);
-    k_eye<<<256, 256, 0, s>>>(X, nb);
-    TLR_LAUNCH_CHECK();
-    ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, X, nb, TOP_SOLVE, 1.0, s));
-    k_copy<<<256, 256, 0, s>>>(X, h->Dz + (size_t)k * nn, (int64_t)nn);
+    { PhaseScope ps("trtri.row", s);  // A_kj <- L_kk^{-1} A_kj: U <- L_kk^{-1} U
+      ZTRY(tops_trmul(h, z, Mi, 0, L(ZP_T3_LR), N(ZP_T3_LR), 0, 0, L(ZP_T3_D), N(ZP_T3_D), 0, 1.0, s)); }
+    PhaseScope ps_d("trtri.store", s);
+    k_copy<<<256, 256, 0, s>>>(Mi, h->Dz + (size_t)k * nn, (int64_t)nn);
     TLR_LAUNCH_CHECK();
   }
   // ---- LAUUM
@@ -326,8 +328,9 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
       ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s)); }
     { PhaseScope ps("lauum.update_dd", s);
       ZTRY(tops_update_dd(h, z, ALG_LAUUM, k, L(ZP_L2_DD), N(ZP_L2_DD), eps, d_zeta, 1.0, s)); }
-    { PhaseScope ps("lauum.row", s);
-      ZTRY(tops_trop(h, z, k, L(ZP_L3_LR), N(ZP_L3_LR), 0, L(ZP_L3_D), N(ZP_L3_D), 0, TOP_MUL_T, 1.0, s)); }
+    { PhaseScope ps("lauum.row", s);  // A_kn <- A_kk^T A_kn
+      ZTRY(tops_trmul(h, z, h->Dz + (size_t)k * nn, 1, L(ZP_L3_LR), N(ZP_L3_LR), 0, 1, L(ZP_L3_D), N(ZP_L3_D), 0, 1.0,
+                      s)); }
     PhaseScope ps_d("lauum.diag", s);
     // D_k <- D_k^T D_k via the workspace
     GemmGen g;

@@ -279,40 +279,11 @@ __device__ void cta_trop32(const double* __restrict__ T, int nb, double* __restr
   }
 }
 
-__global__ void k_trop_tiles(TlrView v, int kdiag, const int2* __restrict__ items, int which, int op, double alpha) {
-  const int2 it = items[blockIdx.y];
-  const int64_t t = dtile_index(it.x, it.y);
-  const int nb = v.nb;
-  double* X;
-  int ncols;
-  if (which == 2) { X = tileA(v, t); ncols = nb; }
-  else { X = which == 0 ? tileU(v, t) : tileV(v, t); ncols = v.rank[t]; }
-  const int cb = blockIdx.x * 32;
-  if (cb >= ncols) return;
-  cta_trop32(diagT(v, kdiag), nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
-}
-
 __global__ void k_trop_raw(const double* __restrict__ T, int nb, double* __restrict__ X, int ncols, int op,
                            double alpha) {
   const int cb = blockIdx.x * 32;
   if (cb >= ncols) return;
   cta_trop32(T, nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
-}
-
-// in-place transpose of listed dense tiles
-__global__ void k_transpose_tiles(TlrView v, const int2* __restrict__ items) {
-  const int2 it = items[blockIdx.y];
-  double* A = tileA(v, dtile_index(it.x, it.y));
-  const int nb = v.nb;
-  const int64_t npair = (int64_t)nb * (nb - 1) / 2;
-  for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < npair;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    int a, b;
-    decode_lower(id, &a, &b);  // a > b
-    const double t = A[(size_t)b * nb + a];
-    A[(size_t)b * nb + a] = A[(size_t)a * nb + b];
-    A[(size_t)a * nb + b] = t;
-  }
 }
 
 // LAUUM step: D_n += A_kn^T A_kn, n = 0 .. k-1 (one CTA per n builds the descriptor)
@@ -383,6 +354,41 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
   __syncthreads();
   const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, tileU(v, tt), tileV(v, tt), st, tt, sh, shi);
   if (threadIdx.x == 0) v.rank[tt] = kr;
+}
+
+// descriptors of X_tmp = alpha op(M) X (or alpha A op(M)) for tile items
+__global__ void k_trmul_desc(TlrView v, const double* __restrict__ M, int transM, const int2* __restrict__ items,
+                             int cnt, int which, int dense_right, double alpha, double* __restrict__ tmp,
+                             size_t tmp_elems, GemmGen* __restrict__ desc, double** __restrict__ dst) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const int2 it = items[q];
+  const int64_t t = dtile_index(it.x, it.y);
+  const int nb = v.nb;
+  GemmGen g;
+  g.C = tmp + (size_t)q * tmp_elems; g.ldc = nb; g.lda = nb; g.ldb = nb; g.alpha = alpha; g.beta = 0.0;
+  g.lower = 0; g.m = nb; g.k = nb;
+  double* X;
+  if (which == 2) {
+    X = tileA(v, t);
+    g.n = nb;
+    if (dense_right) { g.A = X; g.tA = 0; g.B = M; g.tB = transM; }
+    else { g.A = M; g.tA = transM; g.B = X; g.tB = 0; }
+  } else {
+    X = which == 0 ? tileU(v, t) : tileV(v, t);
+    g.n = v.rank[t];
+    g.A = M; g.tA = transM; g.B = X; g.tB = 0;
+  }
+  desc[q] = g;
+  dst[q] = X;
+}
+
+__global__ void k_copy_back(const GemmGen* __restrict__ desc, double* const* __restrict__ dst) {
+  const GemmGen g = desc[blockIdx.y];
+  double* X = dst[blockIdx.y];
+  const int64_t cnt = (int64_t)g.m * g.n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    X[e] = g.C[e];
 }
 
 int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
@@ -478,21 +484,30 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   return TLR_OK;
 }
 
-int tops_trop(tlr_ctx* h, const TlrView& v, int kdiag, const int2* d_lr, int n_lr, int which, const int2* d_dn,
-              int n_dn, int dense_right, int op, double alpha, cudaStream_t s) {
-  if (n_lr > 0) {
-    k_trop_tiles<<<dim3((h->kcap + 31) / 32, n_lr), 256, 0, s>>>(v, kdiag, d_lr, which, op, alpha);
-    TLR_LAUNCH_CHECK();
-  }
-  if (n_dn > 0) {
-    if (dense_right) {
-      k_transpose_tiles<<<dim3(64, n_dn), 256, 0, s>>>(v, d_dn);
+int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
+               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s) {
+  const size_t nb = h->nb;
+  const size_t gd = (sizeof(GemmGen) + 7) / 8 + 1;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int total = pass == 0 ? n_lr : n_dn;
+    const int2* items = pass == 0 ? d_lr : d_dn;
+    if (total <= 0) continue;
+    const size_t tmp_elems = pass == 0 ? nb * (size_t)h->kcap : nb * nb;
+    const int ncols_max = pass == 0 ? h->kcap : h->nb;
+    const int chunk = chunk_of(h, tmp_elems + gd, 64);
+    if (chunk < 1) return TLR_ERR_OOM;
+    for (int q0 = 0; q0 < total; q0 += chunk) {
+      const int cnt = total - q0 < chunk ? total - q0 : chunk;
+      GemmGen* desc = (GemmGen*)h->scratch;
+      double** dst = (double**)(h->scratch + (size_t)cnt * (gd - 1) + 8);
+      double* tmp = h->scratch + (size_t)cnt * gd + 16;
+      k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, pass == 0 ? transM : transM_dense, items + q0, cnt,
+                                                      pass == 0 ? which : 2, dense_right, alpha, tmp, tmp_elems,
+                                                      desc, dst);
       TLR_LAUNCH_CHECK();
-    }
-    k_trop_tiles<<<dim3((h->nb + 31) / 32, n_dn), 256, 0, s>>>(v, kdiag, d_dn, 2, op, alpha);
-    TLR_LAUNCH_CHECK();
-    if (dense_right) {
-      k_transpose_tiles<<<dim3(64, n_dn), 256, 0, s>>>(v, d_dn);
+      int rc = tops_gemm(desc, cnt, h->nb, ncols_max, s);
+      if (rc) return rc;
+      k_copy_back<<<dim3(32, cnt), 256, 0, s>>>(desc, dst);
       TLR_LAUNCH_CHECK();
     }
   }

@@ -28,10 +28,12 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
 // low-rank targets whose two sources are both dense (materialise, ACA, recompress)
 int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
                    const double* d_zeta, double zpow, cudaStream_t s);
-// X <- alpha op(T_kdiag) X on listed tiles: low-rank ones on U (which = 0) or V (which = 1), dense ones on A
-// (transposed first and back when dense_right: A <- (alpha op(T) A^T)^T)
-int tops_trop(tlr_ctx* h, const TlrView& v, int kdiag, const int2* d_lr, int n_lr, int which, const int2* d_dn,
-              int n_dn, int dense_right, int op, double alpha, cudaStream_t s);
+// Triangular tile transforms by multiplication with an explicit nb x nb matrix M
+// (for instance L_kk^{-1}): low-rank tiles U <- alpha op(M) U (which 0) or V <- alpha op(M) V (which 1);
+// dense tiles A <- alpha op(M) A, or A <- alpha A op(M) when dense_right.  op(M) = M^T when transM.
+// Batched multi-CTA GEMMs into a workspace, then copied back.
+int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
+               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s);
 // X <- alpha op(T) X for a raw nb x ncols matrix
 int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s);
 // batched general GEMM from a device descriptor array
