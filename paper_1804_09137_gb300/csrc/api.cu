@@ -134,9 +134,12 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->dinv};
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->dinv, h->d_ctr, h->scratch_dd, h->msave};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   free(h->kind);
   free(h->h_list);
   free(h->plan_off);
@@ -214,6 +217,7 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->tab, TAB_ELEMS);
   rc |= dmalloc(&h->dinv, nb * nb);
   rc |= dmalloc(&h->d_stat, 4);
+  rc |= dmalloc(&h->d_ctr, 4);
   rc |= dmalloc(&h->d_vec, 4 * (size_t)cnp);
   h->red_len = 2 * h->cap_nt + 64;
   rc |= dmalloc(&h->d_red, h->red_len);
@@ -642,9 +646,17 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
           if (h->kind[tile_index(i, k)] == want) L.push_back(make_int2(i, k));
       } else {
         const char want = ph == PH_UPD_D;
+        const size_t b = L.size();
         for (int i = k + 2; i < nt; ++i)
           for (int j = k + 1; j < i; ++j)
             if (h->kind[tile_index(i, j)] == want) L.push_back(make_int2(i, j));
+        if (ph == PH_UPD_LR) {
+          // longest items first (the recompression cost grows with the square of
+          // the concatenated rank), so that a launch does not end on a long tail
+          auto r = [&](int p, int q) { return h->kind[tile_index(p, q)] ? h->nb : rk[tile_index(p, q)]; };
+          auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(t.y, k)); return K * K; };
+          std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
+        }
       }
     }
   }

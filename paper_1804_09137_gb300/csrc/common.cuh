@@ -37,13 +37,8 @@
 #define ZP_T2_D 3
 #define ZP_T3_LR 4
 #define ZP_T3_D 5
-#define ZP_L2_LR 6
-#define ZP_L2_D 7
-#define ZP_L3_LR 8
-#define ZP_L3_D 9
-#define ZP_T2_DD 10
-#define ZP_L2_DD 11
-#define ZPH 12
+#define ZP_T2_DD 6
+#define ZPH 7
 
 #define ST_CODE 0
 #define ST_INFO 1
@@ -105,12 +100,21 @@ struct tlr_ctx {
   size_t item_elems;  // workspace per low-rank update item
   int items_per_launch;
   long long* d_stat;  // status words
+  int* d_ctr;         // item counter of the persistent update kernel
   double* d_vec;      // 4 vectors of npad
   double* d_red;      // reduction partials
   int red_len;
   int state;          // 0 created, 1 generated, 2 compressed, 3 factored
   int tab_valid;
   cudaStream_t last_stream;
+  // second stream of the inverse (dense x dense products overlap the other updates of a step)
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
+  double* scratch_dd;
+  size_t scratch_dd_elems;
+  // copy of the inverse's dense sources (diagonal and dense tiles) read by LAUUM
+  double* msave;
+  size_t msave_elems;
 };
 
 // ---------------------------------------------------------------- helpers

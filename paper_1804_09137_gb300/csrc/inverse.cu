@@ -6,19 +6,16 @@
 //   2. A_ij <- A_ij + A_ik A_kj                i > k > j
 //   3. A_kj <- L_kk^{-1} A_kj                  j < k  (low rank: U <- L_kk^{-1} U)
 //   4. A_kk <- L_kk^{-1}
-// then right-looking tile LAUUM (Z = M^T M, lower part), step k:
-//   1. A_nn <- A_nn + A_kn^T A_kn              n < k
-//   2. A_mn <- A_mn + A_km^T A_kn              n < m < k
-//   3. A_kn <- A_kk^T A_kn                     n < k  (low rank: U <- M_kk^T U)
-//   4. A_kk <- A_kk^T A_kk
+// then left-looking tile LAUUM (Z = M^T M, lower part, out of place):
+//   Z_mn = sum_{k >= m} M_km^T M_kn           m >= n
+// with every tile of Z one GEMM over the stacked thin factors of its products.
 // TRTRI keeps L^{-1} in tile low-rank form (its tiles are sources of later
 // products) and recompresses at tau_M = eps sqrt(zeta), zeta = max_a 1 / L_aa^2
 // (the scale of L^{-1} squared), so the truncation is relative to the size of
 // L^{-1} as eps is to Sigma; a dense x dense product landing on a low-rank tile
 // is formed by GEMM and recompressed.  Sigma^{-1}'s tiles are never sources:
-// only the gradient pass reads them, so LAUUM accumulates every off-diagonal
-// tile densely (no truncation): a row of L^{-1} is expanded to dense right
-// after its last use as a source.
+// only the gradient pass reads them, so LAUUM forms every tile densely (no
+// truncation).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -85,23 +82,6 @@ __global__ void k_copy_to_z(TlrView f, TlrView z, int64_t ntiles) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) z.rank[t] = kr;
   }
-}
-
-// tiles (r, n), n < r, still low rank: A = U V^T into their own dense slot (slot = tile index)
-__global__ void k_expand_row(TlrView z, int r) {
-  const int n = blockIdx.y;
-  const int64_t t = dtile_index(r, n);
-  if (z.dslot[t] >= 0) return;
-  const int nb = z.nb;
-  cta_gemm_df_blocks(nb, nb, z.rank[t], 1.0, tileU(z, t), nb, 0, tileV(z, t), nb, 1, 0.0,
-                     z.dpool + (size_t)t * nb * nb, nb, blockIdx.x, gridDim.x, 0);
-}
-
-__global__ void k_mark_row_dense(TlrView z, int r) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= r) return;
-  const int64_t t = dtile_index(r, n);
-  z.dslot[t] = (int)t;
 }
 
 __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
@@ -174,22 +154,27 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
         case ZP_T1_LR: case ZP_T1_D:
           for (int i = k + 1; i < nt; ++i) if (kd(i, k) == want) L.push_back(make_int2(i, k));
           break;
-        case ZP_T2_LR: case ZP_T2_D: case ZP_T2_DD:
+        case ZP_T2_LR: case ZP_T2_D: case ZP_T2_DD: {
+          const size_t b = L.size();
           for (int i = k + 1; i < nt; ++i)
             for (int j = 0; j < k; ++j) {
               const bool dd = kd(i, k) && kd(k, j);
               if (ph == ZP_T2_D ? kd(i, j) == 1 : (kd(i, j) == 0 && dd == (ph == ZP_T2_DD)))
                 L.push_back(make_int2(i, j));
             }
+          if (ph == ZP_T2_LR) {
+            // longest recompressions first (cost ~ square of the concatenated rank,
+            // estimated from the factor's ranks), so a launch does not end on a tail
+            auto r = [&](int p, int q) { return kd(p, q) ? h->nb : std::max(rk[tile_index(p, q)], 1); };
+            auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(k, t.y)); return K * K; };
+            std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
+          }
           break;
-        case ZP_T3_LR: case ZP_T3_D: case ZP_L3_LR: case ZP_L3_D:
+        }
+        case ZP_T3_LR: case ZP_T3_D:
           for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
           break;
-        case ZP_L2_D:  // LAUUM targets are dense (their rows were expanded before)
-          for (int m = 1; m < k; ++m)
-            for (int n2 = 0; n2 < m; ++n2) L.push_back(make_int2(m, n2));
-          break;
-        case ZP_L2_LR: case ZP_L2_DD:
+        default:  // the LAUUM phases have no per-step lists (left-looking LAUUM)
           break;
       }
     }
@@ -199,10 +184,9 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     int64_t cnt[ZPH] = {0};
     for (int k = 0; k < nt; ++k)
       for (int ph = 0; ph < ZPH; ++ph) cnt[ph] += off[(size_t)k * ZPH + ph + 1] - off[(size_t)k * ZPH + ph];
-    fprintf(stderr, "tlr inverse plan: dense %d; items T1 %lld/%lld T2 %lld/%lld/dd %lld T3 %lld/%lld L2 %lld/%lld/dd %lld L3 %lld/%lld\n",
-            nd, (long long)cnt[ZP_T1_LR], (long long)cnt[ZP_T1_D], (long long)cnt[ZP_T2_LR], (long long)cnt[ZP_T2_D],
-            (long long)cnt[ZP_T2_DD], (long long)cnt[ZP_T3_LR], (long long)cnt[ZP_T3_D], (long long)cnt[ZP_L2_LR],
-            (long long)cnt[ZP_L2_D], (long long)cnt[ZP_L2_DD], (long long)cnt[ZP_L3_LR], (long long)cnt[ZP_L3_D]);
+    fprintf(stderr, "tlr inverse plan: dense %d; items T1 %lld/%lld T2 %lld/%lld/dd %lld T3 %lld/%lld\n", nd,
+            (long long)cnt[ZP_T1_LR], (long long)cnt[ZP_T1_D], (long long)cnt[ZP_T2_LR], (long long)cnt[ZP_T2_D],
+            (long long)cnt[ZP_T2_DD], (long long)cnt[ZP_T3_LR], (long long)cnt[ZP_T3_D]);
   }
   const int64_t len = std::max<int64_t>((int64_t)L.size(), 1);
   if (len > h->zlist_cap) {
@@ -252,6 +236,286 @@ static int ensure_z(tlr_ctx* h) {
     if (rc_ != TLR_OK) return rc_; \
   } while (0)
 
+struct CopySeg {
+  const double* src;
+  double* dst;
+  int64_t count;
+};
+
+__global__ void k_seg_copy(const CopySeg* __restrict__ segs) {
+  const CopySeg c = segs[blockIdx.y];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < c.count; e += (int64_t)gridDim.x * blockDim.x)
+    c.dst[e] = c.src[e];
+}
+
+__global__ void k_mark_all_dense(int* __restrict__ dslot, int64_t T) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x)
+    dslot[t] = (int)t;
+}
+
+static int seg_copy(const CopySeg* d_segs, int64_t n, cudaStream_t s) {
+  for (int64_t c0 = 0; c0 < n; c0 += 65535) {
+    const int cnt = (int)std::min<int64_t>(65535, n - c0);
+    k_seg_copy<<<dim3(32, cnt), 256, 0, s>>>(d_segs + c0);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+// Left-looking LAUUM: every tile of Z = M^T M (M = L^{-1} after TRTRI, lower) at once,
+//   Z_mn = sum_{k >= m} M_km^T M_kn,  m >= n  (M_mm the inverse diagonal tile).
+// A product with a low-rank factor is a pair of thin panels, Z_mn += A B^T:
+//   both low rank:  G = U_km^T U_kn;  A = V_km, B = V_kn G^T  or  A = V_km G, B = V_kn  (thinner side)
+//   M_km dense:     A = M_km^T U_kn,  B = V_kn
+//   M_kn dense:     A = V_km,         B = M_kn^T U_km
+// The pairs of one tile are stacked along the depth, so each tile of Z is one GEMM
+// of depth sum(rank) written once; dense x dense products are added afterwards, one
+// GEMM per tile and launch.  Z overwrites the dense sources' slots, so those (and the
+// diagonal) are read from a copy.  Workspace: h->scratch (descriptors, G, panels).
+static int lauum_left(tlr_ctx* h, cudaStream_t s) {
+  const int nt = h->nt, nb = h->nb;
+  const int64_t T = h->ntiles;
+  const size_t nn = (size_t)nb * nb;
+  std::vector<int> rk(std::max<int64_t>(T, 1), 0);
+  if (T > 0) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(rk.data(), h->rankz, T * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  const char* K = h->kindz;
+  std::vector<int> dix(std::max<int64_t>(T, 1), -1);
+  int nd = 0;
+  for (int64_t t = 0; t < T; ++t)
+    if (K[t]) dix[t] = nd++;
+  const size_t msave_want = (size_t)(nt + nd) * nn;
+  if (msave_want > h->msave_elems) {
+    if (h->msave) cudaFree(h->msave);
+    h->msave = nullptr;
+    h->msave_elems = 0;
+    if (cudaMalloc((void**)&h->msave, msave_want * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return TLR_ERR_OOM;
+    }
+    h->msave_elems = msave_want;
+  }
+  auto isD = [&](int p, int q) { return p == q || K[tile_index(p, q)]; };
+  auto Msrc = [&](int p, int q) -> const double* {
+    return p == q ? h->msave + (size_t)p * nn : h->msave + (size_t)(nt + dix[tile_index(p, q)]) * nn;
+  };
+  auto Uof = [&](int p, int q) -> const double* { return h->Uz + (size_t)tile_index(p, q) * nb * h->kcap; };
+  auto Vof = [&](int p, int q) -> const double* { return h->Vz + (size_t)tile_index(p, q) * nb * h->kcap; };
+  auto rnk = [&](int p, int q) { return rk[tile_index(p, q)]; };
+  auto Zdst = [&](int m, int n) -> double* {
+    return m == n ? h->Dz + (size_t)n * nn : h->dpoolz + (size_t)tile_index(m, n) * nn;
+  };
+  static_assert(sizeof(GemmGen) % 8 == 0 && sizeof(CopySeg) % 8 == 0, "descriptor regions are 8-byte padded");
+  const size_t gd = sizeof(GemmGen) / 8, cd = sizeof(CopySeg) / 8;
+  {  // dense sources and diagonal tiles into the copy
+    std::vector<CopySeg> cs;
+    cs.push_back({h->Dz, h->msave, (int64_t)nt * (int64_t)nn});
+    for (int64_t t = 0; t < T; ++t)
+      if (K[t]) cs.push_back({h->dpoolz + (size_t)t * nn, h->msave + (size_t)(nt + dix[t]) * nn, (int64_t)nn});
+    if (cs.size() * cd > h->scratch_elems) return TLR_ERR_OOM;
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->scratch, cs.data(), cs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, s));
+    ZTRY(seg_copy((const CopySeg*)h->scratch, (int64_t)cs.size(), s));
+  }
+  // targets (m, n), m >= n, and their depth
+  std::vector<int2> tg;
+  std::vector<int64_t> depth, gel;
+  for (int m = 0; m < nt; ++m)
+    for (int n = 0; n <= m; ++n) {
+      int64_t d = 0, g = 0;
+      for (int k = m; k < nt; ++k) {
+        const bool dm = isD(k, m), dn = isD(k, n);
+        if (dm && dn) continue;
+        if (!dm && !dn) {
+          const int a = rnk(k, m), c = rnk(k, n);
+          if (a == 0 || c == 0) continue;
+          d += std::min(a, c);
+          g += (int64_t)a * c;
+        } else {
+          d += dm ? rnk(k, n) : rnk(k, m);
+        }
+      }
+      tg.push_back(make_int2(m, n));
+      depth.push_back(d);
+      gel.push_back(g);
+    }
+  const size_t budget = h->scratch_elems;
+  size_t b0 = 0;
+  std::vector<char> host;
+  while (b0 < tg.size()) {
+    // greedy batch: descriptors, copy segments, G and both panels within the workspace
+    size_t b1 = b0, need = 64;
+    while (b1 < tg.size()) {
+      const int m = tg[b1].x;
+      const size_t per = (size_t)(nt - m) * (3 * gd + cd + 2) + gd + (size_t)gel[b1] + 2 * (size_t)nb * depth[b1] + 8;
+      if (b1 > b0 && need + per > budget) break;
+      need += per;
+      ++b1;
+    }
+    if (need > budget) return TLR_ERR_OOM;
+    std::vector<GemmGen> g1, g1b, g2, gbig;
+    std::vector<std::vector<GemmGen>> gdd;
+    std::vector<CopySeg> cs;
+    // region sizes first (pointers into the workspace below)
+    size_t n_g1 = 0, n_g1b = 0, n_g2 = 0, n_cs = 0, g_tot = 0, p_tot = 0;
+    for (size_t q = b0; q < b1; ++q) {
+      const int m = tg[q].x, n = tg[q].y;
+      for (int k = m; k < nt; ++k) {
+        const bool dm = isD(k, m), dn = isD(k, n);
+        if (dm && dn) continue;
+        if (!dm && !dn) {
+          if (rnk(k, m) == 0 || rnk(k, n) == 0) continue;
+          ++n_g1; ++n_g2; ++n_cs;
+        } else {
+          if ((dm ? rnk(k, n) : rnk(k, m)) == 0) continue;
+          ++n_g1b; ++n_cs;
+        }
+      }
+      g_tot += gel[q];
+      p_tot += 2 * (size_t)nb * depth[q];
+    }
+    const size_t nbig = b1 - b0;
+    double* base = h->scratch;
+    GemmGen* dg1 = (GemmGen*)base;
+    GemmGen* dg1b = dg1 + n_g1;
+    GemmGen* dg2 = dg1b + n_g1b;
+    GemmGen* dbig = dg2 + n_g2;
+    GemmGen* ddd = dbig + nbig;
+    size_t n_dd = 0;
+    for (size_t q = b0; q < b1; ++q)
+      for (int k = tg[q].x; k < nt; ++k) n_dd += isD(k, tg[q].x) && isD(k, tg[q].y);
+    CopySeg* dcs = (CopySeg*)(ddd + n_dd);
+    double* Gw = base + ((size_t)(n_g1 + n_g1b + n_g2 + nbig + n_dd) * gd + n_cs * cd + 8);
+    double* Pw = Gw + g_tot + 8;
+    if ((size_t)(Pw + p_tot - base) > budget) return TLR_ERR_OOM;
+    GemmGen z0;
+    memset(&z0, 0, sizeof(z0));
+    z0.alpha = 1.0; z0.beta = 0.0;
+    auto gemm = [&](int mm, int nn2, int kk, const double* A, int lda, int tA, const double* B, int ldb, int tB,
+                    double* C, int ldc, double beta) {
+      GemmGen g = z0;
+      g.m = mm; g.n = nn2; g.k = kk; g.A = A; g.lda = lda; g.tA = tA; g.B = B; g.ldb = ldb; g.tB = tB;
+      g.C = C; g.ldc = ldc; g.beta = beta;
+      return g;
+    };
+    int mx_g = 1, mx_r = 1;
+    size_t goff = 0;
+    double* P = Pw;
+    for (size_t q = b0; q < b1; ++q) {
+      const int m = tg[q].x, n = tg[q].y;
+      double* Ap = P;
+      double* Bp = P + (size_t)nb * depth[q];
+      int64_t off = 0;
+      int r_dd = 0;
+      for (int k = m; k < nt; ++k) {
+        const bool dm = isD(k, m), dn = isD(k, n);
+        if (dm && dn) {
+          if ((int)gdd.size() <= r_dd) gdd.emplace_back();
+          gdd[r_dd++].push_back(gemm(nb, nb, nb, Msrc(k, m), nb, 1, Msrc(k, n), nb, 0, Zdst(m, n), nb, 1.0));
+          continue;
+        }
+        if (!dm && !dn) {
+          const int a = rnk(k, m), c = rnk(k, n);
+          if (a == 0 || c == 0) continue;
+          double* G = Gw + goff;
+          goff += (size_t)a * c;
+          g1.push_back(gemm(a, c, nb, Uof(k, m), nb, 1, Uof(k, n), nb, 0, G, a, 0.0));
+          mx_g = std::max(mx_g, std::max(a, c));
+          if (a <= c) {  // A = V_km, B = V_kn G^T (depth a)
+            cs.push_back({Vof(k, m), Ap + (size_t)off * nb, (int64_t)nb * a});
+            g2.push_back(gemm(nb, a, c, Vof(k, n), nb, 0, G, a, 1, Bp + (size_t)off * nb, nb, 0.0));
+            off += a;
+            mx_r = std::max(mx_r, a);
+          } else {  // A = V_km G, B = V_kn (depth c)
+            g2.push_back(gemm(nb, c, a, Vof(k, m), nb, 0, G, a, 0, Ap + (size_t)off * nb, nb, 0.0));
+            cs.push_back({Vof(k, n), Bp + (size_t)off * nb, (int64_t)nb * c});
+            off += c;
+            mx_r = std::max(mx_r, c);
+          }
+        } else if (dm) {  // A = M_km^T U_kn, B = V_kn
+          const int c = rnk(k, n);
+          if (c == 0) continue;
+          g1b.push_back(gemm(nb, c, nb, Msrc(k, m), nb, 1, Uof(k, n), nb, 0, Ap + (size_t)off * nb, nb, 0.0));
+          cs.push_back({Vof(k, n), Bp + (size_t)off * nb, (int64_t)nb * c});
+          off += c;
+          mx_r = std::max(mx_r, c);
+        } else {  // A = V_km, B = M_kn^T U_km
+          const int a = rnk(k, m);
+          if (a == 0) continue;
+          cs.push_back({Vof(k, m), Ap + (size_t)off * nb, (int64_t)nb * a});
+          g1b.push_back(gemm(nb, a, nb, Msrc(k, n), nb, 1, Uof(k, m), nb, 0, Bp + (size_t)off * nb, nb, 0.0));
+          off += a;
+          mx_r = std::max(mx_r, a);
+        }
+      }
+      if (off != depth[q]) return TLR_ERR_STATE;
+      gbig.push_back(gemm(nb, nb, (int)off, Ap, nb, 0, Bp, nb, 1, Zdst(m, n), nb, 0.0));
+      P += 2 * (size_t)nb * depth[q];
+    }
+    // one upload of descriptors and copy segments, in the order of the device layout
+    std::vector<GemmGen> all;
+    all.reserve(g1.size() + g1b.size() + g2.size() + gbig.size() + n_dd);
+    all.insert(all.end(), g1.begin(), g1.end());
+    all.insert(all.end(), g1b.begin(), g1b.end());
+    all.insert(all.end(), g2.begin(), g2.end());
+    all.insert(all.end(), gbig.begin(), gbig.end());
+    std::vector<size_t> dd_off;
+    for (auto& r : gdd) { dd_off.push_back(all.size() - (g1.size() + g1b.size() + g2.size() + gbig.size())); all.insert(all.end(), r.begin(), r.end()); }
+    if (all.size() != n_g1 + n_g1b + n_g2 + nbig + n_dd || cs.size() != n_cs) return TLR_ERR_STATE;
+    host.resize(all.size() * gd * 8 + cs.size() * cd * 8);
+    memcpy(host.data(), all.data(), all.size() * sizeof(GemmGen));
+    // GemmGen and CopySeg regions are padded to 8-byte multiples (gd, cd doubles per entry)
+    memcpy(host.data() + all.size() * sizeof(GemmGen), cs.data(), cs.size() * sizeof(CopySeg));
+    TLR_CUDA_TRY(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    {
+      PhaseScope ps("lauum.prep", s);
+      ZTRY(seg_copy(dcs, (int64_t)n_cs, s));
+      ZTRY(tops_gemm(dg1, (int)n_g1, mx_g, mx_g, s));
+      ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
+      ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s));
+    }
+    {
+      PhaseScope ps("lauum.gemm", s);
+      ZTRY(tops_gemm(dbig, (int)nbig, nb, nb, s));
+    }
+    {
+      PhaseScope ps("lauum.dense_products", s);
+      for (size_t r = 0; r < gdd.size(); ++r) ZTRY(tops_gemm(ddd + dd_off[r], (int)gdd[r].size(), nb, nb, s));
+    }
+    b0 = b1;
+  }
+  if (T > 0) {
+    k_mark_all_dense<<<256, 256, 0, s>>>(h->dslotz, T);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
+
+// second stream, fork/join events and the dense x dense workspace for `items` items
+static int ensure_aux(tlr_ctx* h, int items) {
+  if (!h->aux) {
+    int lo = 0, hi = 0;
+    TLR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    TLR_CUDA_TRY(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi));
+    TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
+  const size_t want = (size_t)items * tops_dd_item_elems(h) + 16;
+  if (want > h->scratch_dd_elems) {
+    if (h->scratch_dd) cudaFree(h->scratch_dd);
+    h->scratch_dd = nullptr;
+    h->scratch_dd_elems = 0;
+    if (cudaMalloc((void**)&h->scratch_dd, want * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return TLR_ERR_OOM;
+    }
+    h->scratch_dd_elems = want;
+  }
+  return TLR_OK;
+}
+
+
 int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   ZTRY(ensure_z(h));
   if (!h->zplan_valid) ZTRY(zplan(h, s));
@@ -282,7 +546,13 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     }
   }
   const double eps = (h->opts.eps > 0 ? h->opts.eps : 0.0) * (h->opts.inv_scale > 0 ? h->opts.inv_scale : 0.1);
-  double* X = h->scratch;  // nb x nb workspace for the diagonal tiles
+  // dense x dense products run on a second stream next to the other updates of their step
+  int max_dd = 0;
+  for (int k = 0; k < nt; ++k) {
+    const int64_t* off = h->zoff + (size_t)k * ZPH;
+    max_dd = std::max(max_dd, (int)(off[ZP_T2_DD + 1] - off[ZP_T2_DD]));
+  }
+  if (max_dd > 0) ZTRY(ensure_aux(h, std::min(max_dd, 32)));
   // ---- TRTRI
   for (int k = 0; k < nt; ++k) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
@@ -295,10 +565,22 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
       ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, Mi, nb, TOP_SOLVE, 1.0, s)); }
     { PhaseScope ps("trtri.col", s);  // A_ik <- -A_ik L_kk^{-1}: V <- -L_kk^{-T} V
       ZTRY(tops_trmul(h, z, Mi, 1, L(ZP_T1_LR), N(ZP_T1_LR), 1, 0, L(ZP_T1_D), N(ZP_T1_D), 1, -1.0, s)); }
+    // the three target sets of step 2 are disjoint and read only column k and row k
+    const int ndd = N(ZP_T2_DD);
+    if (ndd > 0) {
+      TLR_CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+      TLR_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+      PhaseScope ps("trtri.update_dd", h->aux);
+      ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), ndd, eps, d_zeta, 0.5, h->aux, h->scratch_dd,
+                          h->scratch_dd_elems));
+    }
     { PhaseScope ps("trtri.update", s);
-      ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s)); }
-    { PhaseScope ps("trtri.update_dd", s);
-      ZTRY(tops_update_dd(h, z, ALG_TRTRI, k, L(ZP_T2_DD), N(ZP_T2_DD), eps, d_zeta, 0.5, s)); }
+      ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s,
+                       std::min(ndd, 32))); }
+    if (ndd > 0) {
+      TLR_CUDA_TRY(cudaEventRecord(h->ev_join, h->aux));
+      TLR_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    }
     { PhaseScope ps("trtri.row", s);  // A_kj <- L_kk^{-1} A_kj: U <- L_kk^{-1} U
       ZTRY(tops_trmul(h, z, Mi, 0, L(ZP_T3_LR), N(ZP_T3_LR), 0, 0, L(ZP_T3_D), N(ZP_T3_D), 0, 1.0, s)); }
     PhaseScope ps_d("trtri.store", s);
@@ -306,42 +588,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     TLR_LAUNCH_CHECK();
   }
   // ---- LAUUM
-  GemmGen* desc = (GemmGen*)(h->scratch + nn);
-  const int mb = (nb + 63) / 64;
-  auto expand_row = [&](int r) -> int {
-    if (r < 1) return TLR_OK;
-    k_expand_row<<<dim3(mb * mb, r), 256, 0, s>>>(z, r);
-    TLR_LAUNCH_CHECK();
-    k_mark_row_dense<<<(r + 127) / 128, 128, 0, s>>>(z, r);
-    TLR_LAUNCH_CHECK();
-    return TLR_OK;
-  };
-  for (int k = 0; k < nt; ++k) {
-    const int64_t* off = h->zoff + (size_t)k * ZPH;
-    auto L = [&](int ph) { return h->d_zlist + off[ph]; };
-    auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
-    // row k-1 was a source for the last time in step k-1: from now on its tiles are
-    // dense targets of Sigma^{-1}
-    { PhaseScope ps("lauum.expand", s); ZTRY(expand_row(k - 1)); }
-    { PhaseScope ps("lauum.herk", s); ZTRY(tops_herk_row(h, z, k, s)); }
-    { PhaseScope ps("lauum.update", s);
-      ZTRY(tops_update(h, z, ALG_LAUUM, k, L(ZP_L2_LR), N(ZP_L2_LR), L(ZP_L2_D), N(ZP_L2_D), eps, d_zeta, 1.0, s)); }
-    { PhaseScope ps("lauum.update_dd", s);
-      ZTRY(tops_update_dd(h, z, ALG_LAUUM, k, L(ZP_L2_DD), N(ZP_L2_DD), eps, d_zeta, 1.0, s)); }
-    { PhaseScope ps("lauum.row", s);  // A_kn <- A_kk^T A_kn
-      ZTRY(tops_trmul(h, z, h->Dz + (size_t)k * nn, 1, L(ZP_L3_LR), N(ZP_L3_LR), 0, 1, L(ZP_L3_D), N(ZP_L3_D), 0, 1.0,
-                      s)); }
-    PhaseScope ps_d("lauum.diag", s);
-    // D_k <- D_k^T D_k via the workspace
-    GemmGen g;
-    g.A = h->Dz + (size_t)k * nn; g.B = g.A; g.C = X; g.m = nb; g.n = nb; g.k = nb;
-    g.lda = nb; g.ldb = nb; g.ldc = nb; g.tA = 1; g.tB = 0; g.alpha = 1.0; g.beta = 0.0; g.lower = 0;
-    TLR_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, s));
-    ZTRY(tops_gemm(desc, 1, nb, nb, s));
-    k_copy<<<256, 256, 0, s>>>(X, h->Dz + (size_t)k * nn, (int64_t)nn);
-    TLR_LAUNCH_CHECK();
-  }
-  { PhaseScope ps("lauum.expand", s); ZTRY(expand_row(nt - 1)); }
+  { PhaseScope ps("lauum", s); ZTRY(lauum_left(h, s)); }
   h->zplan_valid = 0;  // the device tile kinds of Z changed: the next inverse re-plans
   return TLR_OK;
 }

@@ -6,6 +6,9 @@
 //   dense X and Y:  only into dense targets (the plans close the dense set).
 // Low-rank targets append the product's factors and recompress (one CTA per
 // tile); dense targets get C += P Q^T by batched 64 x 64-block GEMM.
+#include <algorithm>
+#include <atomic>
+
 #include "recompress.cuh"
 #include "tileops.h"
 
@@ -39,17 +42,13 @@ __device__ __forceinline__ Opnd operand(const TlrView& v, int p, int q, bool tra
 __device__ __forceinline__ void operands(const TlrView& v, int alg, int a, int b, int k, Opnd* X, Opnd* Y,
                                          double* alpha) {
   if (alg == ALG_CHOL) { *X = operand(v, a, k, false); *Y = operand(v, b, k, true); *alpha = -1.0; }
-  else if (alg == ALG_TRTRI) { *X = operand(v, a, k, false); *Y = operand(v, k, b, false); *alpha = 1.0; }
-  else { *X = operand(v, k, a, true); *Y = operand(v, k, b, false); *alpha = 1.0; }
+  else { *X = operand(v, a, k, false); *Y = operand(v, k, b, false); *alpha = 1.0; }
 }
 
-__global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items, double eps,
-                             const double* __restrict__ d_zeta, double zpow, int Kmax, int trunc_cap,
-                             double* __restrict__ ws, size_t item_elems, long long* __restrict__ st,
-                             double* __restrict__ flops) {
-  __shared__ double sh[TLR_THREADS / 32 + 2];
-  __shared__ int shi[TLR_THREADS / 32 + 2];
-  const int2 it = items[blockIdx.x];
+// one item: target tile += alpha op(X) op(Y), then recompression; w is this CTA's workspace
+__device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double tau, int Kmax, int trunc_cap,
+                            ItemWs& w, long long* __restrict__ st, double* __restrict__ flops, double* sh,
+                            int* shi) {
   const int nb = v.nb;
   const int64_t tt = dtile_index(it.x, it.y);
   Opnd X, Y;
@@ -60,9 +59,7 @@ __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k
     if (threadIdx.x == 0) set_status(st, TLR_ERR_STATE, tt);
     return;
   }
-  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
   const int k0 = v.rank[tt];
-  ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
   double* Ut = tileU(v, tt);
   double* Vt = tileV(v, tt);
   for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) { w.Up[e] = Ut[e]; w.Vp[e] = Vt[e]; }
@@ -97,6 +94,31 @@ __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k
   if (flops && threadIdx.x == 0) atomicAdd(flops, pf);
   const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, Ut, Vt, st, tt, sh, shi, flops);
   if (threadIdx.x == 0) v.rank[tt] = kr;
+}
+
+// Persistent: gridDim.x CTAs (the resident count) take items in list order from
+// an atomic counter (*ctr starts at 0), so a launch covers a whole phase and the
+// long items, listed first, overlap with the short ones.  Items touch distinct
+// target tiles and read only operand tiles that no item of the launch writes.
+__global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items,
+                                                       int n_items, int* __restrict__ ctr, double eps,
+                                                       const double* __restrict__ d_zeta, double zpow, int Kmax,
+                                                       int trunc_cap, double* __restrict__ ws, size_t item_elems,
+                                                       long long* __restrict__ st, double* __restrict__ flops) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  __shared__ int s_item;
+  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
+  ItemWs w = item_ws(ws, item_elems, blockIdx.x, v.nb, Kmax, v.kcap);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int q = s_item;
+    __syncthreads();  // every thread holds q before thread 0 takes the next one
+    if (q >= n_items) break;
+    upd_lr_item(v, alg, k, items[q], tau, Kmax, trunc_cap, w, st, flops, sh, shi);
+    __syncthreads();  // the workspace is reused by the next item
+  }
 }
 
 // dense target C += alpha op(X) op(Y) as three batched GEMM stages per item:
@@ -286,28 +308,6 @@ __global__ void k_trop_raw(const double* __restrict__ T, int nb, double* __restr
   cta_trop32(T, nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
 }
 
-// LAUUM step: D_n += A_kn^T A_kn, n = 0 .. k-1 (one CTA per n builds the descriptor)
-__global__ void k_herk_prep(TlrView v, int k, GemmGen* __restrict__ desc, double* __restrict__ ws, size_t ws_elems) {
-  const int n = blockIdx.x, nb = v.nb;
-  const int64_t t = dtile_index(k, n);
-  GemmGen g;
-  g.C = diagT(v, n); g.ldc = nb; g.m = nb; g.n = nb; g.alpha = 1.0; g.beta = 1.0; g.lower = 0;
-  g.lda = nb; g.ldb = nb;
-  if (v.dslot[t] >= 0) {
-    g.A = tileA(v, t); g.tA = 1; g.B = g.A; g.tB = 0; g.k = nb;
-  } else {
-    const int kr = v.rank[t];
-    double* G = ws + (size_t)blockIdx.x * ws_elems;
-    double* T = G + (size_t)v.kcap * v.kcap;
-    g.k = kr; g.A = T; g.tA = 0; g.B = tileV(v, t); g.tB = 1;
-    if (kr > 0) {
-      cta_gemm(kr, kr, nb, 1.0, tileU(v, t), nb, 1, tileU(v, t), nb, 0, 0.0, G, kr);  // G = U^T U
-      cta_gemm(nb, kr, kr, 1.0, tileV(v, t), nb, 0, G, kr, 0, 0.0, T, nb);            // T = V G
-    }
-  }
-  if (threadIdx.x == 0) desc[blockIdx.x] = g;
-}
-
 struct DenseEntry {
   const double* A;
   int nb;
@@ -391,6 +391,21 @@ __global__ void k_copy_back(const GemmGen* __restrict__ desc, double* const* __r
     X[e] = g.C[e];
 }
 
+// resident CTAs of the persistent low-rank update kernel on the current device
+int resident_ctas() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  const int c = cached[dev].load();
+  if (c > 0) return c;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_lr_gen, TLR_THREADS, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  cached[dev].store(std::max(per_sm, 1) * sms);
+  return std::max(per_sm, 1) * sms;
+}
+
 int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
   size_t avail = h->scratch_elems > reserve ? h->scratch_elems - reserve : 0;
   size_t c = per_item ? avail / per_item : 65535;
@@ -412,7 +427,7 @@ int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s) {
 }
 
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
-                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s) {
+                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve) {
   if (n_dn > 0) {
     PhaseScope ps("update.dense_target", s);
     const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
@@ -440,26 +455,33 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     const size_t ie = tlr_item_elems(h->nb, h->kcap);
     const int chunk = chunk_of(h, ie, 0);
     if (chunk < 1) return TLR_ERR_OOM;
-    for (int64_t q0 = 0; q0 < n_lr; q0 += chunk) {
-      const int cnt = (int)(n_lr - q0 < chunk ? n_lr - q0 : chunk);
-      if (g_tlr_prof.enabled) tlr_prof_begin(s);
-      k_upd_lr_gen<<<cnt, TLR_THREADS, 0, s>>>(v, alg, k, d_lr + q0, eps, d_zeta, zpow, 2 * h->kcap,
-                                               h->opts.truncate_at_cap, h->scratch, ie, h->d_stat,
-                                               g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
-      TLR_LAUNCH_CHECK();
-      if (g_tlr_prof.enabled) tlr_prof_end(s);
-    }
+    const int slots = std::max(resident_ctas() - std::max(reserve, 0), 1);
+    const int grid = (int)std::min<int64_t>(n_lr, std::min(slots, chunk));
+    TLR_CUDA_TRY(cudaMemsetAsync(h->d_ctr, 0, sizeof(int), s));
+    if (g_tlr_prof.enabled) tlr_prof_begin(s);
+    k_upd_lr_gen<<<grid, TLR_THREADS, 0, s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
+                                              2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie, h->d_stat,
+                                              g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
+    TLR_LAUNCH_CHECK();
+    if (g_tlr_prof.enabled) tlr_prof_end(s);
   }
   return TLR_OK;
 }
 
+size_t tops_dd_item_elems(const tlr_ctx* h) {
+  const size_t gd = (sizeof(GemmGen) + 7) / 8;
+  return (size_t)h->nb * h->nb + tlr_item_elems(h->nb, h->kcap) + 2 * gd;
+}
+
 int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
-                   const double* d_zeta, double zpow, cudaStream_t s) {
+                   const double* d_zeta, double zpow, cudaStream_t s, double* ws_base, size_t ws_elems) {
   if (n_dd <= 0) return TLR_OK;
+  if (!ws_base) { ws_base = h->scratch; ws_elems = h->scratch_elems; }
   const size_t nn = (size_t)h->nb * h->nb;
   const size_t ie = tlr_item_elems(h->nb, h->kcap);
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
-  const int chunk = chunk_of(h, nn + ie + 2 * gd, 16);
+  const size_t per = tops_dd_item_elems(h);
+  const int chunk = ws_elems > 16 ? (int)std::min<size_t>((ws_elems - 16) / per, 65535) : 0;
   if (chunk < 1) return TLR_ERR_OOM;
   const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
   if (smem > 48 * 1024)
@@ -467,9 +489,9 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
       return TLR_ERR_CUDA;
   for (int64_t q0 = 0; q0 < n_dd; q0 += chunk) {
     const int cnt = (int)(n_dd - q0 < chunk ? n_dd - q0 : chunk);
-    GemmGen* d1 = (GemmGen*)h->scratch;
-    GemmGen* d2 = (GemmGen*)(h->scratch + (size_t)cnt * gd + 1);
-    double* bufs = h->scratch + 2 * (size_t)cnt * gd + 2;
+    GemmGen* d1 = (GemmGen*)ws_base;
+    GemmGen* d2 = (GemmGen*)(ws_base + (size_t)cnt * gd + 1);
+    double* bufs = ws_base + 2 * (size_t)cnt * gd + 2;
     double* ws = bufs + (size_t)cnt * nn;
     k_dd_prep<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dd + q0, cnt, d1, d2, bufs);
     TLR_LAUNCH_CHECK();
@@ -520,13 +542,3 @@ int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double 
   return TLR_OK;
 }
 
-int tops_herk_row(tlr_ctx* h, const TlrView& v, int k, cudaStream_t s) {
-  if (k <= 0) return TLR_OK;
-  const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
-  const size_t desc_elems = ((size_t)k * sizeof(GemmGen) + 7) / 8 + 1;
-  if ((size_t)k * per + desc_elems > h->scratch_elems) return TLR_ERR_OOM;
-  GemmGen* desc = (GemmGen*)h->scratch;
-  k_herk_prep<<<k, 256, 0, s>>>(v, k, desc, h->scratch + desc_elems, per);
-  TLR_LAUNCH_CHECK();
-  return tops_gemm(desc, k, h->nb, h->nb, s);
-}

@@ -6,7 +6,6 @@
 // update algorithms: target (a, b) at step k
 #define ALG_CHOL 0   // A_ab -= L_ak L_bk^T
 #define ALG_TRTRI 1  // A_ab += A_ak A_kb
-#define ALG_LAUUM 2  // A_ab += A_ka^T A_kb
 
 // triangular ops X <- alpha op(T) X, T the (lower) diagonal tile
 #define TOP_SOLVE 0   // T^{-1} X
@@ -22,12 +21,16 @@ struct GemmGen {
   int lower;
 };
 
-// low-rank targets (recompressed at tau = eps * zeta^zpow, zeta = *d_zeta or 1) and dense targets
+// low-rank targets (recompressed at tau = eps * zeta^zpow, zeta = *d_zeta or 1) and dense targets;
+// the persistent low-rank kernel leaves `reserve` CTA slots free for work on another stream
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
-                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s);
-// low-rank targets whose two sources are both dense (materialise, ACA, recompress)
+                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve = 0);
+// low-rank targets whose two sources are both dense (materialise, ACA, recompress); workspace ws
+// (ws_elems doubles), h->scratch when null
 int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
-                   const double* d_zeta, double zpow, cudaStream_t s);
+                   const double* d_zeta, double zpow, cudaStream_t s, double* ws = nullptr, size_t ws_elems = 0);
+// doubles of workspace per item of tops_update_dd
+size_t tops_dd_item_elems(const tlr_ctx* h);
 // Triangular tile transforms by multiplication with an explicit nb x nb matrix M
 // (for instance L_kk^{-1}): low-rank tiles U <- alpha op(M) U (which 0) or V <- alpha op(M) V (which 1);
 // dense tiles A <- alpha op(M) A, or A <- alpha A op(M) when dense_right.  op(M) = M^T when transM.
@@ -38,5 +41,4 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
 int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s);
 // batched general GEMM from a device descriptor array
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s);
-// D_n += A_kn^T A_kn for n = 0 .. k-1 (LAUUM step)
-int tops_herk_row(tlr_ctx* h, const TlrView& v, int k, cudaStream_t s);
+
