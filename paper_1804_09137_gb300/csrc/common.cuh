@@ -31,14 +31,16 @@
 #define PH_UPD_D 3
 #define PLAN_PH 4
 // inverse plan phases of one step: TRTRI (1: column k, 2: updates, 3: row k), LAUUM (2: updates, 3: row k)
-#define ZP_T1_LR 0
-#define ZP_T1_D 1
-#define ZP_T2_LR 2
-#define ZP_T2_D 3
-#define ZP_T3_LR 4
-#define ZP_T3_D 5
-#define ZP_T2_DD 6
-#define ZPH 7
+#define ZP_T2_LR 0
+#define ZP_T2_D 1
+#define ZP_T2_DD 2
+#define ZPH 3
+// whole-inverse lists after the per-step ones: column and row transforms of TRTRI
+#define ZG_T1_LR 0
+#define ZG_T1_D 1
+#define ZG_T3_LR 2
+#define ZG_T3_D 3
+#define ZG 4
 
 #define ST_CODE 0
 #define ST_INFO 1
@@ -90,11 +92,11 @@ struct tlr_ctx {
   int2* d_zlist;
   int2* h_zlist;
   int64_t zlist_cap;
-  int64_t* zoff;      // [nt * ZPH + 1]
+  int64_t* zoff;      // [nt * ZPH + ZG + 1]
   int zplan_valid;
   double* tab;     // Matérn table (TAB_ELEMS)
   MaternParams mp;
-  double* dinv;    // nb x nb: explicit inverse (or transform) of the current diagonal tile
+  double* linv;    // nt tiles nb x nb: L_kk^{-1} of every diagonal tile (Cholesky, reused by the inverse)
   double* scratch; // batched-kernel workspace
   size_t scratch_elems;
   size_t item_elems;  // workspace per low-rank update item

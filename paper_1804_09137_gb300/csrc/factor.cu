@@ -165,13 +165,14 @@ static int launch_trsm(tlr_ctx* h, int k, cudaStream_t s) {
   const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
   const int nlr = (int)(off[PH_TRSM_LR + 1] - off[PH_TRSM_LR]);
   const int nd = (int)(off[PH_TRSM_D + 1] - off[PH_TRSM_D]);
-  if (nlr + nd == 0) return TLR_OK;
-  k_eye_f<<<256, 256, 0, s>>>(h->dinv, h->nb);
+  // L_kk^{-1} is kept for the inverse (tile low-rank TRTRI)
+  double* Li = h->linv + (size_t)k * h->nb * h->nb;
+  k_eye_f<<<256, 256, 0, s>>>(Li, h->nb);
   TLR_LAUNCH_CHECK();
-  int rc = tops_trop_raw(h->D + (size_t)k * h->nb * h->nb, h->nb, h->dinv, h->nb, TOP_SOLVE, 1.0, s);
+  int rc = tops_trop_raw(h->D + (size_t)k * h->nb * h->nb, h->nb, Li, h->nb, TOP_SOLVE, 1.0, s);
   if (rc) return rc;
-  return tops_trmul(h, v, h->dinv, 0, h->d_list + off[PH_TRSM_LR], nlr, 1, 1, h->d_list + off[PH_TRSM_D], nd, 1, 1.0,
-                    s);
+  if (nlr + nd == 0) return TLR_OK;
+  return tops_trmul(h, v, Li, 0, h->d_list + off[PH_TRSM_LR], nlr, 1, 1, h->d_list + off[PH_TRSM_D], nd, 1, 1.0, s);
 }
 
 static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {

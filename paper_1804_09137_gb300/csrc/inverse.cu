@@ -145,48 +145,47 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   }
   h->ndensez = nd;
   std::vector<int2> L;
-  std::vector<int64_t> off((size_t)nt * ZPH + 1, 0);
+  std::vector<int64_t> off((size_t)nt * ZPH + ZG + 1, 0);
   for (int k = 0; k < nt; ++k) {
     for (int ph = 0; ph < ZPH; ++ph) {
       off[(size_t)k * ZPH + ph] = (int64_t)L.size();
-      const char want = ph & 1;  // odd phases: dense tiles
-      switch (ph) {
-        case ZP_T1_LR: case ZP_T1_D:
-          for (int i = k + 1; i < nt; ++i) if (kd(i, k) == want) L.push_back(make_int2(i, k));
-          break;
-        case ZP_T2_LR: case ZP_T2_D: case ZP_T2_DD: {
-          const size_t b = L.size();
-          for (int i = k + 1; i < nt; ++i)
-            for (int j = 0; j < k; ++j) {
-              const bool dd = kd(i, k) && kd(k, j);
-              if (ph == ZP_T2_D ? kd(i, j) == 1 : (kd(i, j) == 0 && dd == (ph == ZP_T2_DD)))
-                L.push_back(make_int2(i, j));
-            }
-          if (ph == ZP_T2_LR) {
-            // longest recompressions first (cost ~ square of the concatenated rank,
-            // estimated from the factor's ranks), so a launch does not end on a tail
-            auto r = [&](int p, int q) { return kd(p, q) ? h->nb : std::max(rk[tile_index(p, q)], 1); };
-            auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(k, t.y)); return K * K; };
-            std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
-          }
-          break;
+      const size_t b = L.size();
+      for (int i = k + 1; i < nt; ++i)
+        for (int j = 0; j < k; ++j) {
+          const bool dd = kd(i, k) && kd(k, j);
+          if (ph == ZP_T2_D ? kd(i, j) == 1 : (kd(i, j) == 0 && dd == (ph == ZP_T2_DD)))
+            L.push_back(make_int2(i, j));
         }
-        case ZP_T3_LR: case ZP_T3_D:
-          for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
-          break;
-        default:  // the LAUUM phases have no per-step lists (left-looking LAUUM)
-          break;
+      if (ph == ZP_T2_LR) {
+        // longest recompressions first (cost ~ square of the concatenated rank,
+        // estimated from the factor's ranks), so a launch does not end on a tail
+        auto r = [&](int p, int q) { return kd(p, q) ? h->nb : std::max(rk[tile_index(p, q)], 1); };
+        auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(k, t.y)); return K * K; };
+        std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
       }
     }
   }
-  off[(size_t)nt * ZPH] = (int64_t)L.size();
+  // column transforms (tiles (i, k), i > k) and row transforms (tiles (k, j), j < k) of every step
+  for (int g = 0; g < ZG; ++g) {
+    off[(size_t)nt * ZPH + g] = (int64_t)L.size();
+    const char want = g & 1;  // odd lists: dense tiles
+    for (int k = 0; k < nt; ++k) {
+      if (g <= ZG_T1_D) {
+        for (int i = k + 1; i < nt; ++i) if (kd(i, k) == want) L.push_back(make_int2(i, k));
+      } else {
+        for (int j = 0; j < k; ++j) if (kd(k, j) == want) L.push_back(make_int2(k, j));
+      }
+    }
+  }
+  off[(size_t)nt * ZPH + ZG] = (int64_t)L.size();
   if (getenv("TLR_VERBOSE")) {
     int64_t cnt[ZPH] = {0};
     for (int k = 0; k < nt; ++k)
       for (int ph = 0; ph < ZPH; ++ph) cnt[ph] += off[(size_t)k * ZPH + ph + 1] - off[(size_t)k * ZPH + ph];
+    const int64_t* g = off.data() + (size_t)nt * ZPH;
     fprintf(stderr, "tlr inverse plan: dense %d; items T1 %lld/%lld T2 %lld/%lld/dd %lld T3 %lld/%lld\n", nd,
-            (long long)cnt[ZP_T1_LR], (long long)cnt[ZP_T1_D], (long long)cnt[ZP_T2_LR], (long long)cnt[ZP_T2_D],
-            (long long)cnt[ZP_T2_DD], (long long)cnt[ZP_T3_LR], (long long)cnt[ZP_T3_D]);
+            (long long)(g[1] - g[0]), (long long)(g[2] - g[1]), (long long)cnt[ZP_T2_LR], (long long)cnt[ZP_T2_D],
+            (long long)cnt[ZP_T2_DD], (long long)(g[3] - g[2]), (long long)(g[4] - g[3]));
   }
   const int64_t len = std::max<int64_t>((int64_t)L.size(), 1);
   if (len > h->zlist_cap) {
@@ -528,8 +527,6 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   PhaseScope ps_all("inverse", s);
   k_zeta<<<1, TLR_THREADS, 0, s>>>(h->D, nb, nt, d_zeta);
   TLR_LAUNCH_CHECK();
-  k_copy<<<1024, 256, 0, s>>>(h->D, h->Dz, (int64_t)nt * nn);
-  TLR_LAUNCH_CHECK();
   TLR_CUDA_TRY(cudaMemsetAsync(h->rankz, 0, std::max<int64_t>(h->ntiles, 1) * sizeof(int), s));
   if (h->ntiles > 0) {
     for (int64_t t0 = 0; t0 < h->ntiles; t0 += 65535) {
@@ -554,17 +551,26 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   }
   if (max_dd > 0) ZTRY(ensure_aux(h, std::min(max_dd, 32)));
   // ---- TRTRI
+  // L_kk^{-1} of every diagonal tile comes from the Cholesky (the last one is formed here)
+  {
+    PhaseScope ps("trtri.diag", s);
+    double* last = h->linv + (size_t)(nt - 1) * nn;
+    k_eye<<<256, 256, 0, s>>>(last, nb);
+    TLR_LAUNCH_CHECK();
+    ZTRY(tops_trop_raw(h->D + (size_t)(nt - 1) * nn, nb, last, nb, TOP_SOLVE, 1.0, s));
+  }
+  const int64_t* gl = h->zoff + (size_t)nt * ZPH;
+  auto GL = [&](int g) { return h->d_zlist + gl[g]; };
+  auto GN = [&](int g) { return (int)(gl[g + 1] - gl[g]); };
+  {  // step 1 of every k at once: no earlier step touches column k
+    PhaseScope ps("trtri.col", s);  // A_ik <- -A_ik L_kk^{-1}: V <- -L_kk^{-T} V
+    ZTRY(tops_trmul(h, z, h->linv, 1, GL(ZG_T1_LR), GN(ZG_T1_LR), 1, 0, GL(ZG_T1_D), GN(ZG_T1_D), 1, -1.0, s, nn,
+                    2));
+  }
   for (int k = 0; k < nt; ++k) {
     const int64_t* off = h->zoff + (size_t)k * ZPH;
     auto L = [&](int ph) { return h->d_zlist + off[ph]; };
     auto N = [&](int ph) { return (int)(off[ph + 1] - off[ph]); };
-    double* Mi = h->dinv;  // L_kk^{-1}, applied by GEMM in steps 1 and 3, stored in step 4
-    { PhaseScope ps("trtri.diag", s);
-      k_eye<<<256, 256, 0, s>>>(Mi, nb);
-      TLR_LAUNCH_CHECK();
-      ZTRY(tops_trop_raw(h->Dz + (size_t)k * nn, nb, Mi, nb, TOP_SOLVE, 1.0, s)); }
-    { PhaseScope ps("trtri.col", s);  // A_ik <- -A_ik L_kk^{-1}: V <- -L_kk^{-T} V
-      ZTRY(tops_trmul(h, z, Mi, 1, L(ZP_T1_LR), N(ZP_T1_LR), 1, 0, L(ZP_T1_D), N(ZP_T1_D), 1, -1.0, s)); }
     // the three target sets of step 2 are disjoint and read only column k and row k
     const int ndd = N(ZP_T2_DD);
     if (ndd > 0) {
@@ -581,10 +587,14 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
       TLR_CUDA_TRY(cudaEventRecord(h->ev_join, h->aux));
       TLR_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
     }
-    { PhaseScope ps("trtri.row", s);  // A_kj <- L_kk^{-1} A_kj: U <- L_kk^{-1} U
-      ZTRY(tops_trmul(h, z, Mi, 0, L(ZP_T3_LR), N(ZP_T3_LR), 0, 0, L(ZP_T3_D), N(ZP_T3_D), 0, 1.0, s)); }
-    PhaseScope ps_d("trtri.store", s);
-    k_copy<<<256, 256, 0, s>>>(Mi, h->Dz + (size_t)k * nn, (int64_t)nn);
+  }
+  {  // step 3 of every k at once: row k is final after step k - 1 and a source only in step k
+    PhaseScope ps("trtri.row", s);  // A_kj <- L_kk^{-1} A_kj: U <- L_kk^{-1} U
+    ZTRY(tops_trmul(h, z, h->linv, 0, GL(ZG_T3_LR), GN(ZG_T3_LR), 0, 0, GL(ZG_T3_D), GN(ZG_T3_D), 0, 1.0, s, nn, 1));
+  }
+  {  // step 4: A_kk <- L_kk^{-1}
+    PhaseScope ps("trtri.store", s);
+    k_copy<<<1024, 256, 0, s>>>(h->linv, h->Dz, (int64_t)nt * nn);
     TLR_LAUNCH_CHECK();
   }
   // ---- LAUUM

@@ -357,12 +357,14 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
 }
 
 // descriptors of X_tmp = alpha op(M) X (or alpha A op(M)) for tile items
-__global__ void k_trmul_desc(TlrView v, const double* __restrict__ M, int transM, const int2* __restrict__ items,
-                             int cnt, int which, int dense_right, double alpha, double* __restrict__ tmp,
-                             size_t tmp_elems, GemmGen* __restrict__ desc, double** __restrict__ dst) {
+__global__ void k_trmul_desc(TlrView v, const double* __restrict__ M0, size_t m_stride, int m_by, int transM,
+                             const int2* __restrict__ items, int cnt, int which, int dense_right, double alpha,
+                             double* __restrict__ tmp, size_t tmp_elems, GemmGen* __restrict__ desc,
+                             double** __restrict__ dst) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt) return;
   const int2 it = items[q];
+  const double* M = M0 + (m_by == 1 ? (size_t)it.x * m_stride : m_by == 2 ? (size_t)it.y * m_stride : 0);
   const int64_t t = dtile_index(it.x, it.y);
   const int nb = v.nb;
   GemmGen g;
@@ -507,7 +509,8 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
 }
 
 int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
-               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s) {
+               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s,
+               size_t m_stride, int m_by) {
   const size_t nb = h->nb;
   const size_t gd = (sizeof(GemmGen) + 7) / 8 + 1;
   for (int pass = 0; pass < 2; ++pass) {
@@ -523,7 +526,8 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
       GemmGen* desc = (GemmGen*)h->scratch;
       double** dst = (double**)(h->scratch + (size_t)cnt * (gd - 1) + 8);
       double* tmp = h->scratch + (size_t)cnt * gd + 16;
-      k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, pass == 0 ? transM : transM_dense, items + q0, cnt,
+      k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, m_stride, m_by, pass == 0 ? transM : transM_dense,
+                                                      items + q0, cnt,
                                                       pass == 0 ? which : 2, dense_right, alpha, tmp, tmp_elems,
                                                       desc, dst);
       TLR_LAUNCH_CHECK();

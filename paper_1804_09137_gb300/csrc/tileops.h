@@ -34,9 +34,11 @@ size_t tops_dd_item_elems(const tlr_ctx* h);
 // Triangular tile transforms by multiplication with an explicit nb x nb matrix M
 // (for instance L_kk^{-1}): low-rank tiles U <- alpha op(M) U (which 0) or V <- alpha op(M) V (which 1);
 // dense tiles A <- alpha op(M) A, or A <- alpha A op(M) when dense_right.  op(M) = M^T when transM.
-// Batched multi-CTA GEMMs into a workspace, then copied back.
+// Batched multi-CTA GEMMs into a workspace, then copied back.  m_by 1 / 2: the item's own matrix
+// M + m_stride * (its row / column tile index) instead of M.
 int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
-               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s);
+               int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s,
+               size_t m_stride = 0, int m_by = 0);
 // X <- alpha op(T) X for a raw nb x ncols matrix
 int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s);
 // batched general GEMM from a device descriptor array
