@@ -35,7 +35,7 @@ UNIT = "evals/s"
 THETA = (1.0, 0.3, 1.0)
 # float64 peak of the GB300 derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22500.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22400.json")
 KERNEL_SOURCES = ["tileops.cu", "recompress.cuh", "tile.cuh"]
 
 
