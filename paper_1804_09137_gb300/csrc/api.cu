@@ -134,7 +134,7 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave};
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->aux) cudaStreamDestroy(h->aux);
@@ -218,6 +218,7 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->linv, (size_t)h->cap_nt * nb * nb);
   rc |= dmalloc(&h->d_stat, 4);
   rc |= dmalloc(&h->d_ctr, 4);
+  rc |= dmalloc(&h->d_xk, nb);
   rc |= dmalloc(&h->d_vec, 4 * (size_t)cnp);
   h->red_len = 2 * h->cap_nt + 64;
   rc |= dmalloc(&h->d_red, h->red_len);

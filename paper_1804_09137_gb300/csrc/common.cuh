@@ -103,6 +103,7 @@ struct tlr_ctx {
   int items_per_launch;
   long long* d_stat;  // status words
   int* d_ctr;         // item counter of the persistent update kernel
+  double* d_xk;       // nb: x_k of the current solve step
   double* d_vec;      // 4 vectors of npad
   double* d_red;      // reduction partials
   int red_len;

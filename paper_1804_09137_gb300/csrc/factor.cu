@@ -154,12 +154,6 @@ int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t
 }
 
 // L_ik = A_ik L_kk^{-T}: low rank V <- L_kk^{-1} V, dense A <- A L_kk^{-T}, by GEMM with the explicit L_kk^{-1}
-__global__ void k_eye_f(double* __restrict__ X, int nb) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
-       e += (int64_t)gridDim.x * blockDim.x)
-    X[e] = ((e % nb) == (e / nb)) ? 1.0 : 0.0;
-}
-
 static int launch_trsm(tlr_ctx* h, int k, cudaStream_t s) {
   const TlrView v = view_of(h);
   const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
@@ -167,9 +161,7 @@ static int launch_trsm(tlr_ctx* h, int k, cudaStream_t s) {
   const int nd = (int)(off[PH_TRSM_D + 1] - off[PH_TRSM_D]);
   // L_kk^{-1} is kept for the inverse (tile low-rank TRTRI)
   double* Li = h->linv + (size_t)k * h->nb * h->nb;
-  k_eye_f<<<256, 256, 0, s>>>(Li, h->nb);
-  TLR_LAUNCH_CHECK();
-  int rc = tops_trop_raw(h->D + (size_t)k * h->nb * h->nb, h->nb, Li, h->nb, TOP_SOLVE, 1.0, s);
+  int rc = tops_trinv(h->D + (size_t)k * h->nb * h->nb, h->nb, Li, s);
   if (rc) return rc;
   if (nlr + nd == 0) return TLR_OK;
   return tops_trmul(h, v, Li, 0, h->d_list + off[PH_TRSM_LR], nlr, 1, 1, h->d_list + off[PH_TRSM_D], nd, 1, 1.0, s);

@@ -89,11 +89,6 @@ __global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int
     b[e] = a[e];
 }
 
-__global__ void k_eye(double* __restrict__ X, int nb) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nb * nb;
-       e += (int64_t)gridDim.x * blockDim.x)
-    X[e] = ((e % nb) == (e / nb)) ? 1.0 : 0.0;
-}
 
 }  // namespace
 
@@ -554,10 +549,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
   // L_kk^{-1} of every diagonal tile comes from the Cholesky (the last one is formed here)
   {
     PhaseScope ps("trtri.diag", s);
-    double* last = h->linv + (size_t)(nt - 1) * nn;
-    k_eye<<<256, 256, 0, s>>>(last, nb);
-    TLR_LAUNCH_CHECK();
-    ZTRY(tops_trop_raw(h->D + (size_t)(nt - 1) * nn, nb, last, nb, TOP_SOLVE, 1.0, s));
+    ZTRY(tops_trinv(h->D + (size_t)(nt - 1) * nn, nb, h->linv + (size_t)(nt - 1) * nn, s));
   }
   const int64_t* gl = h->zoff + (size_t)nt * ZPH;
   auto GL = [&](int g) { return h->d_zlist + gl[g]; };

@@ -75,75 +75,107 @@ __global__ void k_trsv_lower_t(const double* __restrict__ L, int nb, double* __r
   }
 }
 
-// forward update of step k: r_i -= L_ik r_k, i = k+1 .. nt-1 (one CTA per i)
-__global__ void k_gemv_fwd(TlrView v, int k, double* __restrict__ r) {
-  extern __shared__ double tv[];
-  const int i = k + 1 + blockIdx.x, nb = v.nb;
-  const int64_t t = dtile_index(i, k);
-  const double* rk = r + (size_t)k * nb;
-  double* ri = r + (size_t)i * nb;
-  if (v.dslot[t] >= 0) {
-    const double* A = tileA(v, t);
-    for (int a = threadIdx.x; a < nb; a += blockDim.x) {
-      double acc = 0.0;
-      for (int b = 0; b < nb; ++b) acc = fma(A[(size_t)b * nb + a], rk[b], acc);
-      ri[a] -= acc;
-    }
-    return;
-  }
-  const int kr = v.rank[t];
-  if (kr <= 0) return;
-  const double* Ut = tileU(v, t);
-  const double* Vt = tileV(v, t);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int l = warp; l < kr; l += nw) {
-    double s = 0.0;
-    for (int q = lane; q < nb; q += 32) s = fma(Vt[(size_t)l * nb + q], rk[q], s);
-    s = warp_sum(s);
-    if (lane == 0) tv[l] = s;
-  }
-  __syncthreads();
-  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+// xo = op(M) r for the explicit inverse M = L_kk^{-1} of a diagonal tile (op(M) = M^T when
+// trans): 32 rows per CTA
+__global__ void k_diag_inv_apply(const double* __restrict__ M, int nb, int trans, const double* __restrict__ r,
+                                 double* __restrict__ xo) {
+  __shared__ double part[8][33];
+  const int r0 = blockIdx.x * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!trans) {  // (M r)_a = sum_b M[b * nb + a] r[b]: lanes over rows (coalesced), warps split b
+    const int a = r0 + lane;
     double acc = 0.0;
-    for (int l = 0; l < kr; ++l) acc = fma(Ut[(size_t)l * nb + a], tv[l], acc);
-    ri[a] -= acc;
+    if (a < nb)
+      for (int b = warp; b <= a; b += 8) acc = fma(M[(size_t)b * nb + a], r[b], acc);
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && a < nb) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += part[w][lane];
+      xo[a] = t;
+    }
+  } else {  // (M^T r)_a = sum_{b >= a} M[a * nb + b] r[b]: warp per row, lanes over b
+    for (int q = warp; q < 32; q += 8) {
+      const int a = r0 + q;
+      if (a >= nb) break;
+      double t = 0.0;
+      for (int b = a + lane; b < nb; b += 32) t = fma(M[(size_t)a * nb + b], r[b], t);
+      t = warp_sum(t);
+      if (lane == 0) xo[a] = t;
+    }
   }
 }
 
-// backward update of step k: r_j -= L_kj^T r_k, j = 0 .. k-1 (one CTA per j)
-__global__ void k_gemv_bwd(TlrView v, int k, double* __restrict__ r) {
-  extern __shared__ double tv[];
-  const int j = blockIdx.x, nb = v.nb;
-  const int64_t t = dtile_index(k, j);
-  const double* rk = r + (size_t)k * nb;
-  double* rj = r + (size_t)j * nb;
+// rows [c0, c1) of  r_i -= L_ik x  (forward, tile (i, k)) or  r_j -= L_kj^T x  (backward, tile (k, j))
+__device__ void tile_gemv_sub(const TlrView& v, int64_t t, int bwd, const double* __restrict__ x,
+                              double* __restrict__ out, int c0, int c1, double* tv) {
+  const int nb = v.nb;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (v.dslot[t] >= 0) {  // (A^T r_k)_a = sum_b A[b, a] r_k[b]: warp per a, lanes over b
+  if (v.dslot[t] >= 0) {
     const double* A = tileA(v, t);
-    for (int a = warp; a < nb; a += nw) {
-      double s = 0.0;
-      for (int b = lane; b < nb; b += 32) s = fma(A[(size_t)a * nb + b], rk[b], s);
-      s = warp_sum(s);
-      if (lane == 0) rj[a] -= s;
+    if (!bwd) {  // (A x)_a = sum_b A[b * nb + a] x[b]
+      for (int a = c0 + threadIdx.x; a < c1; a += blockDim.x) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc = fma(A[(size_t)b * nb + a], x[b], acc);
+        out[a] -= acc;
+      }
+    } else {  // (A^T x)_a = sum_b A[a * nb + b] x[b]
+      for (int a = c0 + warp; a < c1; a += nw) {
+        double acc = 0.0;
+        for (int b = lane; b < nb; b += 32) acc = fma(A[(size_t)a * nb + b], x[b], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) out[a] -= acc;
+      }
     }
     return;
   }
   const int kr = v.rank[t];
   if (kr <= 0) return;
-  const double* Ut = tileU(v, t);
-  const double* Vt = tileV(v, t);
+  // forward: out -= U (V^T x); backward: out -= V (U^T x)
+  const double* P = bwd ? tileV(v, t) : tileU(v, t);
+  const double* Q = bwd ? tileU(v, t) : tileV(v, t);
   for (int l = warp; l < kr; l += nw) {
-    double s = 0.0;
-    for (int q = lane; q < nb; q += 32) s = fma(Ut[(size_t)l * nb + q], rk[q], s);
-    s = warp_sum(s);
-    if (lane == 0) tv[l] = s;
+    double acc = 0.0;
+    for (int q = lane; q < nb; q += 32) acc = fma(Q[(size_t)l * nb + q], x[q], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) tv[l] = acc;
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < nb; a += blockDim.x) {
+  for (int a = c0 + threadIdx.x; a < c1; a += blockDim.x) {
     double acc = 0.0;
-    for (int l = 0; l < kr; ++l) acc = fma(Vt[(size_t)l * nb + a], tv[l], acc);
-    rj[a] -= acc;
+    for (int l = 0; l < kr; ++l) acc = fma(P[(size_t)l * nb + a], tv[l], acc);
+    out[a] -= acc;
   }
+}
+
+// Step k of a solve after x_k = op(L_kk^{-1}) r_k is in xk: CTA 0 stores x_k into r_k;
+// the others update the remaining blocks, GEMV_SPLIT row chunks per tile (a dense tile's
+// nb^2 multiply-adds are spread over the chunks; a low-rank tile is one chunk's work)
+#define GEMV_SPLIT 16
+__global__ void k_gemv_step(TlrView v, int k, int bwd, const double* __restrict__ xk, double* __restrict__ r) {
+  extern __shared__ double tv[];
+  const int nb = v.nb;
+  if (blockIdx.x == 0) {
+    for (int a = threadIdx.x; a < nb; a += blockDim.x) r[(size_t)k * nb + a] = xk[a];
+    return;
+  }
+  const int q = blockIdx.x - 1;
+  const int tix = q / GEMV_SPLIT, c = q % GEMV_SPLIT;
+  const int other = bwd ? tix : k + 1 + tix;  // block row i (forward) or column j (backward)
+  const int64_t t = bwd ? dtile_index(k, other) : dtile_index(other, k);
+  const bool dense = v.dslot[t] >= 0;
+  int c0, c1;
+  if (dense) {
+    const int w = (nb + GEMV_SPLIT - 1) / GEMV_SPLIT;
+    c0 = min(nb, c * w);
+    c1 = min(nb, c0 + w);
+  } else {
+    if (c != 0) return;
+    c0 = 0;
+    c1 = nb;
+  }
+  if (c0 >= c1) return;
+  tile_gemv_sub(v, t, bwd, xk, r + (size_t)other * nb, c0, c1, tv);
 }
 
 // z_i = L_ii e_i + sum_{j<i} L_ij e_j   (one CTA per tile row i)
@@ -304,30 +336,55 @@ int tlr_permute_out(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) 
   return TLR_OK;
 }
 
+// Tile solves.  A diagonal block is applied as a GEMV with the explicit inverse
+// L_kk^{-1} kept by the Cholesky (the last block, whose inverse the Cholesky does not
+// form, by substitution), then the off-diagonal blocks of its column (forward) or row
+// (backward) are subtracted.
+static int solve_diag(tlr_ctx* h, int k, int trans, double* r, cudaStream_t s) {
+  const int nb = h->nb;
+  double* rk = r + (size_t)k * nb;
+  if (k == h->nt - 1 || !h->linv || !h->d_xk) {
+    if (trans) k_trsv_lower_t<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, rk);
+    else k_trsv_lower<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, rk);
+    TLR_LAUNCH_CHECK();
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->d_xk, rk, (size_t)nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return TLR_OK;
+  }
+  k_diag_inv_apply<<<(nb + 31) / 32, 256, 0, s>>>(h->linv + (size_t)k * nb * nb, nb, trans, rk, h->d_xk);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
   const int nb = h->nb, nt = h->nt;
+  if (nt == 1 || !h->d_xk) {  // one tile (also the allocation-free context)
+    k_trsv_lower<<<1, 256, 0, s>>>(h->D, nb, r);
+    TLR_LAUNCH_CHECK();
+    return TLR_OK;
+  }
   const size_t sm = (size_t)h->kcap * sizeof(double);
   for (int k = 0; k < nt; ++k) {
-    k_trsv_lower<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
+    int rc = solve_diag(h, k, 0, r, s);
+    if (rc) return rc;
+    k_gemv_step<<<1 + (nt - k - 1) * GEMV_SPLIT, 256, sm, s>>>(view_of(h), k, 0, h->d_xk, r);
     TLR_LAUNCH_CHECK();
-    if (k < nt - 1) {
-      k_gemv_fwd<<<nt - k - 1, 256, sm, s>>>(view_of(h), k, r);
-      TLR_LAUNCH_CHECK();
-    }
   }
   return TLR_OK;
 }
 
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
   const int nb = h->nb, nt = h->nt;
+  if (nt == 1 || !h->d_xk) {
+    k_trsv_lower_t<<<1, 256, 0, s>>>(h->D, nb, r);
+    TLR_LAUNCH_CHECK();
+    return TLR_OK;
+  }
   const size_t sm = (size_t)h->kcap * sizeof(double);
   for (int k = nt - 1; k >= 0; --k) {
-    k_trsv_lower_t<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, r + (size_t)k * nb);
+    int rc = solve_diag(h, k, 1, r, s);
+    if (rc) return rc;
+    k_gemv_step<<<1 + k * GEMV_SPLIT, 256, sm, s>>>(view_of(h), k, 1, h->d_xk, r);
     TLR_LAUNCH_CHECK();
-    if (k > 0) {
-      k_gemv_bwd<<<k, 256, sm, s>>>(view_of(h), k, r);
-      TLR_LAUNCH_CHECK();
-    }
   }
   return TLR_OK;
 }

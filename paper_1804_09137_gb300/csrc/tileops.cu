@@ -182,130 +182,59 @@ __global__ void k_gemm_gen(const GemmGen* __restrict__ desc) {
                      gridDim.x, g.lower);
 }
 
-// X (nb x ncol <= 32 columns, ld nb) <- op(T) X, one CTA
-__device__ void cta_trop32(const double* __restrict__ T, int nb, double* __restrict__ X, int ncol, int op,
-                           double alpha) {
+// X = T^{-1} for a lower triangular nb x nb tile T (both column-major, ld nb) by forward
+// substitution on the identity, TRINV_COLS columns per CTA.  Column block c0 is zero above
+// row c0 and stays so: the sweep starts at the 32-row block holding c0.
+#define TRINV_COLS 8
+__global__ void k_trinv(const double* __restrict__ T, int nb, double* __restrict__ X) {
   __shared__ double Ls[32][33];
-  __shared__ double Xs[32][33];
-  const int nblk = (nb + 31) / 32;
-  if (op == TOP_SOLVE) {
-    for (int rb0 = 0; rb0 < nb; rb0 += 32) {
-      const int w = min(32, nb - rb0);
-      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-        const int r = id & 31, c = id >> 5;
-        Ls[r][c] = (r < w && c < w) ? T[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
-        Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
-      }
-      __syncthreads();
-      if (threadIdx.x < ncol) {
-        const int c = threadIdx.x;
-        for (int r = 0; r < w; ++r) {
-          double s = Xs[r][c];
-          for (int l = 0; l < r; ++l) s -= Ls[r][l] * Xs[l][c];
-          Xs[r][c] = s / Ls[r][r];
-        }
-      }
-      __syncthreads();
-      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-        const int r = id & 31, c = id >> 5;
-        if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
-      }
-      for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
-        double acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-        for (int l = 0; l < w; ++l) {
-          const double lv = T[(size_t)(rb0 + l) * nb + r];
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < ncol) X[(size_t)c * nb + r] -= acc[c];
-      }
-      __syncthreads();
-    }
-  } else if (op == TOP_SOLVE_T) {
-    for (int bb = nblk - 1; bb >= 0; --bb) {
-      const int rb0 = bb * 32, w = min(32, nb - rb0);
-      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-        const int r = id & 31, c = id >> 5;
-        Ls[r][c] = (r < w && c < w) ? T[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
-        Xs[r][c] = (r < w && c < ncol) ? X[(size_t)c * nb + rb0 + r] : 0.0;
-      }
-      __syncthreads();
-      if (threadIdx.x < ncol) {  // T_bb^T x = b: backward over rows, (T^T)[r][l] = T[l][r]
-        const int c = threadIdx.x;
-        for (int r = w - 1; r >= 0; --r) {
-          double s = Xs[r][c];
-          for (int l = r + 1; l < w; ++l) s -= Ls[l][r] * Xs[l][c];
-          Xs[r][c] = s / Ls[r][r];
-        }
-      }
-      __syncthreads();
-      for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-        const int r = id & 31, c = id >> 5;
-        if (r < w && c < ncol) X[(size_t)c * nb + rb0 + r] = Xs[r][c];
-      }
-      // rows above: X[a] -= sum_l T[rb0 + l, a] Xs[l]
-      for (int a = threadIdx.x; a < rb0; a += blockDim.x) {
-        double acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-        const double* Tc = T + (size_t)a * nb + rb0;
-        for (int l = 0; l < w; ++l) {
-          const double tv = Tc[l];
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] = fma(tv, Xs[l][c], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (c < ncol) X[(size_t)c * nb + a] -= acc[c];
-      }
-      __syncthreads();
-    }
-  } else {  // TOP_MUL_T: X <- T^T X, top-down in place (row block a needs rows >= a only)
-    for (int ab = 0; ab < nblk; ++ab) {
-      const int a0 = ab * 32, wa = min(32, nb - a0);
-      // thread (q = row in block, c = column): acc = sum_{r >= a0 + q} T[r, a0 + q] X[r, c]
-      const int q = threadIdx.x & 31, cgrp = threadIdx.x >> 5;  // 8 column groups of 4
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int r0 = a0; r0 < nb; r0 += 32) {
-        const int wr = min(32, nb - r0);
-        __syncthreads();
-        for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
-          const int r = id & 31, c = id >> 5;
-          Ls[r][c] = (r < wr && c < wa) ? T[(size_t)(a0 + c) * nb + r0 + r] : 0.0;  // Ls[r][q] = T[r0+r, a0+q]
-          Xs[r][c] = (r < wr && c < ncol) ? X[(size_t)c * nb + r0 + r] : 0.0;
-        }
-        __syncthreads();
-        for (int r = 0; r < wr; ++r) {
-          const double tv = (r0 + r >= a0 + q) ? Ls[r][q] : 0.0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[j] = fma(tv, Xs[r][cgrp * 4 + j], acc[j]);
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = cgrp * 4 + j;
-        if (q < wa && c < ncol) X[(size_t)c * nb + a0 + q] = acc[j];
-      }
-      __syncthreads();
-    }
+  __shared__ double Xs[32][TRINV_COLS + 1];
+  const int c0 = blockIdx.x * TRINV_COLS;
+  const int ncol = min(TRINV_COLS, nb - c0);
+  for (int e = threadIdx.x; e < nb * TRINV_COLS; e += blockDim.x) {
+    const int r = e % nb, c = e / nb;
+    if (c < ncol) X[(size_t)(c0 + c) * nb + r] = (r == c0 + c) ? 1.0 : 0.0;
   }
-  if (alpha != 1.0) {
+  __syncthreads();
+  for (int rb0 = (c0 / 32) * 32; rb0 < nb; rb0 += 32) {
+    const int w = min(32, nb - rb0);
+    for (int id = threadIdx.x; id < 32 * 32; id += blockDim.x) {
+      const int r = id & 31, c = id >> 5;
+      Ls[r][c] = (r < w && c < w) ? T[(size_t)(rb0 + c) * nb + rb0 + r] : 0.0;
+    }
+    for (int id = threadIdx.x; id < 32 * TRINV_COLS; id += blockDim.x) {
+      const int r = id % 32, c = id / 32;
+      Xs[r][c] = (r < w && c < ncol) ? X[(size_t)(c0 + c) * nb + rb0 + r] : 0.0;
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * ncol; e += blockDim.x) X[(size_t)(e / nb) * nb + (e % nb)] *= alpha;
+    if (threadIdx.x < ncol) {
+      const int c = threadIdx.x;
+      for (int r = 0; r < w; ++r) {
+        double v = Xs[r][c];
+        for (int l = 0; l < r; ++l) v -= Ls[r][l] * Xs[l][c];
+        Xs[r][c] = v / Ls[r][r];
+      }
+    }
+    __syncthreads();
+    for (int id = threadIdx.x; id < 32 * TRINV_COLS; id += blockDim.x) {
+      const int r = id % 32, c = id / 32;
+      if (r < w && c < ncol) X[(size_t)(c0 + c) * nb + rb0 + r] = Xs[r][c];
+    }
+    for (int r = rb0 + w + threadIdx.x; r < nb; r += blockDim.x) {
+      double acc[TRINV_COLS];
+#pragma unroll
+      for (int c = 0; c < TRINV_COLS; ++c) acc[c] = 0.0;
+      for (int l = 0; l < w; ++l) {
+        const double lv = T[(size_t)(rb0 + l) * nb + r];
+#pragma unroll
+        for (int c = 0; c < TRINV_COLS; ++c) acc[c] = fma(lv, Xs[l][c], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < TRINV_COLS; ++c)
+        if (c < ncol) X[(size_t)(c0 + c) * nb + r] -= acc[c];
+    }
     __syncthreads();
   }
-}
-
-__global__ void k_trop_raw(const double* __restrict__ T, int nb, double* __restrict__ X, int ncols, int op,
-                           double alpha) {
-  const int cb = blockIdx.x * 32;
-  if (cb >= ncols) return;
-  cta_trop32(T, nb, X + (size_t)cb * nb, min(32, ncols - cb), op, alpha);
 }
 
 struct DenseEntry {
@@ -540,8 +469,8 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
   return TLR_OK;
 }
 
-int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s) {
-  k_trop_raw<<<(ncols + 31) / 32, 256, 0, s>>>(T, nb, X, ncols, op, alpha);
+int tops_trinv(const double* T, int nb, double* X, cudaStream_t s) {
+  k_trinv<<<(nb + TRINV_COLS - 1) / TRINV_COLS, 256, 0, s>>>(T, nb, X);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }

@@ -7,10 +7,6 @@
 #define ALG_CHOL 0   // A_ab -= L_ak L_bk^T
 #define ALG_TRTRI 1  // A_ab += A_ak A_kb
 
-// triangular ops X <- alpha op(T) X, T the (lower) diagonal tile
-#define TOP_SOLVE 0   // T^{-1} X
-#define TOP_SOLVE_T 1 // T^{-T} X
-#define TOP_MUL_T 2   // T^T X
 
 struct GemmGen {
   const double* A;
@@ -39,8 +35,8 @@ size_t tops_dd_item_elems(const tlr_ctx* h);
 int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
                int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s,
                size_t m_stride = 0, int m_by = 0);
-// X <- alpha op(T) X for a raw nb x ncols matrix
-int tops_trop_raw(const double* T, int nb, double* X, int ncols, int op, double alpha, cudaStream_t s);
+// X = T^{-1} for a lower triangular nb x nb tile (X fully written)
+int tops_trinv(const double* T, int nb, double* X, cudaStream_t s);
 // batched general GEMM from a device descriptor array
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s);
 
