@@ -22,8 +22,12 @@
  *    is enqueued); a positive TLR_ERR_* code otherwise.  Failures that happen on
  *    the device (non-SPD pivot, rank cap overflow, wait time-out) are recorded in
  *    the handle and reported by tlr_status after the stream has drained.
- *  - The library owns its tile storage, allocated with cudaMalloc in tlr_create
- *    (and grown there only); everything is released by tlr_destroy.
+ *  - The library owns its tile storage, allocated with cudaMalloc in tlr_create;
+ *    the gradient's inverse (Sigma^{-1}, about nt(nt+1)/2 dense tiles) and a
+ *    second stream with its workspace are allocated by the first
+ *    tlr_loglik_grad (TLR_ERR_OOM when that fails); a dense pool
+ *    grows in tlr_compress when more tiles turn dense.  Everything is released
+ *    by tlr_destroy.
  */
 #ifndef TLR_H_
 #define TLR_H_
@@ -54,9 +58,9 @@ typedef struct {
  * off-diagonal tile whose eps-rank exceeds it is stored and updated dense
  * (0 = max(16, nb/9)); tiles are also made dense where a dense x dense
  * product would land on them during the factorization; inv_scale: the
- * gradient's inverse Sigma^{-1} truncates its tiles at inv_scale * eps *
- * zeta^(1/2) (L^{-1}) and inv_scale * eps * zeta (Sigma^{-1}), zeta = the
- * largest 1 / L_aa^2 (0 = 0.1). */
+ * gradient's inverse keeps L^{-1} in tile low-rank form truncated at
+ * inv_scale * eps * zeta^(1/2), zeta = the largest 1 / L_aa^2 (0 = 0.1);
+ * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile. */
 typedef struct {
   int nb;
   double eps;
