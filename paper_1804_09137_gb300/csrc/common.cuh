@@ -208,11 +208,14 @@ __device__ __forceinline__ int tab_locate(double r, int e_lo, double* t) {
   const int e = ((hi >> 20) & 0x7ff) - 1023;
   const double m = __hiloint2double((hi & 0x800fffff) | 0x3ff00000, __double2loint(r));
   // 2^(q/4) boundaries of the 4 sub-intervals of one octave
-  const double b1 = 1.18920711500272106672, b2 = 1.41421356237309504880, b3 = 1.68179283050742908606;
+  constexpr double b1 = 1.18920711500272106672, b2 = 1.41421356237309504880, b3 = 1.68179283050742908606;
   int q = (m >= b1) + (m >= b2) + (m >= b3);
-  double a = q == 0 ? 1.0 : (q == 1 ? b1 : (q == 2 ? b2 : b3));
-  double b = q == 0 ? b1 : (q == 1 ? b2 : (q == 2 ? b3 : 2.0));
-  *t = (2.0 * m - a - b) / (b - a);
+  const double a = q == 0 ? 1.0 : (q == 1 ? b1 : (q == 2 ? b2 : b3));
+  const double b = q == 0 ? b1 : (q == 1 ? b2 : (q == 2 ? b3 : 2.0));
+  // 1 / (b - a) of the four sub-intervals (compile-time constants: no float64 division per entry)
+  constexpr double i0 = 1.0 / (b1 - 1.0), i1 = 1.0 / (b2 - b1), i2 = 1.0 / (b3 - b2), i3 = 1.0 / (2.0 - b3);
+  const double iw = q == 0 ? i0 : (q == 1 ? i1 : (q == 2 ? i2 : i3));
+  *t = (2.0 * m - a - b) * iw;
   return TAB_SUB * (e - e_lo) + q;
 }
 

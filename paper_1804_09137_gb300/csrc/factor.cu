@@ -93,18 +93,18 @@ __global__ void k_syrk_prep(TlrView v, int k, int i0, GemmDesc* __restrict__ des
     double* T = G + (size_t)v.kcap * v.kcap;
     d.P = T;
     if (kr > 0) {
-      cta_gemm(kr, kr, nb, 1.0, tileV(v, t), nb, 1, tileV(v, t), nb, 0, 0.0, G, kr);   // G = V^T V
-      cta_gemm(nb, kr, kr, 1.0, tileU(v, t), nb, 0, G, kr, 0, 0.0, T, nb);             // T = U G
+      cta_gemm_df(kr, kr, nb, 1.0, tileV(v, t), nb, 1, tileV(v, t), nb, 0, 0.0, G, kr);   // G = V^T V
+      cta_gemm_df(nb, kr, kr, 1.0, tileU(v, t), nb, 0, G, kr, 0, 0.0, T, nb);             // T = U G
     }
   }
   if (threadIdx.x == 0) desc[blockIdx.x] = d;
 }
 
-// C -= P Q^T, one 64 x 64 block per CTA
+// C -= P Q^T, one 64 x 64 block per CTA (double-float products, like every other tile update)
 __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
   const GemmDesc d = desc[blockIdx.y];
   if (d.r <= 0) return;
-  cta_gemm_blocks(nb, nb, d.r, -1.0, d.P, nb, 0, d.Q, nb, 1, 1.0, d.C, nb, blockIdx.x, gridDim.x, d.lower);
+  cta_gemm_df_blocks(nb, nb, d.r, -1.0, d.P, nb, 0, d.Q, nb, 1, 1.0, d.C, nb, blockIdx.x, gridDim.x, d.lower);
 }
 
 }  // namespace
