@@ -53,7 +53,7 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
-    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k"],
+    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy"],
                    help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent "
                         "regions; n40k: TLR vs dense likelihood at n = 40,000 and kriging of 10% held out")
     p.add_argument("--regions", type=int, default=512)
@@ -291,8 +291,57 @@ def run_n40k(a):
     print(json.dumps(line), flush=True)
 
 
+def run_accuracy(a):
+    """TLR against the dense float64 path of the same library at the full n = 89,900 configuration.
+
+    One evaluation each of l and dl/dtheta (z drawn from the TLR model as in the benchmark); the dense
+    handle stores every tile dense and runs the same kernels with no truncation anywhere."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_1804_09137_gb300 import inputs
+    from paper_1804_09137_gb300 import tlr as T
+
+    dev = torch.device("cuda")
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(a.side)
+    obs, _ = inputs.holdout(len(x), 100)
+    xo, yo = t64(x[obs]), t64(y[obs])
+    res = {}
+    h = T.Handle(xo, yo, nb=a.nb, eps=a.eps, rank_cap=a.rank_cap)
+    h.factor(THETA)
+    z = h.sample(t64(inputs.standard_normal(len(obs))))
+    for name, eps in (("tlr", a.eps), ("dense", -1.0)):
+        if name == "dense":
+            h.close()
+            torch.cuda.empty_cache()
+            h = T.Handle(xo, yo, nb=a.nb, eps=-1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.factor(THETA)
+        ll, g = h.loglik_grad(z)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        h.check()
+        res[name] = {"loglik": float(ll.item()), "grad": [float(v) for v in g.cpu().numpy()], "seconds": secs}
+        log(name, res[name])
+    h.close()
+    ld, lt = res["dense"]["loglik"], res["tlr"]["loglik"]
+    gd, gt = np.array(res["dense"]["grad"]), np.array(res["tlr"]["grad"])
+    line = {"metric": "TLR vs dense FP64 at n=89,900: relative error of l and of dl/dtheta", "n": len(obs),
+            "nb": a.nb, "eps": a.eps, "theta": list(THETA), "loglik_rel_err": abs(lt - ld) / abs(ld),
+            "grad_rel_err": [float(v) for v in np.abs(gt - gd) / np.abs(gd)],
+            "grad_rel_err_norm": float(np.linalg.norm(gt - gd) / np.linalg.norm(gd)),
+            "seconds": {"tlr": res["tlr"]["seconds"], "dense": res["dense"]["seconds"]}, "result": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
+    if a.workload == "accuracy" and a.impl != "reference":
+        return run_accuracy(a)
     if a.workload == "n40k" and a.impl != "reference":
         return run_n40k(a)
     if a.impl == "reference":
