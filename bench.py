@@ -62,7 +62,7 @@ def args_():
     p.add_argument("--nb", type=int, default=900)
     p.add_argument("--eps", type=float, default=1e-7)
     p.add_argument("--rank-cap", type=int, default=256)
-    p.add_argument("--dense-side", type=int, default=150, help="grid side of the dense FP64 comparator run")
+    p.add_argument("--dense-side", type=int, default=212, help="grid side of the dense FP64 comparator run")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-side", type=int, default=40, help="grid side of the CPU oracle sample")
@@ -235,8 +235,9 @@ def run_n40k(a):
     """200 x 200 jittered grid, theta = (1, 0.1, 0.5), nb = 800, eps = 1e-9, rank cap 200; 10% held out.
 
     One likelihood evaluation on the 36,000 observed points in TLR form and in dense float64 (same library,
-    every tile dense), their relative difference, and the kriging MSE of the 4,000 held-out values (the
-    paper's Sec. VIII-D1 reports an average MSE of 0.036 at beta = 0.1 for 100 held-out of 40K points)."""
+    every tile dense), their relative difference, the kriging MSE of the 4,000 held-out values (the
+    paper's Sec. VIII-D1 reports an average MSE of 0.036 at beta = 0.1 for 100 held-out of 40K points)
+    and their prediction variances."""
     import torch
 
     import __graft_entry__ as ge
@@ -272,8 +273,17 @@ def run_n40k(a):
         h.check()
         pred = h.predict(zo, t64(x[held]), t64(y[held]))
         mse = float(((pred - zh) ** 2).mean().item())
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        var = h.predict_var(t64(x[held]), t64(y[held]))
+        torch.cuda.synchronize()
+        var_s = time.perf_counter() - t1
+        h.check()
+        # standardised errors of a calibrated predictor have mean square 1
+        calib = float((((pred - zh) ** 2) / var.clamp_min(1e-300)).mean().item())
         res[name] = {"loglik": float(out[0].item()), "seconds": secs, "mse": mse,
-                     "ranks": h.rank_stats() if name == "tlr" else None}
+                     "mean_pred_var": float(var.mean().item()), "pred_var_seconds": var_s,
+                     "standardised_mse": calib, "ranks": h.rank_stats() if name == "tlr" else None}
         log(name, res[name])
         h.close()
     rel = abs(res["tlr"]["loglik"] - res["dense"]["loglik"]) / abs(res["dense"]["loglik"])

@@ -122,6 +122,15 @@ int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, double* d_grad3
 int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_new,
                 const double* y_new, double* z_new, tlr_stream_t stream);
 
+/* Prediction variance of eq. 4's predictor (Sec. III: the conditional
+ * covariance Sigma_11 - Sigma_12 Sigma_22^{-1} Sigma_21, its diagonal):
+ * var_new[i] = sigma2 - |L^{-1} sigma_i|^2 with sigma_i the covariances between
+ * new point i and the observed points, L the handle's factor.  x_new, y_new:
+ * m doubles each; var_new: m doubles (device).  One tile forward solve on the
+ * same factor per new point (sigma_i generated on the fly). */
+int tlr_predict_var(tlr_handle h, int64_t m, const double* x_new, const double* y_new,
+                    double* var_new, tlr_stream_t stream);
+
 /* Synthetic measurements of Sec. VIII-D: z = L e on the factored handle. */
 int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream);
 

@@ -68,6 +68,15 @@ def krige(x_obs, y_obs, z_obs, x_new, y_new, theta) -> np.ndarray:
     return S12 @ sl.cho_solve(sl.cho_factor(S22, lower=True), z_obs)
 
 
+def krige_var(x_obs, y_obs, x_new, y_new, theta) -> np.ndarray:
+    """Prediction variance of eq. 4's predictor (Sec. III, the conditional covariance
+    Sigma_11 - Sigma_12 Sigma_22^{-1} Sigma_21): its diagonal at the new locations."""
+    S22 = covariance(x_obs, y_obs, theta)
+    S12 = covariance(x_new, y_new, theta, x_obs, y_obs)
+    W = sl.solve_triangular(sl.cholesky(S22, lower=True), S12.T, lower=True)
+    return theta[0] - np.sum(W * W, axis=0)
+
+
 def sample(x, y, theta, e) -> np.ndarray:
     """z = L e with Sigma(theta) = L L^T (Sec. VIII-D, 'exact computation')."""
     L = sl.cholesky(covariance(x, y, theta), lower=True)

@@ -413,6 +413,37 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
   return TLR_OK;
 }
 
+int tlr_predict_var(tlr_handle h, int64_t m, const double* x_new, const double* y_new, double* var_new,
+                    tlr_stream_t stream) {
+  if (!h) return -1;
+  if (m < 0) return -2;
+  if (!x_new && m > 0) return -3;
+  if (!y_new && m > 0) return -4;
+  if (!var_new && m > 0) return -5;
+  if (h->state != 3) return TLR_ERR_STATE;
+  if (m == 0) return TLR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  // the table must cover distances to the new points (as for tlr_predict)
+  std::vector<double> hx(m + 2), hy(m + 2);
+  TLR_CUDA_TRY(cudaMemcpyAsync(hx.data(), x_new, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(hy.data(), y_new, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  {
+    std::vector<double> ox(h->n), oy(h->n);
+    TLR_CUDA_TRY(cudaMemcpyAsync(ox.data(), h->x, h->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaMemcpyAsync(oy.data(), h->y, h->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    hx[m] = *std::min_element(ox.begin(), ox.end());
+    hx[m + 1] = *std::max_element(ox.begin(), ox.end());
+    hy[m] = *std::min_element(oy.begin(), oy.end());
+    hy[m + 1] = *std::max_element(oy.begin(), oy.end());
+  }
+  if (set_table_range(h, bbox_diag(hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
+  PhaseScope ps("predict_var", s);
+  TRY(tlr_predict_var_sorted(h, m, x_new, y_new, var_new, s));
+  return TLR_OK;
+}
+
 int tlr_status(tlr_handle h, int64_t* info) {
   if (!h) return -1;
   TLR_CUDA_TRY(cudaStreamSynchronize(h->last_stream));

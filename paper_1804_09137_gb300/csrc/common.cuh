@@ -284,9 +284,9 @@ int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s);
 int tlr_reduce_loglik(tlr_ctx* h, const double* w, double* out3, cudaStream_t s);
-int tlr_grad_quad(tlr_ctx* h, const double* a, double* out2, cudaStream_t s);
 int tlr_inverse(tlr_ctx* h, cudaStream_t s);
 int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s);
+int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s);
 int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,
               cudaStream_t s);
 int tlr_permute_in(tlr_ctx* h, const double* src, double* dst, cudaStream_t s);

@@ -1,8 +1,11 @@
 // Triangular solves on the TLR factor, log-determinant and quadratic form of
-// eq. 1, z = L e (Sec. VIII-D), kriging of eq. 4 and the quadratic part of the
-// likelihood gradient.  Reductions are two-stage (per-block partials summed in
+// eq. 1, z = L e (Sec. VIII-D), kriging of eq. 4 and its prediction variance.  Reductions are two-stage (per-block partials summed in
 // a fixed order) so results are bitwise reproducible run to run.
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "tile.cuh"
 
@@ -266,60 +269,31 @@ __global__ void k_krige(const double* __restrict__ tab, const MaternParams mp, c
   if (threadIdx.x == 0) zn[a] = acc;
 }
 
-// quadratic gradient part: per block partials of sum_{a > b} x_a x_b dC/dtheta_p(r_ab), p = beta, nu.
-// Block (I, J, sub): tile pair I >= J, rows of tile I split over gridDim.y sub-blocks.
-__global__ void k_grad_quad(const double* __restrict__ tab_g, const MaternParams mp, const double* __restrict__ x,
-                            const double* __restrict__ y, int64_t n, int nb, const double* __restrict__ av,
-                            double* __restrict__ part) {
-  __shared__ double tb[2 * TAB_NINT * TAB_NC];
-  __shared__ double sh[TLR_THREADS / 32 + 2];
-  for (int e = threadIdx.x; e < 2 * TAB_NINT * TAB_NC; e += blockDim.x) tb[e] = tab_g[TAB_NINT * TAB_NC + e];
-  __syncthreads();
-  const int64_t tp = blockIdx.x;  // tile pair index over I >= J: tp = I(I+1)/2 + J
-  int I = (int)((sqrt(8.0 * (double)tp + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(I + 1) * (I + 2) / 2 <= tp) ++I;
-  while ((int64_t)I * (I + 1) / 2 > tp) --I;
-  const int J = (int)(tp - (int64_t)I * (I + 1) / 2);
-  const int64_t a0 = (int64_t)I * nb, b0 = (int64_t)J * nb;
-  double gb = 0.0, gn = 0.0;
-  const int nsub = gridDim.y;
-  for (int ra = blockIdx.y; ra < nb; ra += nsub) {
-    const int64_t a = a0 + ra;
-    if (a >= n) break;
-    const double xa = x[a], ya = y[a], wa = av[a];
-    const int bend = (I == J) ? ra : nb;  // strictly lower within a diagonal tile pair
-    for (int rb = threadIdx.x; rb < bend; rb += blockDim.x) {
-      const int64_t b = b0 + rb;
-      if (b >= n) break;
-      const double dx = xa - x[b], dy = ya - y[b];
-      const double r = sqrt(dx * dx + dy * dy);
-      const double ww = wa * av[b];
-      if (r > 0.0) {
-        double t;
-        const int j = tab_locate(r, mp.e_lo, &t);
-        if (j >= 0 && j < TAB_NINT) {
-          gb = fma(ww, tab_poly(tb + (size_t)j * TAB_NC, t), gb);
-          gn = fma(ww, tab_poly(tb + (size_t)(TAB_NINT + j) * TAB_NC, t), gn);
-        }
-      }
+// B[i * ldb + b] = C(|s_b - p_i|) for sorted point b < n, 0 on the padded rows (b < npad)
+__global__ void k_cov_block(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
+                            const double* __restrict__ y, int64_t n, int64_t npad, const double* __restrict__ xn,
+                            const double* __restrict__ yn, double* __restrict__ B, int64_t ldb) {
+  const int64_t i = blockIdx.y;
+  const double px = xn[i], py = yn[i];
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npad; b += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (b < n) {
+      const double dx = px - x[b], dy = py - y[b];
+      v = matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy));
     }
-  }
-  gb = block_sum(gb, sh);
-  gn = block_sum(gn, sh);
-  if (threadIdx.x == 0) {
-    const size_t id = (size_t)blockIdx.x * gridDim.y + blockIdx.y;
-    part[2 * id] = gb;
-    part[2 * id + 1] = gn;
+    B[i * ldb + b] = v;
   }
 }
 
-__global__ void k_sum_pairs(const double* __restrict__ part, int64_t cnt, double* __restrict__ out2) {
+// var[i] = sigma2 - sum_b W[b, i]^2 (one CTA per column)
+__global__ void k_colvar(const double* __restrict__ W, int64_t ldw, int64_t rows, double sigma2,
+                         double* __restrict__ var) {
   __shared__ double sh[TLR_THREADS / 32 + 2];
-  double s0 = 0.0, s1 = 0.0;
-  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) { s0 += part[2 * i]; s1 += part[2 * i + 1]; }
-  s0 = block_sum(s0, sh);
-  s1 = block_sum(s1, sh);
-  if (threadIdx.x == 0) { out2[0] = s0; out2[1] = s1; }
+  const double* w = W + (int64_t)blockIdx.x * ldw;
+  double acc = 0.0;
+  for (int64_t b = threadIdx.x; b < rows; b += blockDim.x) acc = fma(w[b], w[b], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) var[blockIdx.x] = sigma2 - acc;
 }
 
 }  // namespace
@@ -414,15 +388,21 @@ int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const do
   return TLR_OK;
 }
 
-int tlr_grad_quad(tlr_ctx* h, const double* a, double* out2, cudaStream_t s) {
-  const int64_t pairs = (int64_t)h->nt * (h->nt + 1) / 2;
-  const int nsub = 8;
-  const int64_t cnt = pairs * nsub;
-  if ((size_t)(2 * cnt) > h->scratch_elems) return TLR_ERR_OOM;
-  dim3 grid((unsigned)pairs, nsub);
-  k_grad_quad<<<grid, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, h->nb, a, h->scratch);
-  TLR_LAUNCH_CHECK();
-  k_sum_pairs<<<1, 256, 0, s>>>(h->scratch, cnt, out2);
-  TLR_LAUNCH_CHECK();
+
+// Prediction variance at m new points (sorted-order observations): for each new point
+// w = L^{-1} sigma_i by the tile forward solve of the likelihood (sigma_i generated on the
+// fly), var_i = sigma2 - |w|^2.
+int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s) {
+  const int64_t npad = h->npad;
+  double* w = h->d_vec + 2 * npad;  // the third work vector (the first two hold a = Sigma^{-1} z and L^{-1} z)
+  const dim3 gcov((unsigned)std::min<int64_t>((npad + 255) / 256, 64), 1);
+  for (int64_t i = 0; i < m; ++i) {
+    k_cov_block<<<gcov, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, npad, xn + i, yn + i, w, npad);
+    TLR_LAUNCH_CHECK();
+    int rc = tlr_fwd_solve(h, w, s);
+    if (rc) return rc;
+    k_colvar<<<1, 256, 0, s>>>(w, npad, npad, h->mp.sigma2, var + i);
+    TLR_LAUNCH_CHECK();
+  }
   return TLR_OK;
 }

@@ -42,7 +42,7 @@ _lib = None
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
            "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
-           "tlr_loglik_grad_batched",
+           "tlr_loglik_grad_batched", "tlr_predict_var",
            "tlr_profile_read"]
 
 
@@ -63,6 +63,7 @@ def lib():
     L.tlr_loglik.argtypes = [vp, vp, vp, vp]
     L.tlr_loglik_grad.argtypes = [vp, vp, vp, vp, vp]
     L.tlr_predict.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    L.tlr_predict_var.argtypes = [vp, i64, vp, vp, vp, vp]
     L.tlr_sample.argtypes = [vp, vp, vp, vp]
     L.tlr_status.argtypes = [vp, C.POINTER(i64)]
     L.tlr_rank_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
@@ -162,6 +163,13 @@ class Handle:
         out = torch.empty(m, dtype=torch.float64, device=self.dev) if out is None else out
         _check("tlr_predict", lib().tlr_predict(self._h, _ptr(z_obs), m, _ptr(x_new), _ptr(y_new), _ptr(out),
                                                 _stream()))
+        return out
+
+    def predict_var(self, x_new, y_new, out=None):
+        """Prediction variance sigma2 - Sigma_12 Sigma_22^{-1} Sigma_21 (diagonal) at the new points."""
+        m = int(x_new.numel())
+        out = torch.empty(m, dtype=torch.float64, device=self.dev) if out is None else out
+        _check("tlr_predict_var", lib().tlr_predict_var(self._h, m, _ptr(x_new), _ptr(y_new), _ptr(out), _stream()))
         return out
 
     def sample(self, e, out=None):

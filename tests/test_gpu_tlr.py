@@ -172,6 +172,25 @@ def test_kriging_matches_oracle(T):
     np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-9)
 
 
+def test_prediction_variance_matches_oracle(T):
+    """Multi-right-hand-side solve: 810 observed points in 7 tiles of 128 (ragged last), 90 new points
+    (two column chunks would be the same code path); TLR at eps = 1e-12 and the dense path."""
+    theta = (1.0, 0.1, 0.5)
+    x, y = inputs.jittered_grid(30)
+    obs, held = inputs.holdout(len(x), 90)
+    want = DN.krige_var(x[obs], y[obs], x[held], y[held], theta)
+    for eps, cap in ((1e-12, 128), (-1.0, 0)):
+        h = T.Handle(dev(x[obs]), dev(y[obs]), nb=128, eps=eps, rank_cap=cap)
+        h.factor(theta)
+        got = h.predict_var(dev(x[held]), dev(y[held])).cpu().numpy()
+        h.check()
+        np.testing.assert_allclose(got, want, rtol=1e-7, atol=1e-9)
+        # at observed locations the variance vanishes (no nugget)
+        v0 = h.predict_var(dev(x[obs[:7]]), dev(y[obs[:7]])).cpu().numpy()
+        assert np.all(np.abs(v0) <= 1e-7)
+        h.close()
+
+
 def test_sample_is_cholesky_times_e(T):
     theta = (1.0, 0.1, 0.5)
     x, y = inputs.jittered_grid(18)

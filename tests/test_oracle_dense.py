@@ -100,3 +100,34 @@ def test_sample_covariance_factor():
     Z = np.stack([DN.sample(x, y, TH, E[:, i]) for i in range(len(x))], axis=1)  # = L
     np.testing.assert_allclose(Z @ Z.T, S, atol=1e-13)
     assert np.allclose(np.triu(Z, 1), 0)
+
+
+def test_krige_var_one_and_two_points_by_hand():
+    """Conditional variance sigma2 - c^T K^{-1} c written out for one and two observed points (nu = 1/2:
+    C(r) = sigma2 exp(-r / beta))."""
+    s2, be = 1.7, 0.2
+    th = (s2, be, 0.5)
+    xo, yo = np.array([0.1]), np.array([0.2])
+    xn, yn = np.array([0.25]), np.array([0.1])
+    r = np.hypot(0.15, -0.1)
+    c = s2 * np.exp(-r / be)
+    assert abs(DN.krige_var(xo, yo, xn, yn, th)[0] - (s2 - c * c / s2)) <= 1e-14
+    xo2, yo2 = np.array([0.1, 0.4]), np.array([0.2, 0.3])
+    k12 = s2 * np.exp(-np.hypot(0.3, 0.1) / be)
+    c1 = s2 * np.exp(-np.hypot(0.15, -0.1) / be)
+    c2 = s2 * np.exp(-np.hypot(-0.15, -0.2) / be)
+    det = s2 * s2 - k12 * k12
+    quad = (s2 * c1 * c1 - 2 * k12 * c1 * c2 + s2 * c2 * c2) / det
+    assert abs(DN.krige_var(xo2, yo2, xn, yn, th)[0] - (s2 - quad)) <= 1e-13
+
+
+def test_krige_var_interpolation_far_field_and_bounds():
+    """Zero at an observed location (no nugget), sigma2 far from every observation, inside [0, sigma2]."""
+    x, y, _ = _problem(12)
+    obs, held = inputs.holdout(len(x), 20)
+    v_obs = DN.krige_var(x[obs], y[obs], x[obs[:5]], y[obs[:5]], TH)
+    assert np.all(np.abs(v_obs) <= 1e-8)
+    v_far = DN.krige_var(x[obs], y[obs], np.array([60.0]), np.array([60.0]), TH)
+    assert abs(v_far[0] - TH[0]) <= 1e-12
+    v = DN.krige_var(x[obs], y[obs], x[held], y[held], TH)
+    assert np.all(v >= -1e-10) and np.all(v <= TH[0] + 1e-12)
