@@ -195,7 +195,8 @@ __device__ void cta_apply_q_df(const dfloat* __restrict__ A, int lda, int m, int
   }
 }
 
-// C[0:m, 0:n] = beta C + alpha op(A) op(B) like cta_gemm_blocks, with the
+// C[0:m, 0:n] = beta C + alpha op(A) op(B) (op(X) = X^T when tX), column-major, in 64 x 64
+// blocks blk0, blk0 + nblk_step, ... (lower_only: blocks on or below the diagonal), with the
 // products accumulated in double-float (Dot2) on the float32 pipe; inputs are
 // split to double-float as they are staged in shared memory.
 __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double alpha, const double* __restrict__ A,
@@ -262,74 +263,6 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
 __device__ __forceinline__ void cta_gemm_df(int m, int n, int k, double alpha, const double* A, int lda, int tA,
                                             const double* B, int ldb, int tB, double beta, double* C, int ldc) {
   cta_gemm_df_blocks(m, n, k, alpha, A, lda, tA, B, ldb, tB, beta, C, ldc, 0, 1, 0);
-}
-
-// round-robin pairing: round rr of K2-1, pair pi of K2/2
-__device__ __forceinline__ void rr_pair(int K2, int rr, int pi, int* p, int* q) {
-  const int L = K2 - 1;
-  auto el = [&](int pos) { return ((pos - rr) % L + L) % L + 1; };
-  if (pi == 0) { *p = 0; *q = el(0); }
-  else { *p = el(pi); *q = el(L - pi); }
-}
-
-// one-sided Jacobi: M (K x K, ld K) <- M Y with orthogonal columns, Y (K x K) accumulated
-__device__ void cta_jacobi(double* __restrict__ M, double* __restrict__ Y, int K, int* sh_flag, double* flops) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) Y[e] = ((e % K) == (e / K)) ? 1.0 : 0.0;
-  __syncthreads();
-  if (K < 2) return;
-  const int K2 = K + (K & 1);
-  double fl = 0.0;  // per-warp count, lane 0 holds it
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (threadIdx.x == 0) *sh_flag = 0;
-    __syncthreads();
-    int rotated = 0;
-    for (int rr = 0; rr < K2 - 1; ++rr) {
-      for (int pi = warp; pi < K2 / 2; pi += nw) {
-        int p, q;
-        rr_pair(K2, rr, pi, &p, &q);
-        if (p >= K || q >= K) continue;
-        double* mp = M + (size_t)p * K;
-        double* mq = M + (size_t)q * K;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < K; r += 32) {
-          const double a = mp[r], b = mq[r];
-          al = fma(a, a, al);
-          be = fma(b, b, be);
-          ga = fma(a, b, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        fl += 6.0 * K;
-        if (al > 0.0 && be > 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
-          fl += 12.0 * K;
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          for (int r = lane; r < K; r += 32) {
-            const double a = mp[r], b = mq[r];
-            mp[r] = c * a - s * b;
-            mq[r] = s * a + c * b;
-          }
-          double* yp = Y + (size_t)p * K;
-          double* yq = Y + (size_t)q * K;
-          for (int r = lane; r < K; r += 32) {
-            const double a = yp[r], b = yq[r];
-            yp[r] = c * a - s * b;
-            yq[r] = s * a + c * b;
-          }
-          rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (rotated && lane == 0) atomicOr(sh_flag, 1);
-    __syncthreads();
-    if (*sh_flag == 0) break;
-    __syncthreads();
-  }
-  if (lane == 0 && flops) atomicAdd(flops, fl);
 }
 
 // Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
