@@ -151,11 +151,18 @@ def cpu_oracle_sample(side):
     return time.perf_counter() - t, len(x)
 
 
+def main_config(a, n_obs, held, parallelism):
+    """The configuration both arms report: the n = 89,900 TLR workload."""
+    return {"workload": f"matern_tlr_n{n_obs}_nb{a.nb}_eps{a.eps:g}_theta1-0.3-1.0", "n": n_obs, "nb": a.nb,
+            "eps": a.eps, "rank_cap": a.rank_cap, "theta": list(THETA), "kriging_points": held,
+            "l2": "inputs larger than L2 (TLR factor > 1 GB)", "parallelism": parallelism}
+
+
 def run_reference(a):
     world, rank, _ = dist()
     if rank != 0:
         return
-    n_full = a.side * a.side
+    n_full = a.side * a.side - 100  # the evaluated (observed) points of the main arm
     times = []
     for i in range(a.warmup + a.steps):
         dt, ns = cpu_oracle_sample(a.cpu_side)
@@ -167,7 +174,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"matern_n{n_full}", "n": n_full},
+            "config": main_config(a, n_full, 100, "single"),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"dense float64 oracle loglik+grad at n={ns} ({a.cpu_side}^2 grid), "
                                        f"mean of {a.steps} runs {statistics.mean(times):.3f} s, scaled by "
@@ -375,8 +382,8 @@ def main():
     dev = torch.device("cuda", local)
     t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
     x, y = inputs.jittered_grid(a.side)
-    n = len(x)
-    obs, held = inputs.holdout(n, 100)
+    obs, held = inputs.holdout(len(x), 100)
+    n = len(obs)  # the evaluated points
     xo, yo = t64(x[obs]), t64(y[obs])
     xh, yh = t64(x[held]), t64(y[held])
     h = T.Handle(xo, yo, nb=a.nb, eps=a.eps, rank_cap=a.rank_cap)
@@ -508,10 +515,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (jittered grid, z drawn from the model)",
-            "config": {"workload": f"matern_tlr_n{len(obs)}_nb{a.nb}_eps{a.eps:g}_theta1-0.3-1.0",
-                       "n": len(obs), "nb": a.nb, "eps": a.eps, "rank_cap": a.rank_cap, "theta": list(THETA),
-                       "kriging_points": len(held), "l2": "inputs larger than L2 (TLR factor > 1 GB)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": main_config(a, len(obs), len(held), "replicas" if world > 1 else "single"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "dense_fp64_gpu": dense,
             "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,
