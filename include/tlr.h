@@ -60,7 +60,11 @@ typedef struct {
  * product would land on them during the factorization; inv_scale: the
  * gradient's inverse keeps L^{-1} in tile low-rank form truncated at
  * inv_scale * eps * zeta^(1/2), zeta = the largest 1 / L_aa^2 (0 = 0.1);
- * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile. */
+ * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile.
+ * metric: 0 = Euclidean distance; 1 = great-circle distance of eq. 6 (Sec. IV,
+ * haversine) with x = longitude and y = latitude in degrees (also for the new
+ * points of tlr_predict / tlr_predict_var) on a sphere of the given radius
+ * (radius <= 0 = 1: distances in radians); beta is in the units of the distance. */
 typedef struct {
   int nb;
   double eps;
@@ -69,6 +73,8 @@ typedef struct {
   int order;
   int dense_rank;
   double inv_scale;
+  int metric;
+  double radius;
 } tlr_opts;
 
 enum {

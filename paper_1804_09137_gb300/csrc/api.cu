@@ -120,6 +120,13 @@ double bbox_diag(const double* x, const double* y, size_t n) {
   return hypot(x1 - x0, y1 - y0);
 }
 
+// largest distance the table must cover: the bounding-box diagonal, or for the
+// great-circle distance half the circumference (no two points are farther apart)
+double dist_range(const tlr_ctx* h, const double* x, const double* y, size_t n) {
+  if (h->mp.metric == 1) return M_PI * h->mp.radius;
+  return bbox_diag(x, y, n);
+}
+
 template <class T>
 int dmalloc(T** p, size_t count) {
   if (count == 0) count = 1;
@@ -164,7 +171,7 @@ int bind_points(tlr_ctx* h, int64_t n, const std::vector<double>& hx, const std:
   for (int64_t s2 = 0; s2 < n; ++s2) { sx[s2] = hx[perm[s2]]; sy[s2] = hy[perm[s2]]; }
   h->mp.e_lo = 0;
   h->tab_valid = 0;
-  set_table_range(h, bbox_diag(hx.data(), hy.data(), n));
+  set_table_range(h, dist_range(h, hx.data(), hy.data(), n));
   h->state = 0;
   h->zplan_valid = 0;
   cudaError_t e1 = cudaMemcpyAsync(h->x, sx.data(), h->npad * sizeof(double), cudaMemcpyHostToDevice, s);
@@ -193,6 +200,9 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   memset(h, 0, sizeof(*h));
   h->opts = *opts;
   h->nb = opts->nb;
+  h->mp.metric = opts->metric == 1 ? 1 : 0;
+  h->mp.radius = opts->radius > 0 ? opts->radius : 1.0;
+  h->mp.rad = M_PI / 180.0;
   h->cap_n = n;
   h->cap_nt = (int)((n + h->nb - 1) / h->nb);
   h->cap_ntiles = (int64_t)h->cap_nt * (h->cap_nt - 1) / 2;
@@ -252,6 +262,8 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   if (!x) return -2;
   if (!y) return -3;
   if (!opts || opts->nb <= 0 || opts->rank_cap < 0 || !(opts->eps == opts->eps)) return -4;
+  if (opts->metric != 0 && opts->metric != 1) return -4;
+  if (opts->metric == 1 && !(opts->radius == opts->radius)) return -4;
   if (!out) return -6;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
@@ -403,7 +415,7 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
     by[1] = *std::max_element(oy.begin(), oy.end());
   }
   hx[m] = bx[0]; hy[m] = by[0]; hx[m + 1] = bx[1]; hy[m + 1] = by[1];
-  if (set_table_range(h, bbox_diag(hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
+  if (set_table_range(h, dist_range(h, hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
   double* a = h->d_vec;
   PhaseScope ps("predict", s);
   TRY(tlr_permute_in(h, z_obs, a, s));
@@ -438,7 +450,7 @@ int tlr_predict_var(tlr_handle h, int64_t m, const double* x_new, const double* 
     hy[m] = *std::min_element(oy.begin(), oy.end());
     hy[m + 1] = *std::max_element(oy.begin(), oy.end());
   }
-  if (set_table_range(h, bbox_diag(hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
+  if (set_table_range(h, dist_range(h, hx.data(), hy.data(), m + 2))) TRY(tlr_build_table(h, s));
   PhaseScope ps("predict_var", s);
   TRY(tlr_predict_var_sorted(h, m, x_new, y_new, var_new, s));
   return TLR_OK;

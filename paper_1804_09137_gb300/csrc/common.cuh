@@ -50,6 +50,9 @@ struct MaternParams {
   double cnu;    // 1 / (2^(nu-1) Gamma(nu))
   double psi;    // digamma(nu)
   int e_lo;      // table covers [2^e_lo, 2^(e_lo + TAB_OCT))
+  int metric;    // 0 Euclidean, 1 great circle (x = longitude, y = latitude, degrees)
+  double radius; // sphere radius of the great-circle distance
+  double rad;    // pi / 180
 };
 
 struct tlr_ctx {
@@ -239,14 +242,27 @@ __device__ __forceinline__ double matern_tab(const double* __restrict__ tab, con
   return tab_poly(tab + ((size_t)f * TAB_NINT + j) * TAB_NC, t);
 }
 
+// distance between (xa, ya) and (xb, yb): Euclidean, or the great-circle distance of
+// eq. 6 (Sec. IV), hav(d / r) = hav(phi_b - phi_a) + cos(phi_a) cos(phi_b) hav(lam_b - lam_a),
+// with hav(t) = sin^2(t / 2), longitude lam = x and latitude phi = y in degrees
+__device__ __forceinline__ double pt_dist(const MaternParams& mp, double xa, double ya, double xb, double yb) {
+  if (mp.metric == 0) {
+    const double dx = xa - xb, dy = ya - yb;
+    return sqrt(dx * dx + dy * dy);
+  }
+  const double pa = ya * mp.rad, pb = yb * mp.rad;
+  const double sp = sin(0.5 * (pb - pa)), sl = sin(0.5 * (xb - xa) * mp.rad);
+  const double h = fma(cos(pa) * cos(pb), sl * sl, sp * sp);
+  return 2.0 * mp.radius * asin(sqrt(fmin(h, 1.0)));
+}
+
 // covariance between sorted points p and q (padded points are identity points)
 __device__ __forceinline__ double cov_pts(const double* __restrict__ tab, const MaternParams& mp,
                                           const double* __restrict__ x, const double* __restrict__ y,
                                           int64_t n, int64_t p, int64_t q) {
   if (p >= n || q >= n) return (p == q) ? 1.0 : 0.0;
   if (p == q) return mp.sigma2;
-  const double dx = x[p] - x[q], dy = y[p] - y[q];
-  return matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy));
+  return matern_tab(tab, mp, 0, pt_dist(mp, x[p], y[p], x[q], y[q]));
 }
 
 // profiling of the low-rank update kernel (the dominant one): per-launch CUDA

@@ -86,8 +86,7 @@ __global__ void k_grad_fused(TlrView z, const double* __restrict__ tab, const Ma
         if (I == J && b > a) continue;
         const double zab = Zd ? Zd[(size_t)b * nb + a] : acc[i][j];
         if (I == J && a == b) continue;  // dC_beta(0) = dC_nu(0) = 0
-        const double dx = xa - x[pb], dy = ya - y[pb];
-        const double r = sqrt(dx * dx + dy * dy);
+        const double r = pt_dist(mp, xa, ya, x[pb], y[pb]);
         const double w = wa * al[pb] - zab;
         if (r > 0.0) {
           double t;

@@ -262,8 +262,7 @@ __global__ void k_krige(const double* __restrict__ tab, const MaternParams mp, c
   const double px = xn[a], py = yn[a];
   double acc = 0.0;
   for (int64_t b = threadIdx.x; b < n; b += blockDim.x) {
-    const double dx = px - x[b], dy = py - y[b];
-    acc = fma(matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy)), alpha[b], acc);
+    acc = fma(matern_tab(tab, mp, 0, pt_dist(mp, px, py, x[b], y[b])), alpha[b], acc);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) zn[a] = acc;
@@ -278,8 +277,7 @@ __global__ void k_cov_block(const double* __restrict__ tab, const MaternParams m
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npad; b += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
     if (b < n) {
-      const double dx = px - x[b], dy = py - y[b];
-      v = matern_tab(tab, mp, 0, sqrt(dx * dx + dy * dy));
+      v = matern_tab(tab, mp, 0, pt_dist(mp, px, py, x[b], y[b]));
     }
     B[i * ldb + b] = v;
   }

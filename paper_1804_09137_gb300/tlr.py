@@ -22,7 +22,8 @@ ERR_NAMES = {1: "not SPD", 2: "rank cap exceeded", 3: "out of memory", 4: "CUDA 
 
 class TlrOpts(C.Structure):
     _fields_ = [("nb", C.c_int), ("eps", C.c_double), ("rank_cap", C.c_int), ("truncate_at_cap", C.c_int),
-                ("order", C.c_int), ("dense_rank", C.c_int), ("inv_scale", C.c_double)]
+                ("order", C.c_int), ("dense_rank", C.c_int), ("inv_scale", C.c_double), ("metric", C.c_int),
+                ("radius", C.c_double)]
 
 
 class TlrTheta(C.Structure):
@@ -105,10 +106,14 @@ class Handle:
     """Owns one tlr_handle (tile storage on the current CUDA device)."""
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, nb: int, eps: float = 1e-9, rank_cap: int = 0,
-                 truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0, inv_scale: float = 0.0):
+                 truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0, inv_scale: float = 0.0,
+                 radius: float | None = None):
+        """radius: None for Euclidean distances; a sphere radius for great-circle distances (eq. 6) with
+        x = longitude and y = latitude in degrees."""
         L = lib()
         self._opts = TlrOpts(int(nb), float(eps), int(rank_cap), int(bool(truncate_at_cap)), int(bool(order)),
-                             int(dense_rank), float(inv_scale))
+                             int(dense_rank), float(inv_scale), 0 if radius is None else 1,
+                             0.0 if radius is None else float(radius))
         h = C.c_void_p()
         _check("tlr_create", L.tlr_create(int(x.numel()), _ptr(x), _ptr(y), C.byref(self._opts), _stream(),
                                           C.byref(h)))

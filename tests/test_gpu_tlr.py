@@ -288,3 +288,24 @@ def test_gradient_finite_differences_of_gpu_loglik(T):
             vals.append(h.loglik(zt).cpu().numpy()[0])
         fd = (vals[0] - vals[1]) / (2 * hp)
         assert abs(g[p] - fd) <= 1e-5 * max(abs(fd), 1.0), (p, g[p], fd)
+
+
+def test_great_circle_distance_matches_oracle(T):
+    """Eq. 6 distances (x = longitude, y = latitude in degrees, radius 6371 km): l in dense mode and in
+    TLR form, and kriging, against the oracle on 576 points of a 20 x 20 degree region."""
+    theta, radius = (1.0, 400.0, 1.0), 6371.0
+    u, v = inputs.jittered_grid(24)
+    lon, lat = 30.0 + 20.0 * u, 10.0 + 20.0 * v
+    z = DN.sample(lon, lat, theta, inputs.standard_normal(len(lon)), radius=radius)
+    obs, held = inputs.holdout(len(lon), 40)
+    want, _, _ = DN.loglik(lon[obs], lat[obs], z[obs], theta, radius=radius)
+    kw = DN.krige(lon[obs], lat[obs], z[obs], lon[held], lat[held], theta, radius=radius)
+    for eps, cap, tol in ((-1.0, 0, 1e-10), (1e-12, 96, 1e-9)):
+        h = T.Handle(dev(lon[obs]), dev(lat[obs]), nb=96, eps=eps, rank_cap=cap, radius=radius)
+        h.factor(theta)
+        got = h.loglik(dev(z[obs]))[0].item()
+        h.check()
+        assert abs(got - want) <= tol * abs(want)
+        kg = h.predict(dev(z[obs]), dev(lon[held]), dev(lat[held])).cpu().numpy()
+        np.testing.assert_allclose(kg, kw, rtol=1e-7, atol=1e-8)
+        h.close()

@@ -131,3 +131,22 @@ def test_krige_var_interpolation_far_field_and_bounds():
     assert abs(v_far[0] - TH[0]) <= 1e-12
     v = DN.krige_var(x[obs], y[obs], x[held], y[held], TH)
     assert np.all(v >= -1e-10) and np.all(v <= TH[0] + 1e-12)
+
+
+def test_great_circle_distance_closed_cases():
+    """Eq. 6 against distances known without the haversine: arcs along the equator and along a
+    meridian, pole to pole, symmetry, and the small-distance limit r sqrt(dphi^2 + cos^2 phi dlam^2)."""
+    r = 6371.0
+    d = DN.distances(np.array([10.0]), np.array([0.0]), np.array([55.0]), np.array([0.0]), r)[0, 0]
+    assert abs(d - r * np.radians(45.0)) <= 1e-9 * r
+    d = DN.distances(np.array([-20.0]), np.array([-30.0]), np.array([-20.0]), np.array([40.0]), r)[0, 0]
+    assert abs(d - r * np.radians(70.0)) <= 1e-9 * r
+    d = DN.distances(np.array([0.0]), np.array([90.0]), np.array([123.0]), np.array([-90.0]), r)[0, 0]
+    assert abs(d - np.pi * r) <= 1e-9 * r
+    xa, ya = np.array([3.0, -70.0, 120.0]), np.array([10.0, 45.0, -60.0])
+    D = DN.distances(xa, ya, xa, ya, r)
+    assert np.allclose(D, D.T, rtol=0, atol=1e-9) and np.all(np.abs(np.diag(D)) <= 1e-9)
+    phi, dphi, dlam = np.radians(50.0), np.radians(1e-3), np.radians(2e-3)
+    d = DN.distances(np.array([7.0]), np.array([50.0]), np.array([7.002]), np.array([50.001]), 1.0)[0, 0]
+    approx = np.sqrt(dphi ** 2 + (np.cos(phi) * dlam) ** 2)
+    assert abs(d - approx) <= 1e-5 * approx
