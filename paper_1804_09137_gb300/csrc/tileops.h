@@ -1,5 +1,5 @@
 // Generic batched tile operations on a TlrView (hybrid dense / low-rank tiles),
-// shared by the Cholesky factorization, the inverse (TRTRI and LAUUM) and the solves.
+// shared by the Cholesky factorization and the inverse (TRTRI and LAUUM).
 #pragma once
 #include "tile.cuh"
 
