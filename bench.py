@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -39,11 +40,20 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22400.json")
 KERNEL_SOURCES = ["tileops.cu", "recompress.cuh", "tile.cuh"]
 
 
+def _code_only(src: str) -> str:
+    """C++ source without comments and whitespace: what the compiler turns into the kernel."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return re.sub(r"\s+", "", src)
+
+
 def kernel_hash():
+    """Hash of the dominant kernel's source code (comments and layout excluded): a DRAM traffic
+    figure measured on another code state is not reported."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1804_09137_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1804_09137_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -223,8 +223,8 @@ int tlr_launch_count(int64_t* count);
 /* enable != 0: from now on time every launch of the low-rank update kernel
  * (the TLR GEMM with recompression, the dominant kernel) with CUDA events on
  * its stream and accumulate its algorithmic float64 flops on the device
- * (Householder QR, core product, Jacobi rotations as executed, applying Q,
- * forming the product); enable == 0 stops.  Either call resets the counters
+ * (Householder QR, core product and its pivoted QR, applying Q, forming the
+ * product); enable == 0 stops.  Either call resets the counters
  * and synchronises the device. */
 int tlr_profile(int enable);
 

@@ -1,10 +1,11 @@
 // Low-rank recompression core shared by the factor and inverse kernels.
 //
 // cta_recompress(Up, Vp, K) replaces the rank-K product Up Vp^T (nb x K
-// factors) by its eps-truncated SVD: Householder QR of both factors, the small
-// core R_u R_v^T, one-sided (Hestenes) Jacobi SVD of the core with round-robin
-// pair ordering, keep the singular values > eps, apply both orthogonal factors
-// back.  One CTA of 256 threads per tile; workspace in global memory (L2).
+// factors) by an eps-truncated rank-revealing factorization: Householder QR of
+// both factors (double-float), the small core M = R_u R_v^T, column-pivoted QR of
+// M stopped when the trailing block's Frobenius norm is <= eps (spectral error
+// <= eps), and both orthogonal factors applied back.  One CTA of 256 threads per
+// tile; workspace in global memory (L2).
 #pragma once
 #include "df.cuh"
 #include "tile.cuh"
@@ -434,8 +435,8 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   }
   __syncthreads();
   if (flops && threadIdx.x == 0) {
-    // Householder QR of two nb x K factors, triangular core product, column norms,
-    // applying both Q to k columns, plus the Jacobi sweeps as executed
+    // Householder QR of two nb x K factors and applying both Q to k columns (the core
+    // product and its pivoted QR were counted above)
     const double m = nb, KK = K, Kq = Ke;
     (void)KK;
     const double qr = 2.0 * (2.0 * m * KK * Kq - (KK + m) * Kq * Kq + 2.0 * Kq * Kq * Kq / 3.0);
