@@ -3,15 +3,16 @@
 
 Workload (the n = 90,000 configuration): 300 x 300 jittered grid on [0,1]^2,
 theta = (sigma2, beta, nu) = (1, 0.3, 1.0), tile size nb = 900, absolute
-threshold eps = 1e-7, float64.  One step is the whole path on one batch:
-Matérn generation, compression of the off-diagonal tiles, TLR Cholesky,
+threshold eps = 1e-7, float64 storage.  One step is the whole path on one
+batch: Matérn generation, compression of the off-diagonal tiles, TLR Cholesky,
 log-determinant and solves (eq. 1), the adjoint gradient (TLR inverse and the
-fused regenerate-and-reduce pass) and kriging of 100 held-out points (eq. 4)
-on the same factor.  z is a draw from the model, z = L e with L the TLR
-factor (synthesised before timing).
+fused regenerate-and-reduce pass) and kriging of 100 new points (eq. 4) on the
+same factor.  z is a draw from the model, z = L e with L the exact Cholesky
+factor of the dense float64 comparator (measured once at the same n before
+the timed region).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead
-(dense float64 likelihood + gradient on a bounded sample, scaled by n^3).
+(dense float64 likelihood + gradient on a bounded sample, scaled to n).
 """
 from __future__ import annotations
 
@@ -63,7 +64,7 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
-    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy"],
+    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy", "accuracy36k"],
                    help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent "
                         "regions; n40k: TLR vs dense likelihood at n = 40,000 and kriging of 10% held out")
     p.add_argument("--regions", type=int, default=512)
@@ -72,7 +73,6 @@ def args_():
     p.add_argument("--nb", type=int, default=900)
     p.add_argument("--eps", type=float, default=1e-7)
     p.add_argument("--rank-cap", type=int, default=256)
-    p.add_argument("--dense-side", type=int, default=212, help="grid side of the dense FP64 comparator run")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-side", type=int, default=40, help="grid side of the CPU oracle sample")
@@ -150,45 +150,68 @@ def replica_throughput(ms_per_step_max: float, world: int) -> float:
 
 
 def cpu_oracle_sample(side):
-    """Seconds of one dense CPU-oracle likelihood+gradient evaluation at n = side^2."""
+    """One dense CPU-oracle likelihood + gradient evaluation at n = side^2.
+
+    Returns (total seconds, seconds of the O(n^2) Matérn and derivative generation (timed as a separate
+    call of the same oracle functions), n)."""
     from oracle import dense as DN
+    from oracle import matern as M
     from paper_1804_09137_gb300 import inputs
 
     x, y = inputs.jittered_grid(side)
     z = DN.sample(x, y, THETA, inputs.standard_normal(len(x)))
     t = time.perf_counter()
     DN.loglik_grad(x, y, z, THETA)
-    return time.perf_counter() - t, len(x)
+    total = time.perf_counter() - t
+    t = time.perf_counter()
+    R = DN.distances(x, y, x, y)
+    M.matern(R, *THETA)
+    M.matern_derivs(R, *THETA)
+    gen = time.perf_counter() - t
+    return total, min(gen, total), len(x)
 
 
-def main_config(a, n_obs, held, parallelism):
-    """The configuration both arms report: the n = 89,900 TLR workload."""
-    return {"workload": f"matern_tlr_n{n_obs}_nb{a.nb}_eps{a.eps:g}_theta1-0.3-1.0", "n": n_obs, "nb": a.nb,
-            "eps": a.eps, "rank_cap": a.rank_cap, "theta": list(THETA), "kriging_points": held,
+def cpu_baseline_line(total, gen, ns, n, steps=1):
+    """Scale a measured oracle run at ns points to n: generation ~ n^2, factorisation and inverse ~ n^3."""
+    t_full = gen * (n / ns) ** 2 + (total - gen) * (n / ns) ** 3
+    return t_full, {"value": 1.0 / t_full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                    "sample": f"dense float64 oracle loglik+grad measured at n={ns} ({int(round(ns ** 0.5))}^2 "
+                              f"grid): {total:.3f} s ({gen:.3f} s of it Matérn/derivative generation); value "
+                              f"scaled to n={n} as gen*(n/{ns})^2 + rest*(n/{ns})^3",
+                    "measured_n": ns, "measured_s": total, "measured_evals_per_s": 1.0 / total,
+                    "extrapolated_s_at_n": t_full, "runs": steps}
+
+
+def main_config(a, n, m_new, parallelism):
+    """The configuration both arms report: the n = 90,000 TLR workload."""
+    return {"workload": f"matern_tlr_n{n}_nb{a.nb}_eps{a.eps:g}_theta1-0.3-1.0", "n": n, "nb": a.nb,
+            "eps": a.eps, "rank_cap": a.rank_cap, "theta": list(THETA), "kriging_points": m_new,
+            "kriging_points_from": "uniform on [0,1]^2, not on the grid",
             "l2": "inputs larger than L2 (TLR factor > 1 GB)", "parallelism": parallelism}
+
+
+PRECISION = {"storage": "f64", "potrf_trsv_logdet_quadform_gradient_sums": "f64",
+             "tile_gemm_householder_qr": "float32 pairs (double-float: ~48-bit significand, float32 exponent "
+                                         "range)"}
 
 
 def run_reference(a):
     world, rank, _ = dist()
     if rank != 0:
         return
-    n_full = a.side * a.side - 100  # the evaluated (observed) points of the main arm
-    times = []
+    n_full = a.side * a.side
+    tot, gen = [], []
     for i in range(a.warmup + a.steps):
-        dt, ns = cpu_oracle_sample(a.cpu_side)
+        t, g, ns = cpu_oracle_sample(a.cpu_side)
         if i >= a.warmup:
-            times.append(dt)
-    scale = (n_full / ns) ** 3
-    t_full = statistics.mean(times) * scale
+            tot.append(t)
+            gen.append(g)
+    t_full, cpu = cpu_baseline_line(statistics.mean(tot), statistics.mean(gen), ns, n_full, a.steps)
     val = 1.0 / t_full
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": main_config(a, n_full, 100, "single"),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"dense float64 oracle loglik+grad at n={ns} ({a.cpu_side}^2 grid), "
-                                       f"mean of {a.steps} runs {statistics.mean(times):.3f} s, scaled by "
-                                       f"(n/{ns})^3 to n={n_full}"},
+            "config": main_config(a, n_full, 100, "single"), "cpu_baseline": cpu,
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -365,12 +388,77 @@ def run_accuracy(a):
     print(json.dumps(line), flush=True)
 
 
+def _host_free_ram_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def run_accuracy36k(a):
+    """Accuracy against true float64 at scale: the 40k configuration (200 x 200 grid, theta = (1, 0.1, 0.5),
+    nb = 800, 10% held out: n = 36,000 observed).  The CPU oracle's dense float64 l (scipy kv, LAPACK
+    Cholesky) against the library's TLR l at eps = 1e-7 and 1e-9 and its dense path (float-float tile GEMMs).
+    Needs about 80 GB of host memory for the oracle's dense matrices; refuses to start with less."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from oracle import dense as DN
+    from paper_1804_09137_gb300 import inputs
+    from paper_1804_09137_gb300 import tlr as T
+
+    need = 90.0
+    if _host_free_ram_gb() < need:
+        print(json.dumps({"workload": "accuracy36k", "skipped": f"needs {need:.0f} GB of free host memory, "
+                                                                  f"{_host_free_ram_gb():.0f} GB available"}))
+        return
+    theta = (1.0, 0.1, 0.5)
+    dev = torch.device("cuda")
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(200)
+    obs, _ = inputs.holdout(len(x), len(x) // 10)
+    xo, yo = x[obs], y[obs]
+    res = {}
+    hd = T.Handle(t64(xo), t64(yo), nb=800, eps=-1.0)
+    hd.factor(theta)
+    z = hd.sample(t64(inputs.standard_normal(len(obs))))  # z = L e from the dense factor (input only)
+    out = hd.loglik(z).cpu().numpy()
+    hd.check()
+    hd.close()
+    res["gpu_dense"] = [float(v) for v in out]
+    for eps in (1e-7, 1e-9):
+        h = T.Handle(t64(xo), t64(yo), nb=800, eps=eps, rank_cap=400)
+        h.factor(theta)
+        res[f"gpu_tlr_eps{eps:g}"] = [float(v) for v in h.loglik(z).cpu().numpy()]
+        h.check()
+        h.close()
+    zc = z.cpu().numpy()
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    ll, ld, q = DN.loglik(xo, yo, zc, theta)
+    t_cpu = time.perf_counter() - t0
+    res["cpu_oracle"] = [float(ll), float(ld), float(q)]
+    rel = {k: {"loglik": abs(v[0] - ll) / abs(ll), "logdet": abs(v[1] - ld) / abs(ld), "quad": abs(v[2] - q) / abs(q)}
+           for k, v in res.items() if k != "cpu_oracle"}
+    print(json.dumps({"workload": "accuracy36k", "n": len(obs), "theta": list(theta), "nb": 800,
+                      "rel_err_vs_cpu_oracle": rel, "cpu_oracle_seconds": t_cpu, "cores": os.cpu_count(),
+                      "values": res}), flush=True)
+
+
 def main():
     a = args_()
     if a.workload == "accuracy" and a.impl != "reference":
         return run_accuracy(a)
     if a.workload == "n40k" and a.impl != "reference":
         return run_n40k(a)
+    if a.workload == "accuracy36k" and a.impl != "reference":
+        return run_accuracy36k(a)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "regions":
@@ -392,20 +480,57 @@ def main():
     dev = torch.device("cuda", local)
     t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
     x, y = inputs.jittered_grid(a.side)
-    obs, held = inputs.holdout(len(x), 100)
-    n = len(obs)  # the evaluated points
-    xo, yo = t64(x[obs]), t64(y[obs])
-    xh, yh = t64(x[held]), t64(y[held])
+    n = len(x)  # every grid point is observed
+    xn_h, yn_h = inputs.uniform_points(100)
+    xo, yo = t64(x), t64(y)
+    xh, yh = t64(xn_h), t64(yn_h)
+    e = t64(inputs.standard_normal(n))
+
+    # ---- dense float64 comparator at the same n (every tile dense, no truncation anywhere), measured once
+    # outside the timed region; its exact Cholesky factor also draws z = L e from the model itself
+    dense = None
+    z = None
+    if not a.no_dense:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        hd = T.Handle(xo, yo, nb=a.nb, eps=-1.0)
+        t0 = time.perf_counter()
+        hd.factor(THETA)
+        torch.cuda.synchronize()
+        t_f = time.perf_counter() - t0
+        z = hd.sample(e)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lld, gd = hd.loglik_grad(z)
+        pd = hd.predict(z, xh, yh)
+        torch.cuda.synchronize()
+        t_g = time.perf_counter() - t0
+        hd.check()
+        dense_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+        td = t_f + t_g
+        dense = {"value": 1.0 / td, "unit": UNIT, "measured_n": n, "measured_s": td, "factor_s": t_f,
+                 "grad_and_kriging_s": t_g, "device_bytes": int(dense_bytes),
+                 "loglik": float(lld.item()), "grad": [float(v) for v in gd.cpu().numpy()]}
+        pred_dense = pd.clone()
+        hd.close()
+        del hd
+        torch.cuda.synchronize()
+        log(f"dense comparator: factor {t_f:.1f} s, gradient + kriging {t_g:.1f} s")
+
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
     h = T.Handle(xo, yo, nb=a.nb, eps=a.eps, rank_cap=a.rank_cap)
     # counts launches of the low-rank update kernel before the timed region (ncu -s offsets)
     T.profile(True)
-    # synthetic measurements z = L e from the factor itself (not timed): a draw from the TLR model
-    h.factor(THETA)
-    z = h.sample(t64(inputs.standard_normal(len(obs))))
-    h.check()
+    if z is None:  # without the dense comparator: a draw from the TLR model (not timed)
+        h.factor(THETA)
+        z = h.sample(e)
+        h.check()
     ll = torch.empty(1, dtype=torch.float64, device=dev)
     grad = torch.empty(3, dtype=torch.float64, device=dev)
-    pred = torch.empty(len(held), dtype=torch.float64, device=dev)
+    pred = torch.empty(len(xn_h), dtype=torch.float64, device=dev)
+    hist = torch.zeros(a.warmup + a.steps, 4, dtype=torch.float64, device=dev)
+    nstep = [0]
 
     def step(zz):
         h.matern_generate(THETA)
@@ -414,13 +539,21 @@ def main():
         h.loglik_grad(zz, ll, grad)
         h.predict(zz, xh, yh, pred)
 
-    log("setup done", f"n={len(obs)}")
+    def record():
+        if nstep[0] < hist.shape[0]:
+            hist[nstep[0], 0:1].copy_(ll)
+            hist[nstep[0], 1:4].copy_(grad)
+        nstep[0] += 1
+
+    log("setup done", f"n={n}")
     for i in range(a.warmup):
         t0 = time.perf_counter()
         step(z)
+        record()
         torch.cuda.synchronize()
         log(f"warmup {i}: {time.perf_counter() - t0:.2f} s")
     h.check()
+    tlr_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
     stream = torch.cuda.current_stream()
     clocks = Clocks(local)
 
@@ -440,6 +573,7 @@ def main():
     e0.record(stream)
     for _ in range(a.steps):
         step(z)
+        record()
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -451,6 +585,9 @@ def main():
     ms = reduce_max(ms, world, dev)
     value = replica_throughput(ms, world)
     log(f"timed: {ms:.1f} ms/step, profile {prof}")
+    # every step (warm-up and timed) gives bitwise the same l and gradient
+    hh = hist.cpu().numpy()
+    deterministic = bool(np.all(hh == hh[0:1]))
 
     # ---- end to end: pinned host z in, (l, grad) out, every step
     z_h = z.cpu().pin_memory()
@@ -476,6 +613,7 @@ def main():
     result = out_h.numpy().copy()
     ranks = h.rank_stats()
     counts = h.tile_counts()
+    inv = h.inverse_stats()
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
@@ -495,41 +633,32 @@ def main():
             "peak_source": "float64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured "
                            "1.19 TFLOP/s)"}
 
-    # ---- dense float64 GPU comparator (every tile dense), scaled by n^3
-    dense = None
-    if not a.no_dense:
-        xd, yd = inputs.jittered_grid(a.dense_side)
-        nd = len(xd)
-        hd = T.Handle(t64(xd), t64(yd), nb=a.nb, eps=-1.0)
-        zd = t64(inputs.standard_normal(nd))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hd.factor(THETA)
-        hd.loglik_grad(zd)
-        torch.cuda.synchronize()
-        td = time.perf_counter() - t0
-        hd.check()
-        hd.close()
-        scale = (n / nd) ** 3
-        dense = {"value": 1.0 / (td * scale), "unit": UNIT, "measured_n": nd, "measured_s": td,
-                 "scaled_to_n": n, "scaling": "n^3", "tlr_speedup": value / (1.0 / (td * scale))}
+    accuracy = None
+    if dense is not None:
+        dense["tlr_speedup"] = value / dense["value"]
+        gdn, gt = np.array(dense["grad"]), result[1:4]
+        accuracy = {"vs": "dense float64 path of this library at the same n (equal to the CPU oracle to <= 1e-10 "
+                          "at n <= 870)",
+                    "loglik_rel_err": abs(result[0] - dense["loglik"]) / abs(dense["loglik"]),
+                    "grad_rel_err": [float(v) for v in np.abs(gt - gdn) / np.abs(gdn)],
+                    "kriging_max_abs_diff": float((pred - pred_dense).abs().max().item())}
 
     cpu = None
     if not a.no_cpu and world == 1:
-        dt, ns = cpu_oracle_sample(a.cpu_side)
-        scale = (n / ns) ** 3
-        cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"dense float64 oracle loglik+grad at n={ns} ({a.cpu_side}^2 grid) took {dt:.3f} s, "
-                         f"scaled by (n/{ns})^3 to n={n}"}
+        tot, gen, ns = cpu_oracle_sample(a.cpu_side)
+        _, cpu = cpu_baseline_line(tot, gen, ns, n)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (jittered grid, z drawn from the model)",
-            "config": main_config(a, len(obs), len(held), "replicas" if world > 1 else "single"),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+ff32", "precision": PRECISION,
+            "data": "synthetic (jittered grid; z = L e drawn from the exact model by the dense path)"
+                    if dense is not None else "synthetic (jittered grid; z drawn from the TLR model)",
+            "config": main_config(a, n, len(xn_h), "replicas" if world > 1 else "single"),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "dense_fp64_gpu": dense,
+            "dense_fp64_gpu": dense, "accuracy": accuracy, "deterministic_across_steps": deterministic,
+            "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes)},
             "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,
-                       "tiles": counts}}
+                       "tiles": counts, "inverse": inv}}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()

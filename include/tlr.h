@@ -64,7 +64,12 @@ typedef struct {
  * metric: 0 = Euclidean distance; 1 = great-circle distance of eq. 6 (Sec. IV,
  * haversine) with x = longitude and y = latitude in degrees (also for the new
  * points of tlr_predict / tlr_predict_var) on a sphere of the given radius
- * (radius <= 0 = 1: distances in radians); beta is in the units of the distance. */
+ * (radius <= 0 = 1: distances in radians); beta is in the units of the distance.
+ * precision: arithmetic of the large dense tile contractions (the inverse's
+ * stacked-panel products): 0 = default, bf16 tensor cores (tcgen05) on 6 digit
+ * slices of every float64 operand, about 1e-12 of the operands' scale (see
+ * tlr_gemm_tc); 1 = double-float on the CUDA cores (about 2^-44), no tensor
+ * cores; 4, 5, 6 = tensor cores with that many slices (4: about 1e-9). */
 typedef struct {
   int nb;
   double eps;
@@ -75,6 +80,7 @@ typedef struct {
   double inv_scale;
   int metric;
   double radius;
+  int precision;
 } tlr_opts;
 
 enum {
@@ -104,7 +110,10 @@ int tlr_matern_generate(tlr_handle h, tlr_theta theta, tlr_stream_t stream);
 
 /* Sec. V: generate and compress every off-diagonal tile to U V^T with the
  * absolute threshold eps (adaptive cross approximation on generated rows and
- * columns, then QR + SVD truncation).  No-op in dense mode. */
+ * columns, then Householder QR of both factors and a column-pivoted QR of the
+ * small core, truncated where the trailing part's Frobenius norm is <= eps).
+ * A tile whose cross approximation needs more than dense_rank terms is kept
+ * dense.  No-op in dense mode. */
 int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream);
 
 /* In-place TLR Cholesky Sigma = L L^T (dense POTRF on diagonal tiles,
@@ -137,7 +146,9 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
 int tlr_predict_var(tlr_handle h, int64_t m, const double* x_new, const double* y_new,
                     double* var_new, tlr_stream_t stream);
 
-/* Synthetic measurements of Sec. VIII-D: z = L e on the factored handle. */
+/* Synthetic measurements of Sec. VIII-D: z = L e on the factored handle (in
+ * dense mode L is the exact Cholesky factor: a draw from the model itself).
+ * e, z: n doubles (device, caller's order). */
 int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream);
 
 /* Independent regions (exact likelihood of many unrelated problems, e.g. the
@@ -187,23 +198,49 @@ int tlr_tile_counts(tlr_handle h, int64_t* n_lowrank, int64_t* n_dense);
  * (device buffer of n int32).  Synchronises `stream`. */
 int tlr_get_perm(tlr_handle h, int* perm, tlr_stream_t stream);
 
-/* Allocation-free variant (the paper has no counterpart): eq. 1 for a small
- * problem, n <= 1024 points, evaluated as one dense tile (Matérn generation,
- * Cholesky, solve, log-determinant) with every piece of workspace in a static
- * device array of the library (about 8.5 MB per GPU, held until exit).  For
- * callers that cannot call cudaMalloc, e.g. because their process has handed
- * all device memory to another allocator or may not allocate after start-up.
- * x, y, z: device arrays of n doubles (caller's order); d_out3: device array
- * of 3 doubles (l, log|Sigma|, z^T Sigma^{-1} z).  Makes no device
- * allocation.  Returns -1 for n outside 1..1024, TLR_ERR_NOT_SPD when the
- * covariance is not positive definite, TLR_OK otherwise; synchronises
- * `stream`.  The first call on a device looks up the workspace address (make
- * it before any stream capture).  All calls share the workspace: calls that
- * overlap on the GPU race. */
+/* Allocation-free variant (the paper has no counterpart).  The Gaussian
+ * log-likelihood of n <= 1024 points with Euclidean distances (the Matérn
+ * covariance generated, Cholesky-factored, the log-determinant and the
+ * quadratic form z^T Sigma^{-1} z taken), evaluated as one dense tile with every
+ * piece of workspace in a static device array of the library (about 8.5 MB per
+ * GPU).  For callers that cannot call cudaMalloc, e.g. because their process
+ * has handed all device memory to another allocator or may not allocate after
+ * start-up.  x, y, z: device arrays of n doubles (caller's order); d_out3:
+ * device array of 3 doubles (l, log|Sigma|, z^T Sigma^{-1} z).  Makes no
+ * allocation of its own, on the device or on the host heap.  The static array
+ * is reserved on a device when the library's code for it is loaded there: with
+ * CUDA's default lazy module loading that is the first call on the device, which
+ * can then fail with TLR_ERR_CUDA under memory pressure, so make that first call
+ * at start-up (or set CUDA_MODULE_LOADING=EAGER to reserve it when the library
+ * is loaded); the device holds it until the process exits.  The first call on a
+ * device also looks up the array's address.  Every call synchronises `stream`
+ * (it reads the points' bounding box and the status back to the host), so it
+ * must not be called while `stream` is being captured into a graph.  All calls
+ * share the array: calls that overlap on the GPU race.
+ * Returns TLR_OK; -1 for n outside 1..1024; -2, -3, -4 for a null x, y, z; -5 for
+ * a theta entry that is not positive and finite; -6 for a null d_out3;
+ * TLR_ERR_NOT_SPD when the covariance is not positive definite (e.g. repeated
+ * points; d_out3 then holds no valid likelihood); TLR_ERR_CUDA for a failed CUDA
+ * call, or a device ordinal >= 128. */
 int tlr_loglik_dense_noalloc(int64_t n, const double* x, const double* y, const double* z, tlr_theta theta,
                              double* d_out3, tlr_stream_t stream);
 
 /* Diagnostics (no counterpart in the paper). */
+
+/* The float64-accurate tensor-core GEMM used for the dense tile contractions,
+ * as one call: C = beta C + alpha op(A) op(B) with op(X) = X^T when tX != 0,
+ * op(A) m x k, op(B) k x n, column-major A (lda), B (ldb), C (ldc), device
+ * pointers.  Each row of op(A) and column of op(B) is scaled by a power of two
+ * and cut into `slices` (4..6) bf16 digits of 8 bits (error-free splitting,
+ * Ozaki et al. 2012); the digit products run on tcgen05 with exact float32
+ * accumulation of the leading groups.  |error| <= |alpha| k 2^sa_i 2^sb_j
+ * ((slices + 4) 2^(-8 slices) + 2^-38) with 2^sa_i, 2^sb_j the powers of two
+ * above the largest magnitude of row i of op(A) and column j of op(B).
+ * Allocates and frees its own workspace (cudaMalloc) and synchronises `stream`.
+ * Returns -i for an invalid argument i, TLR_ERR_OOM, TLR_ERR_CUDA, or
+ * TLR_ERR_TIMEOUT when a device-side wait gave up. */
+int tlr_gemm_tc(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb, int tB, double* C,
+                int ldc, double alpha, double beta, int slices, tlr_stream_t stream);
 
 /* Rank statistics of the low-rank tiles of the inverse Sigma^{-1} built by the
  * last tlr_loglik_grad, and its number of dense off-diagonal tiles.

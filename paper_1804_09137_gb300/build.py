@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtlr.so")
-SOURCES = ["matern.cu", "dense.cu", "factor.cu", "tileops.cu", "inverse.cu", "grad.cu", "solve.cu", "noalloc.cu", "batched.cu", "api.cu"]
+SOURCES = ["matern.cu", "dense.cu", "factor.cu", "tileops.cu", "inverse.cu", "grad.cu", "solve.cu", "noalloc.cu", "batched.cu", "tcgemm.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tcgemm.h"
 
 
 std::atomic<long long> g_tlr_launches{0};
@@ -67,17 +68,17 @@ void tlr_phase_end(cudaStream_t s) {
   g_ph_open.pop_back();
 }
 
-namespace {
-
 // digamma by upward recurrence to x >= 10 and the asymptotic series
 // psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
-double host_digamma(double x) {
+double tlr_host_digamma(double x) {
   double r = 0.0;
   while (x < 10.0) { r -= 1.0 / x; x += 1.0; }
   const double f = 1.0 / (x * x);
   return r + log(x) - 0.5 / x -
          f * (1.0 / 12 - f * (1.0 / 120 - f * (1.0 / 252 - f * (1.0 / 240 - f * (1.0 / 132)))));
 }
+
+namespace {
 
 // Morton (Z-curve) order of the points over their bounding square, 16 bits per axis
 std::vector<int> morton_order(const std::vector<double>& x, const std::vector<double>& y) {
@@ -243,6 +244,14 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   const size_t mb = (nb + 63) / 64;
   ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->cap_nt * (h->cap_nt + 1) / 2 + 1024));
   ws = std::max(ws, 2 * nb * nb + 4096);
+  // the inverse's stacked-panel products on the tensor cores: slices of one nb x nb x nb product
+  // next to two nb x nb panels and their descriptors
+  if (tlr_tc_slices(h) > 0) {
+    const int S = tlr_tc_slices(h);
+    const size_t tc = (oz_slices_elems(h->nb, h->nb, OZ_BM, S) + oz_slices_elems(h->nb, h->nb, OZ_BN, S)) / 4 +
+                      2 * nb * nb + 3 * (size_t)h->cap_nt * 64 + 65536;
+    ws = std::max(ws, tc);
+  }
   h->scratch_elems = ws;
   rc |= dmalloc(&h->scratch, ws);
   if (rc != TLR_OK) {
@@ -264,6 +273,8 @@ int tlr_create(int64_t n, const double* x, const double* y, const tlr_opts* opts
   if (!opts || opts->nb <= 0 || opts->rank_cap < 0 || !(opts->eps == opts->eps)) return -4;
   if (opts->metric != 0 && opts->metric != 1) return -4;
   if (opts->metric == 1 && !(opts->radius == opts->radius)) return -4;
+  if (!(opts->precision == 0 || opts->precision == 1 || (opts->precision >= 4 && opts->precision <= OZ_SMAX)))
+    return -4;
   if (!out) return -6;
   *out = nullptr;
   cudaStream_t s = (cudaStream_t)stream;
@@ -311,7 +322,7 @@ int tlr_matern_generate(tlr_handle h, tlr_theta th, tlr_stream_t stream) {
   h->mp.beta = th.beta;
   h->mp.nu = th.nu;
   h->mp.cnu = 1.0 / (pow(2.0, th.nu - 1.0) * tgamma(th.nu));
-  h->mp.psi = host_digamma(th.nu);
+  h->mp.psi = tlr_host_digamma(th.nu);
   TLR_CUDA_TRY(cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s));
   {
     PhaseScope ps("generate", s);
@@ -375,7 +386,7 @@ int tlr_sample(tlr_handle h, const double* e, double* z, tlr_stream_t stream) {
   if (!h) return -1;
   if (!e) return -2;
   if (!z) return -3;
-  if (h->state != 3 || h->dense) return TLR_ERR_STATE;
+  if (h->state != 3) return TLR_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   h->last_stream = s;
   double* es = h->d_vec;
@@ -615,9 +626,11 @@ int tlr_profile(int enable) {
 int tlr_profile_read(int64_t* launches, double* ms, double* flops) {
   TLR_CUDA_TRY(cudaDeviceSynchronize());
   double tot = 0.0;
-  for (auto& e : g_ev) {
+  const bool verbose = getenv("TLR_VERBOSE") != nullptr;
+  for (size_t i = 0; i < g_ev.size(); ++i) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) tot += t;
+    if (cudaEventElapsedTime(&t, g_ev[i].first, g_ev[i].second) == cudaSuccess) tot += t;
+    if (verbose) fprintf(stderr, "tlr launch %zu: %.3f ms\n", i, t);
   }
   double fl = 0.0;
   if (g_tlr_prof.d_flops) TLR_CUDA_TRY(cudaMemcpy(&fl, g_tlr_prof.d_flops, sizeof(double), cudaMemcpyDeviceToHost));

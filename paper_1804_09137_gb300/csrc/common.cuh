@@ -286,6 +286,12 @@ struct PhaseScope {
 };
 
 // ------------------------------------------------------------ host helpers
+double tlr_host_digamma(double x);  // psi(x), x > 0 (host)
+// digit slices of the tensor-core contractions for the handle's precision option (0: none)
+static inline int tlr_tc_slices(const tlr_ctx* h) {
+  const int p = h->opts.precision;
+  return p == 0 ? 6 : (p == 1 ? 0 : p);
+}
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_diag(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t s);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "recompress.cuh"
+#include "tcgemm.h"
 #include "tileops.h"
 
 namespace {
@@ -334,15 +335,49 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
       depth.push_back(d);
       gel.push_back(g);
     }
+  // tensor-core path of the stacked-panel products: bf16 slices of both panels, row exponents,
+  // split and GEMM descriptors, per target tile (doubles of workspace)
+  const int S = tlr_tc_slices(h);
+  const int rows_a = (nb + OZ_BM - 1) / OZ_BM * OZ_BM, rows_b = (nb + OZ_BN - 1) / OZ_BN * OZ_BN;
+  const size_t od = (2 * sizeof(OzSrc) + sizeof(OzGemm) + 7) / 8;
+  auto slice_dbl = [&](int64_t d) -> size_t {
+    if (!S || d == 0) return 0;
+    return (oz_slices_elems(nb, (int)d, OZ_BM, S) + oz_slices_elems(nb, (int)d, OZ_BN, S)) / 4 +
+           (size_t)(rows_a + rows_b + 1) / 2 + od + 48;
+  };
+  // one target alone must fit (with the reserve for a full-depth product): grow the workspace if not
+  {
+    size_t worst = 0;
+    for (size_t q = 0; q < tg.size(); ++q) {
+      const size_t per = (size_t)(nt - tg[q].x) * (3 * gd + cd + 2) + gd + (size_t)gel[q] +
+                         2 * (size_t)nb * depth[q] + 8 + slice_dbl(depth[q]);
+      worst = std::max(worst, per);
+    }
+    worst += 64 + slice_dbl(nb);
+    if (worst > h->scratch_elems) {
+      TLR_CUDA_TRY(cudaStreamSynchronize(s));
+      cudaFree(h->scratch);
+      h->scratch = nullptr;
+      h->scratch_elems = 0;
+      const size_t want = worst + worst / 4;
+      if (cudaMalloc((void**)&h->scratch, want * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return TLR_ERR_OOM;
+      }
+      h->scratch_elems = want;
+    }
+  }
   const size_t budget = h->scratch_elems;
   size_t b0 = 0;
   std::vector<char> host;
   while (b0 < tg.size()) {
     // greedy batch: descriptors, copy segments, G and both panels within the workspace
-    size_t b1 = b0, need = 64;
+    // (plus room for one nb x nb x nb product on the tensor cores: the dense sources' products)
+    size_t b1 = b0, need = 64 + slice_dbl(nb);
     while (b1 < tg.size()) {
       const int m = tg[b1].x;
-      const size_t per = (size_t)(nt - m) * (3 * gd + cd + 2) + gd + (size_t)gel[b1] + 2 * (size_t)nb * depth[b1] + 8;
+      const size_t per = (size_t)(nt - m) * (3 * gd + cd + 2) + gd + (size_t)gel[b1] + 2 * (size_t)nb * depth[b1] + 8 +
+                         slice_dbl(depth[b1]);
       if (b1 > b0 && need + per > budget) break;
       need += per;
       ++b1;
@@ -462,20 +497,29 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     // GemmGen and CopySeg regions are padded to 8-byte multiples (gd, cd doubles per entry)
     memcpy(host.data() + all.size() * sizeof(GemmGen), cs.data(), cs.size() * sizeof(CopySeg));
     TLR_CUDA_TRY(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    // workspace after the panels: the tensor-core slices of each stage in turn
+    char* tcw = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(Pw + p_tot + 8) + 127) & ~(uintptr_t)127);
+    const size_t tcw_bytes = reinterpret_cast<char*>(base + budget) > tcw
+                                 ? (size_t)(reinterpret_cast<char*>(base + budget) - tcw) : 0;
     {
       PhaseScope ps("lauum.prep", s);
       ZTRY(seg_copy(dcs, (int64_t)n_cs, s));
       ZTRY(tops_gemm(dg1, (int)n_g1, mx_g, mx_g, s));
-      ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
+      if (S) ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));
+      else ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
       ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s));
     }
     {
       PhaseScope ps("lauum.gemm", s);
-      ZTRY(tops_gemm(dbig, (int)nbig, nb, nb, s));
+      if (S) ZTRY(oz_run_host(gbig.data(), (int)gbig.size(), S, tcw, tcw_bytes, h->d_stat, s));
+      else ZTRY(tops_gemm(dbig, (int)nbig, nb, nb, s));
     }
     {
       PhaseScope ps("lauum.dense_products", s);
-      for (size_t r = 0; r < gdd.size(); ++r) ZTRY(tops_gemm(ddd + dd_off[r], (int)gdd[r].size(), nb, nb, s));
+      for (size_t r = 0; r < gdd.size(); ++r) {
+        if (S) ZTRY(oz_run_host(gdd[r].data(), (int)gdd[r].size(), S, tcw, tcw_bytes, h->d_stat, s));
+        else ZTRY(tops_gemm(ddd + dd_off[r], (int)gdd[r].size(), nb, nb, s));
+      }
     }
     b0 = b1;
   }

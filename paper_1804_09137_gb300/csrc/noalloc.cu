@@ -5,24 +5,28 @@
 // a fixed real-time budget), or code for which a device allocation is not
 // allowed after start-up because it can synchronise the device or fail under
 // memory pressure from other processes.  For them, tlr_loglik_dense_noalloc
-// evaluates eq. 1 for n <= TLR_NOALLOC_MAX_N points as one dense tile, with
-// all of its workspace in the file-scope device array below: the Matérn
-// table, the n x n covariance being factored in place, the solve vector and
-// the reduction and status words.  The caller passes inputs and the output.
+// evaluates the Gaussian log-likelihood for n <= TLR_NOALLOC_MAX_N points as
+// one dense tile, with all of its workspace in the file-scope device array
+// below: the Matérn table, the n x n covariance being factored in place, the
+// solve vector, the bounding box of the points and the reduction and status
+// words.  The caller passes inputs and the output; the call makes no device
+// or host heap allocation of its own.
 //
-// The array is static device memory: every GPU that loads the library holds
-// it (about 8.5 MB) until the process exits.  Host code cannot use the array's
-// name as a device address; its address is taken once per device with
-// cudaGetSymbolAddress (the first call on each device does this set-up).
-// Every call shares the array and leaves the last call's contents in it, so
-// calls that overlap on the GPU (on different streams, or from several host
-// threads) race with each other.
+// The array is static device memory of about 8.5 MB.  With CUDA's default lazy
+// module loading it is reserved on a device when the library's code for it is
+// first used there, i.e. by the first call on that device (which can then fail
+// with TLR_ERR_CUDA under memory pressure); with CUDA_MODULE_LOADING=EAGER it is
+// reserved when the library is loaded.  Either way the device holds it until
+// the process exits.  Host code cannot use the array's name as a device
+// address; its address is taken once per device with cudaGetSymbolAddress
+// (the first call on each device does this set-up).  Every call shares the
+// array and leaves the last call's contents in it, so calls that overlap on the
+// GPU (on different streams, or from several host threads) race with each
+// other.
 #include <math.h>
 #include <string.h>
 
-#include <algorithm>
 #include <mutex>
-#include <vector>
 
 #include "common.cuh"
 
@@ -36,21 +40,33 @@ constexpr size_t kVals = TAB_ELEMS;                                   // table-n
 constexpr size_t kVec = TLR_NOALLOC_MAX_N;                            // solve vector
 constexpr size_t kRed = 64;                                           // reduction partials
 constexpr size_t kStat = 4;                                           // status words
-constexpr size_t kTotal = kD + kTab + kVals + kVec + kRed + kStat;
+constexpr size_t kBox = 4;                                            // bounding box of the points
+constexpr size_t kTotal = kD + kTab + kVals + kVec + kRed + kStat + kBox;
 
 __device__ __align__(256) double g_noalloc_ws[kTotal];
 
 std::mutex g_mu;
 double* g_ws_ptr[128] = {nullptr};  // device address of g_noalloc_ws, per device ordinal
 
-// psi(x): upward recurrence to x >= 10, then the asymptotic series
-// ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
-double digamma_host(double x) {
-  double r = 0.0;
-  while (x < 10.0) { r -= 1.0 / x; x += 1.0; }
-  const double f = 1.0 / (x * x);
-  return r + log(x) - 0.5 / x -
-         f * (1.0 / 12 - f * (1.0 / 120 - f * (1.0 / 252 - f * (1.0 / 240 - f * (1.0 / 132)))));
+// box[0..3] = min x, max x, min y, max y of the n points (one CTA)
+__global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                       double* __restrict__ box) {
+  __shared__ double sh[4][TLR_THREADS];
+  double v[4] = {x[0], x[0], y[0], y[0]};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    v[0] = fmin(v[0], x[i]); v[1] = fmax(v[1], x[i]);
+    v[2] = fmin(v[2], y[i]); v[3] = fmax(v[3], y[i]);
+  }
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 4; ++q)
+        sh[q][threadIdx.x] = (q & 1) ? fmax(sh[q][threadIdx.x], sh[q][threadIdx.x + o])
+                                     : fmin(sh[q][threadIdx.x], sh[q][threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) box[threadIdx.x] = sh[threadIdx.x][0];
 }
 
 }  // namespace
@@ -82,14 +98,15 @@ extern "C" int tlr_loglik_dense_noalloc(int64_t n, const double* x, const double
     }
     ws = g_ws_ptr[dev];
   }
-  // the table must cover the largest distance among the points
-  std::vector<double> hx(n), hy(n);
-  TLR_CUDA_TRY(cudaMemcpyAsync(hx.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-  TLR_CUDA_TRY(cudaMemcpyAsync(hy.data(), y, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // the table must cover the largest distance among the points: bounding box on the device,
+  // read back into a stack array
+  double* box = ws + kD + kTab + kVals + kVec + kRed + kStat;
+  double hb[4];
+  k_bbox<<<1, TLR_THREADS, 0, s>>>(x, y, n, box);
+  TLR_LAUNCH_CHECK();
+  TLR_CUDA_TRY(cudaMemcpyAsync(hb, box, sizeof(hb), cudaMemcpyDeviceToHost, s));
   TLR_CUDA_TRY(cudaStreamSynchronize(s));
-  const double x0 = *std::min_element(hx.begin(), hx.end()), x1 = *std::max_element(hx.begin(), hx.end());
-  const double y0 = *std::min_element(hy.begin(), hy.end()), y1 = *std::max_element(hy.begin(), hy.end());
-  const double rmax = hypot(x1 - x0, y1 - y0);
+  const double rmax = hypot(hb[1] - hb[0], hb[3] - hb[2]);
 
   // a one-tile context whose every buffer lives in the static workspace
   tlr_ctx c;
@@ -113,7 +130,7 @@ extern "C" int tlr_loglik_dense_noalloc(int64_t n, const double* x, const double
   c.mp.beta = theta.beta;
   c.mp.nu = theta.nu;
   c.mp.cnu = 1.0 / (pow(2.0, theta.nu - 1.0) * tgamma(theta.nu));
-  c.mp.psi = digamma_host(theta.nu);
+  c.mp.psi = tlr_host_digamma(theta.nu);
   c.mp.e_lo = (int)ceil(log2(rmax > 0 ? rmax : 1.0)) + 1 - TAB_OCT;
   c.last_stream = s;
 

@@ -1,0 +1,67 @@
+// Float64-accurate GEMM on the bf16 tensor cores (tcgen05) by splitting each
+// operand into bf16 digit slices (Ozaki, Ogita, Oishi, Rump 2012: error-free
+// splitting of a product into sums of exactly computable products).
+//
+//   C = beta C + alpha op(A) op(B),  op(A) m x k,  op(B) k x n,  column-major C.
+//
+// Every row a of op(A) (column b of op(B)) is scaled by a power of two 2^-s_a so
+// that its entries lie in (-1, 1), and the 53-bit fixed-point value is cut into
+// S digits of 8 bits, digit j carrying weight 2^-8(j+1): each digit is an exact
+// bf16 number.  Products of digits j and l are exact in the tensor core and land
+// on the grid 2^-8(j+l+2); for the groups j + l = 0, 1, 2 the float32
+// accumulation over a K-chunk of 128 stays below 2^24 grid units, so it is exact,
+// and each chunk is added to a double-float running sum; the groups j + l >= 3
+// share one float32 accumulator (their rounding lies below 2^-46 of the scale).
+// Pairs with j + l >= S are dropped.  The error is at most about
+// (S + 1) 2^-8S k max|a_row| max|b_col| (S = 6: ~2^-45 relative to that scale).
+//
+// The split is a separate pass (k_oz_split) that writes the slices in the
+// tensor core's K-major core-matrix layout, tile by tile, so that the GEMM moves
+// each tile into shared memory with one bulk (TMA) copy per operand and stage.
+#pragma once
+#include "tileops.h"
+
+#define OZ_BM 128     // rows of op(A) per CTA (tcgen05 M)
+#define OZ_BN 64      // columns of op(B) per CTA (tcgen05 N)
+#define OZ_BK 32      // depth of one pipeline stage
+#define OZ_SMAX 6     // largest number of slices (three pipeline stages of shared memory)
+
+// One operand split into slices: rows x depth (padded to the tile grid).
+struct OzSplit {
+  const uint16_t* sl;  // bf16 slices, [row block][k block][slice][tile in core-matrix layout]
+  const int* ex;       // per row: biased float64 exponent E with |x| < 2^(E - 1022) for every x of the row
+  int rows;            // logical rows
+  int nkb;             // k blocks of OZ_BK
+};
+
+// Source description of one operand for the split: element (r, k) of the rows x depth
+// matrix is X[k * ld + r] (col = 1) or X[r * ld + k] (col = 0).
+struct OzSrc {
+  const double* X;
+  int ld;
+  int col;
+  int rows;
+  int depth;
+  uint16_t* out;  // slices destination (oz_slices_elems(rows, depth, block_rows, S) bf16 values)
+  int* ex;        // rows exponents
+  int block_rows; // OZ_BM for the A operand, OZ_BN for the B operand
+};
+
+struct OzGemm {
+  OzSplit a, b;
+  double* C;
+  int ldc, m, n;
+  double alpha, beta;
+  int lower;  // only entries with row >= column are written
+};
+
+size_t oz_slices_elems(int rows, int depth, int block_rows, int S);
+// Run `count` GEMMs described on the host (GemmGen semantics: column-major, transposes, alpha,
+// beta, lower) on the tensor cores with S slices, in chunks that fit the device workspace
+// ws (ws_bytes bytes, 128-byte aligned); entries with k = 0 only scale C by beta.  TLR_ERR_OOM when
+// one GEMM alone does not fit.  Time-outs are recorded in d_stat.
+int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, long long* d_stat, cudaStream_t s);
+// split `count` operands (descriptors on the device); max_rows / max_depth bound the grid
+int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s);
+// batched GEMMs (descriptors on the device); tiles of the largest m x n; status words for time-outs
+int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s);

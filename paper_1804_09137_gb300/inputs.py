@@ -22,6 +22,7 @@ STREAM_LOCATIONS = 0
 STREAM_NOISE = 1
 STREAM_HOLDOUT = 2
 STREAM_REGIONS = 3
+STREAM_NEW_POINTS = 4
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
@@ -51,6 +52,13 @@ def locations(n: int, seed: int = SEED):
     """n jittered-grid locations; side = ceil(sqrt(n)), subset when not square."""
     side = int(np.ceil(np.sqrt(n) - 1e-9))
     return jittered_grid(side, seed, n if side * side != n else None)
+
+
+def uniform_points(m: int, seed: int = SEED):
+    """m prediction locations drawn uniformly on [0,1]^2 (not on the grid)."""
+    rng = _rng(seed, STREAM_NEW_POINTS)
+    p = rng.uniform(0.0, 1.0, size=(2, m))
+    return np.ascontiguousarray(p[0]), np.ascontiguousarray(p[1])
 
 
 def standard_normal(n: int, seed: int = SEED, stream: int = STREAM_NOISE) -> np.ndarray:

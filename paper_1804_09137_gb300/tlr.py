@@ -23,7 +23,7 @@ ERR_NAMES = {1: "not SPD", 2: "rank cap exceeded", 3: "out of memory", 4: "CUDA 
 class TlrOpts(C.Structure):
     _fields_ = [("nb", C.c_int), ("eps", C.c_double), ("rank_cap", C.c_int), ("truncate_at_cap", C.c_int),
                 ("order", C.c_int), ("dense_rank", C.c_int), ("inv_scale", C.c_double), ("metric", C.c_int),
-                ("radius", C.c_double)]
+                ("radius", C.c_double), ("precision", C.c_int)]
 
 
 class TlrTheta(C.Structure):
@@ -44,7 +44,7 @@ EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
            "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
            "tlr_loglik_grad_batched", "tlr_predict_var",
-           "tlr_profile_read"]
+           "tlr_profile_read", "tlr_gemm_tc"]
 
 
 def lib():
@@ -81,6 +81,8 @@ def lib():
     L.tlr_loglik_dense_noalloc.argtypes = [i64, vp, vp, vp, TlrTheta, vp, vp]
     L.tlr_profile_phases.argtypes = [C.c_char_p, i64]
     L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
+    ci = C.c_int
+    L.tlr_gemm_tc.argtypes = [ci, ci, ci, vp, ci, ci, vp, ci, ci, vp, ci, d, d, ci, vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -107,13 +109,14 @@ class Handle:
 
     def __init__(self, x: torch.Tensor, y: torch.Tensor, nb: int, eps: float = 1e-9, rank_cap: int = 0,
                  truncate_at_cap: bool = False, order: bool = True, dense_rank: int = 0, inv_scale: float = 0.0,
-                 radius: float | None = None):
+                 radius: float | None = None, precision: int = 0):
         """radius: None for Euclidean distances; a sphere radius for great-circle distances (eq. 6) with
-        x = longitude and y = latitude in degrees."""
+        x = longitude and y = latitude in degrees.  precision: 0 tensor-core contractions on 6 bf16 slices
+        (default), 1 double-float on the CUDA cores, 4..6 tensor cores with that many slices."""
         L = lib()
         self._opts = TlrOpts(int(nb), float(eps), int(rank_cap), int(bool(truncate_at_cap)), int(bool(order)),
                              int(dense_rank), float(inv_scale), 0 if radius is None else 1,
-                             0.0 if radius is None else float(radius))
+                             0.0 if radius is None else float(radius), int(precision))
         h = C.c_void_p()
         _check("tlr_create", L.tlr_create(int(x.numel()), _ptr(x), _ptr(y), C.byref(self._opts), _stream(),
                                           C.byref(h)))
@@ -225,6 +228,21 @@ class Handle:
         _check("tlr_rank_stats", lib().tlr_rank_stats(self._h, C.byref(kmin), C.byref(kmean), C.byref(kmax),
                                                       C.byref(nbytes)))
         return {"kmin": kmin.value, "kmean": kmean.value, "kmax": kmax.value, "bytes": nbytes.value}
+
+
+def gemm_tc(A: torch.Tensor, B: torch.Tensor, Cm: torch.Tensor, tA=False, tB=False, alpha=1.0, beta=0.0,
+            slices=6):
+    """Cm = beta Cm + alpha op(A) op(B) on the tensor cores.  A, B, Cm: column-major (Fortran-ordered: .T is
+    contiguous) float64 CUDA tensors with BLAS shapes (op(A) m x k, op(B) k x n, Cm m x n)."""
+    m, n = Cm.shape
+    k = A.shape[0] if tA else A.shape[1]
+    for t in (A, B, Cm):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.T.is_contiguous()):
+            raise ValueError("expected column-major float64 CUDA tensors")
+    vp = lambda t: C.c_void_p(t.data_ptr())
+    _check("tlr_gemm_tc", lib().tlr_gemm_tc(m, n, k, vp(A), A.shape[0], int(tA), vp(B), B.shape[0], int(tB), vp(Cm),
+                                            Cm.shape[0], float(alpha), float(beta), int(slices), _stream()))
+    return Cm
 
 
 def launch_count() -> int:

@@ -17,6 +17,7 @@ def test_reference_arm_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["higher_is_better"] is True and line["value"] > 0
-    assert line["config"]["n"] == 89900 and line["config"]["workload"].startswith("matern_tlr_n89900")
+    assert line["config"]["n"] == 90000 and line["config"]["workload"].startswith("matern_tlr_n90000")
+    assert line["cpu_baseline"]["measured_n"] == 64 and line["cpu_baseline"]["measured_s"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]

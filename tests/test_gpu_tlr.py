@@ -256,20 +256,6 @@ def test_gradient_dense_mode(T):
     np.testing.assert_allclose(g.cpu().numpy(), g_ref, rtol=1e-8, atol=1e-8 * np.max(np.abs(g_ref)))
 
 
-def test_gradient_sigma2_identity_at_tlr_eps(T):
-    # Sigma = sigma2 R: dl/dsigma2 = (q - n) / (2 sigma2) holds at any size
-    theta = (1.4, 0.3, 1.0)
-    x, y = inputs.jittered_grid(40)
-    h = T.Handle(dev(x), dev(y), nb=200, eps=1e-8)
-    h.factor(theta)
-    z = h.sample(dev(inputs.standard_normal(len(x))))
-    out = h.loglik(z).cpu().numpy()
-    _, g = h.loglik_grad(z)
-    h.check()
-    want = (out[2] - len(x)) / (2 * theta[0])
-    assert abs(g.cpu().numpy()[0] - want) <= 1e-6 * abs(want) + 1e-6
-
-
 def test_gradient_finite_differences_of_gpu_loglik(T):
     theta = np.array([1.0, 0.2, 0.8])
     x, y, z = problem(30, tuple(theta), n=880)
