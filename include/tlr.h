@@ -59,17 +59,21 @@ typedef struct {
  * (0 = max(16, nb/9)); tiles are also made dense where a dense x dense
  * product would land on them during the factorization; inv_scale: the
  * gradient's inverse keeps L^{-1} in tile low-rank form truncated at
- * inv_scale * eps * zeta^(1/2), zeta = the largest 1 / L_aa^2 (0 = 0.1);
+ * inv_scale * eps * zeta^(1/2), zeta = the largest 1 / L_aa^2 (0 = 1: the same
+ * truncation relative to the size of L^{-1} as eps is to Sigma);
  * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile.
  * metric: 0 = Euclidean distance; 1 = great-circle distance of eq. 6 (Sec. IV,
  * haversine) with x = longitude and y = latitude in degrees (also for the new
  * points of tlr_predict / tlr_predict_var) on a sphere of the given radius
  * (radius <= 0 = 1: distances in radians); beta is in the units of the distance.
- * precision: arithmetic of the large dense tile contractions (the inverse's
- * stacked-panel products): 0 = default, bf16 tensor cores (tcgen05) on 6 digit
- * slices of every float64 operand, about 1e-12 of the operands' scale (see
- * tlr_gemm_tc); 1 = double-float on the CUDA cores (about 2^-44), no tensor
- * cores; 4, 5, 6 = tensor cores with that many slices (4: about 1e-9). */
+ * precision: arithmetic of the gradient's inverse's batched tile contractions of
+ * depth >= 256 (dense x dense and dense x thin updates, the triangular transforms
+ * with the diagonal inverses, the stacked-panel products of Sigma^{-1}): 0 =
+ * default, bf16 tensor cores (tcgen05) on 6 digit slices of every float64
+ * operand, about 1e-12 of the operands' scale (see tlr_gemm_tc); 1 = double-float
+ * on the CUDA cores (about 2^-44), no tensor cores; 4, 5, 6 = tensor cores with
+ * that many slices (4: about 1e-9).  The Cholesky factorization and dense mode
+ * (eps < 0) always use double-float. */
 typedef struct {
   int nb;
   double eps;

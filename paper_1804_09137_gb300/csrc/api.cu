@@ -146,6 +146,7 @@ void free_ctx(tlr_ctx* h) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->aux) cudaStreamDestroy(h->aux);
+
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   free(h->kind);
@@ -246,8 +247,8 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   ws = std::max(ws, 2 * nb * nb + 4096);
   // the inverse's stacked-panel products on the tensor cores: slices of one nb x nb x nb product
   // next to two nb x nb panels and their descriptors
-  if (tlr_tc_slices(h) > 0) {
-    const int S = tlr_tc_slices(h);
+  if (tlr_tc_slices_opt(h) > 0) {
+    const int S = tlr_tc_slices_opt(h);
     const size_t tc = (oz_slices_elems(h->nb, h->nb, OZ_BM, S) + oz_slices_elems(h->nb, h->nb, OZ_BN, S)) / 4 +
                       2 * nb * nb + 3 * (size_t)h->cap_nt * 64 + 65536;
     ws = std::max(ws, tc);

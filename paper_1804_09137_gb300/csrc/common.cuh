@@ -11,6 +11,7 @@
 #include "../../include/tlr.h"
 
 #define TLR_THREADS 256
+#define TLR_MAX_WARPS 32  // largest block: 1024 threads
 
 // Matérn interpolation table: C(r), dC/dbeta(r), dC/dnu(r) on geometric
 // intervals [2^(e_lo + j/4), 2^(e_lo + (j+1)/4)), j = 0..TAB_NINT-1, each a
@@ -111,6 +112,7 @@ struct tlr_ctx {
   double* d_red;      // reduction partials
   int red_len;
   int state;          // 0 created, 1 generated, 2 compressed, 3 factored
+  int in_inverse;     // 1 while the gradient's inverse is being formed (tensor-core products allowed)
   int tab_valid;
   cudaStream_t last_stream;
   // second stream of the inverse (dense x dense products overlap the other updates of a step)
@@ -156,21 +158,22 @@ __device__ __forceinline__ void set_status(long long* st, long long code, long l
     st[ST_INFO] = info;
 }
 
-// block-wide sum of one double per thread (blockDim.x == TLR_THREADS); all threads get the result
+// block-wide sum of one double per thread (any block size up to 1024 threads, a multiple of 32;
+// sh holds blockDim.x / 32 + 1 doubles); all threads get the result
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x < 32) {
-    t = (l < (TLR_THREADS / 32)) ? sh[l] : 0.0;
+    t = (l < nw) ? sh[l] : 0.0;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (l == 0) sh[TLR_THREADS / 32] = t;
+    if (l == 0) sh[nw] = t;
   }
   __syncthreads();
-  return sh[TLR_THREADS / 32];
+  return sh[nw];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -178,30 +181,31 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block-wide argmax of |v| over threads; returns index (ties: smaller index)
+// block-wide argmax of |v| over threads; returns index (ties: smaller index); shv, shi hold
+// blockDim.x / 32 + 1 entries
 __device__ __forceinline__ int block_argmax(double a, int idx, double* shv, int* shi, double* outv) {
   for (int o = 16; o > 0; o >>= 1) {
     double a2 = __shfl_xor_sync(0xffffffffu, a, o);
     int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
     if (a2 > a || (a2 == a && i2 < idx)) { a = a2; idx = i2; }
   }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) { shv[w] = a; shi[w] = idx; }
   __syncthreads();
   if (threadIdx.x < 32) {
-    a = (l < TLR_THREADS / 32) ? shv[l] : -1.0;
-    idx = (l < TLR_THREADS / 32) ? shi[l] : 0x7fffffff;
+    a = (l < nw) ? shv[l] : -1.0;
+    idx = (l < nw) ? shi[l] : 0x7fffffff;
     for (int o = 16; o > 0; o >>= 1) {
       double a2 = __shfl_xor_sync(0xffffffffu, a, o);
       int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
       if (a2 > a || (a2 == a && i2 < idx)) { a = a2; idx = i2; }
     }
-    if (l == 0) { shv[TLR_THREADS / 32] = a; shi[TLR_THREADS / 32] = idx; }
+    if (l == 0) { shv[nw] = a; shi[nw] = idx; }
   }
   __syncthreads();
-  if (outv) *outv = shv[TLR_THREADS / 32];
-  return shi[TLR_THREADS / 32];
+  if (outv) *outv = shv[nw];
+  return shi[nw];
 }
 
 // ------------------------------------------------------- Matérn evaluation
@@ -287,11 +291,16 @@ struct PhaseScope {
 
 // ------------------------------------------------------------ host helpers
 double tlr_host_digamma(double x);  // psi(x), x > 0 (host)
-// digit slices of the tensor-core contractions for the handle's precision option (0: none)
-static inline int tlr_tc_slices(const tlr_ctx* h) {
+// digit slices of the tensor-core contractions for the handle's precision option (0: none).  Only the
+// gradient's inverse uses them: the Cholesky's products with the explicit diagonal-tile inverses
+// amplify the rounding of their operands' scale (with tensor-core products the l error at eps = 1e-9
+// exceeded 1e-8 relative), and dense mode, the exact full-tile comparator, stays in double-float.
+static inline int tlr_tc_slices_opt(const tlr_ctx* h) {  // the option alone (workspace sizing)
   const int p = h->opts.precision;
+  if (h->dense) return 0;
   return p == 0 ? 6 : (p == 1 ? 0 : p);
 }
+static inline int tlr_tc_slices(const tlr_ctx* h) { return h->in_inverse ? tlr_tc_slices_opt(h) : 0; }
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_diag(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t s);

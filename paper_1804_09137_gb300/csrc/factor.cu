@@ -45,6 +45,7 @@ __global__ void k_aca_compress(const double* __restrict__ tab, const MaternParam
   int ti, tj;
   decode_lower(t, &ti, &tj);
   ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  w.vs = reinterpret_cast<dfloat*>(dsm);  // free after the cross approximation
   const int64_t pi0 = (int64_t)ti * nb, pj0 = (int64_t)tj * nb;
   const int mi = (int)min((int64_t)nb, n - pi0), mj = (int)min((int64_t)nb, n - pj0);
   GenEntry ge{tab, mp, x, y, n, pi0, pj0};
@@ -93,8 +94,13 @@ __global__ void k_syrk_prep(TlrView v, int k, int i0, GemmDesc* __restrict__ des
     double* T = G + (size_t)v.kcap * v.kcap;
     d.P = T;
     if (kr > 0) {
-      cta_gemm_df(kr, kr, nb, 1.0, tileV(v, t), nb, 1, tileV(v, t), nb, 0, 0.0, G, kr);   // G = V^T V
-      cta_gemm_df(nb, kr, kr, 1.0, tileU(v, t), nb, 0, G, kr, 0, 0.0, T, nb);             // T = U G
+      if (kr <= 48) {
+        cta_gemm_tn_thin(kr, kr, nb, 1.0, tileV(v, t), tileV(v, t), G, kr);  // G = V^T V
+        cta_gemm_nn_thin(nb, kr, kr, 1.0, tileU(v, t), G, kr, 0, T);         // T = U G
+      } else {
+        cta_gemm_df(kr, kr, nb, 1.0, tileV(v, t), nb, 1, tileV(v, t), nb, 0, 0.0, G, kr);
+        cta_gemm_df(nb, kr, kr, 1.0, tileU(v, t), nb, 0, G, kr, 0, 0.0, T, nb);
+      }
     }
   }
   if (threadIdx.x == 0) desc[blockIdx.x] = d;

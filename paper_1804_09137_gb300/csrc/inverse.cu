@@ -554,7 +554,16 @@ static int ensure_aux(tlr_ctx* h, int items) {
 }
 
 
+namespace {
+struct InverseScope {  // marks the handle as forming the inverse for the scope's lifetime
+  tlr_ctx* h;
+  explicit InverseScope(tlr_ctx* hh) : h(hh) { h->in_inverse = 1; }
+  ~InverseScope() { h->in_inverse = 0; }
+};
+}  // namespace
+
 int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
+  InverseScope scope(h);
   ZTRY(ensure_z(h));
   if (!h->zplan_valid) ZTRY(zplan(h, s));
   const int nt = h->nt, nb = h->nb;
@@ -581,7 +590,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
       TLR_LAUNCH_CHECK();
     }
   }
-  const double eps = (h->opts.eps > 0 ? h->opts.eps : 0.0) * (h->opts.inv_scale > 0 ? h->opts.inv_scale : 0.1);
+  const double eps = (h->opts.eps > 0 ? h->opts.eps : 0.0) * (h->opts.inv_scale > 0 ? h->opts.inv_scale : 1.0);
   // dense x dense products run on a second stream next to the other updates of their step
   int max_dd = 0;
   for (int k = 0; k < nt; ++k) {

@@ -25,6 +25,7 @@ struct ItemWs {  // per-item workspace layout (doubles)
   double* s;     // Kmax
   int* eu;       // Kmax column scale exponents of Up
   int* ev;       // Kmax column scale exponents of Vp
+  dfloat* vs;    // shared memory: two staged reflectors, 2 nb (the kernel's dynamic shared memory)
 };
 
 __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int slot, int nb, int Kmax, int kcap) {
@@ -42,6 +43,7 @@ __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int s
   w.s = p; p += Kmax;
   w.eu = (int*)p;
   w.ev = w.eu + Kmax;
+  w.vs = nullptr;
   return w;
 }
 
@@ -177,23 +179,102 @@ __device__ void cta_geqr2_df(dfloat* __restrict__ A, int lda, int m, int K, doub
   }
 }
 
-// B <- Q B (double-float), Q = H_0 ... H_{K-1} from cta_geqr2_df; warp per column
-__device__ void cta_apply_q_df(const dfloat* __restrict__ A, int lda, int m, int K, const double* __restrict__ tau,
-                               dfloat* __restrict__ B, int ldb, int ncol) {
+// Householder QR of two m x K double-float matrices in lockstep (A1 -> tau1, A2 -> tau2), same
+// arithmetic per column as cta_geqr2_df: the squared norms are reduced in double-float, the two
+// reflectors' scalars are formed by two threads at once, and the scaled reflectors are staged in
+// shared memory (vs: 2 m double-floats) for the trailing columns of both matrices, which all warps share.
+__device__ void cta_geqr2_pair_df(dfloat* __restrict__ A1, double* __restrict__ tau1, dfloat* __restrict__ A2,
+                                  double* __restrict__ tau2, int lda, int m, int K, dfloat* __restrict__ vs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = warp; j < ncol; j += nw) {
-    dfloat* b = B + (size_t)j * ldb;
-    for (int c = K - 1; c >= 0; --c) {
-      const double tc = tau[c];
-      if (tc == 0.0) continue;
-      const dfloat tcd = df_from_scaled(tc, 0);
-      const dfloat* v = A + (size_t)c * lda;
+  const int nref = K < m ? K : m;
+  __shared__ dfloat sc_tau[2], sc_scal[2], red[2][TLR_MAX_WARPS];
+  __shared__ int sc_on[2];
+  for (int c = 0; c < nref; ++c) {
+    dfloat* a1 = A1 + (size_t)c * lda;
+    dfloat* a2 = A2 + (size_t)c * lda;
+    float ps1 = 0.f, pc1 = 0.f, ps2 = 0.f, pc2 = 0.f;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      df_dot_add(ps1, pc1, a1[r], a1[r]);
+      df_dot_add(ps2, pc2, a2[r], a2[r]);
+    }
+    const dfloat s1 = df_warp_sum(df_norm(ps1, pc1)), s2 = df_warp_sum(df_norm(ps2, pc2));
+    if (lane == 0) { red[0][warp] = s1; red[1][warp] = s2; }
+    __syncthreads();
+    if (threadIdx.x == 0 || threadIdx.x == 32) {  // the reflectors' scalars, in float64
+      const int side = threadIdx.x == 0 ? 0 : 1;
+      dfloat t = red[side][0];
+      for (int q = 1; q < nw; ++q) t = df_add(t, red[side][q]);
+      const double sig = df_to(t);
+      dfloat* a = side ? a2 : a1;
+      const double alpha = df_to(a[c]);
+      double beta = alpha, tc = 0.0, scal = 1.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tc = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      sc_on[side] = sig > 0.0;
+      sc_tau[side] = df_from(tc);
+      sc_scal[side] = df_from(scal);
+      (side ? tau2 : tau1)[c] = tc;
+      a[c] = df_from(beta);
+    }
+    __syncthreads();
+    const int on1 = sc_on[0], on2 = sc_on[1];
+    const dfloat sc1 = sc_scal[0], sc2 = sc_scal[1];
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      const dfloat v1 = on1 ? df_mul(a1[r], sc1) : a1[r];
+      const dfloat v2 = on2 ? df_mul(a2[r], sc2) : a2[r];
+      a1[r] = v1;
+      a2[r] = v2;
+      vs[r] = v1;
+      vs[m + r] = v2;
+    }
+    __syncthreads();
+    const int n1 = on1 ? K - c - 1 : 0, n2 = on2 ? K - c - 1 : 0;
+    for (int jj = warp; jj < n1 + n2; jj += nw) {
+      const int side = jj < n1 ? 0 : 1;
+      const int j = c + 1 + (side ? jj - n1 : jj);
+      dfloat* b = (side ? A2 : A1) + (size_t)j * lda;
+      const dfloat* v = vs + (size_t)side * m;
       const dfloat bc = b[c];
-      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(v, b, c + 1, m, lane)), bc), tcd);
+      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(v, b, c + 1, m, lane)), bc), sc_tau[side]);
+      if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
+      df_col_axpy(b, d, v, c + 1, m, lane);
+    }
+    __syncthreads();
+  }
+}
+
+// B1 <- Q1 B1 and B2 <- Q2 B2 (double-float), Qi = H_0 ... H_{K-1} from cta_geqr2_df (reflectors Ai,
+// taus ti), ncol columns each: reflector by reflector (staged in shared memory, vs: 2 m double-floats),
+// every warp taking columns of either side, so both sides share the warps
+__device__ void cta_apply_q2_df(const dfloat* __restrict__ A1, const double* __restrict__ t1, dfloat* __restrict__ B1,
+                                const dfloat* __restrict__ A2, const double* __restrict__ t2, dfloat* __restrict__ B2,
+                                int lda, int m, int K, int ldb, int ncol, dfloat* __restrict__ vs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = K - 1; c >= 0; --c) {
+    const double tc1 = t1[c], tc2 = t2[c];
+    if (tc1 == 0.0 && tc2 == 0.0) continue;
+    __syncthreads();  // the previous reflectors' readers are done
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      vs[r] = A1[(size_t)c * lda + r];
+      vs[m + r] = A2[(size_t)c * lda + r];
+    }
+    __syncthreads();
+    const dfloat td1 = df_from_scaled(tc1, 0), td2 = df_from_scaled(tc2, 0);
+    for (int jj = warp; jj < 2 * ncol; jj += nw) {
+      const bool first = jj < ncol;
+      if ((first ? tc1 : tc2) == 0.0) continue;
+      dfloat* b = (first ? B1 : B2) + (size_t)(first ? jj : jj - ncol) * ldb;
+      const dfloat* v = vs + (first ? 0 : m);
+      const dfloat bc = b[c];
+      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(v, b, c + 1, m, lane)), bc), first ? td1 : td2);
       if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
       df_col_axpy(b, d, v, c + 1, m, lane);
     }
   }
+  __syncthreads();
 }
 
 // C[0:m, 0:n] = beta C + alpha op(A) op(B) (op(X) = X^T when tX), column-major, in 64 x 64
@@ -206,7 +287,9 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
                                                    int nblk_step, int lower_only) {
   __shared__ dfloat As[16][64 + 1];
   __shared__ dfloat Bs[16][64 + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // 256 threads (16 x 16) compute; in larger blocks the other threads only take part in the barriers
+  const bool act = threadIdx.x < 256;
+  const int tx = threadIdx.x & 15, ty = (threadIdx.x >> 4) & 15;
   const int mb = (m + 63) / 64, nbk = (n + 63) / 64;
   for (int blk = blk0; blk < mb * nbk; blk += nblk_step) {
     const int bi = blk % mb, bj = blk / mb;
@@ -219,7 +302,7 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
       for (int j = 0; j < 4; ++j) { as[i][j] = 0.f; ae[i][j] = 0.f; }
     for (int k0 = 0; k0 < k; k0 += 16) {
       __syncthreads();
-      for (int id = threadIdx.x; id < 64 * 16; id += 256) {
+      for (int id = threadIdx.x; act && id < 64 * 16; id += 256) {
         int a, kk;
         if (!tA) { a = id & 63; kk = id >> 6; } else { kk = id & 15; a = id >> 4; }
         const int ra = r0 + a, kc = k0 + kk;
@@ -234,7 +317,7 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
       }
       __syncthreads();
 #pragma unroll 4
-      for (int kk = 0; kk < 16; ++kk) {
+      for (int kk = 0; kk < 16 && act; ++kk) {
         dfloat av[4], bv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
@@ -251,7 +334,7 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
-        if (r < m && c < n && (!lower_only || r >= c)) {
+        if (act && r < m && c < n && (!lower_only || r >= c)) {
           double* cp = C + (size_t)c * ldc + r;
           const double v = df_to_scaled(df_norm(as[i][j], ae[i][j]), 0);
           *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * v;
@@ -264,6 +347,92 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
 __device__ __forceinline__ void cta_gemm_df(int m, int n, int k, double alpha, const double* A, int lda, int tA,
                                             const double* B, int ldb, int tB, double beta, double* C, int ldc) {
   cta_gemm_df_blocks(m, n, k, alpha, A, lda, tA, B, ldb, tB, beta, C, ldc, 0, 1, 0);
+}
+
+// Thin products of the low-rank updates (ranks k << nb), double-float accumulation.
+//
+// W[a + b ldw] = alpha sum_r P[r + a nb] Q[r + b nb] for a < ka, b < kb: every warp takes
+// 4 x 4 blocks of W with its lanes striding the nb rows (coalesced column reads), then a
+// warp reduction per entry; no CTA barrier inside.
+__device__ void cta_gemm_tn_thin(int ka, int kb, int nb, double alpha, const double* __restrict__ P,
+                                 const double* __restrict__ Q, double* __restrict__ W, int ldw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ba = (ka + 3) >> 2, bb = (kb + 3) >> 2;
+  for (int blk = warp; blk < ba * bb; blk += nw) {
+    const int a0 = (blk % ba) * 4, b0 = (blk / ba) * 4;
+    float s[4][4], c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
+    for (int r = lane; r < nb; r += 32) {
+      dfloat pa[4], qb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) pa[i] = (a0 + i < ka) ? df_from_scaled(P[(size_t)(a0 + i) * nb + r], 0) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) qb[j] = (b0 + j < kb) ? df_from_scaled(Q[(size_t)(b0 + j) * nb + r], 0) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_dot_add(s[i][j], c[i][j], pa[i], qb[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const dfloat v = df_warp_sum(df_norm(s[i][j], c[i][j]));
+        if (lane == 0 && a0 + i < ka && b0 + j < kb) W[(size_t)(b0 + j) * ldw + a0 + i] = alpha * df_to_scaled(v, 0);
+      }
+  }
+  __syncthreads();
+}
+
+// C[r + b nb] = alpha sum_l A[r + l nb] op(W)[l, b] for r < nb, b < kb, depth ka, with op(W)[l, b] =
+// W[l + b ldw] (tw = 0) or W[b + l ldw]: a thread per row (two at a time), 8 output columns at a time, op(W) staged as
+// double-float in shared memory 64 x 8 at a time.
+__device__ void cta_gemm_nn_thin(int nb, int kb, int ka, double alpha, const double* __restrict__ A,
+                                 const double* __restrict__ W, int ldw, int tw, double* __restrict__ C) {
+  __shared__ dfloat Ws[64][8];
+  for (int rb = 0; rb < nb; rb += 2 * blockDim.x) {  // up to 2 rows per thread at a time
+    for (int b0 = 0; b0 < kb; b0 += 8) {
+      float s[2][8], c[2][8];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { s[q][j] = 0.f; c[q][j] = 0.f; }
+      for (int l0 = 0; l0 < ka; l0 += 64) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
+          const int l = e >> 3, j = e & 7;
+          double v = 0.0;
+          if (l0 + l < ka && b0 + j < kb)
+            v = tw ? W[(size_t)(l0 + l) * ldw + b0 + j] : W[(size_t)(b0 + j) * ldw + l0 + l];
+          Ws[l][j] = df_from_scaled(v, 0);
+        }
+        __syncthreads();
+        const int lmax = min(64, ka - l0);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = rb + threadIdx.x + q * blockDim.x;
+          if (r >= nb) continue;
+          for (int l = 0; l < lmax; ++l) {
+            const dfloat a = df_from_scaled(A[(size_t)(l0 + l) * nb + r], 0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) df_dot_add(s[q][j], c[q][j], a, Ws[l][j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = rb + threadIdx.x + q * blockDim.x;
+        if (r >= nb) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (b0 + j < kb) C[(size_t)(b0 + j) * nb + r] = alpha * df_to_scaled(df_norm(s[q][j], c[q][j]), 0);
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
@@ -295,8 +464,7 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     Vd[e] = df_from_scaled(w.Vp[e], -w.ev[j]);
   }
   __syncthreads();
-  cta_geqr2_df(Ud, nb, nb, K, w.tu, sh);
-  cta_geqr2_df(Vd, nb, nb, K, w.tv, sh);
+  cta_geqr2_pair_df(Ud, w.tu, Vd, w.tv, nb, nb, K, w.vs);
   const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
   // R_u, R_v unscaled to float64 (Ke x K each, upper trapezoid) in the output buffers, then M = R_u R_v^T
   double* Ru = (double*)w.Uq;
@@ -426,8 +594,7 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from_scaled(Uo[e], 0);
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
-  cta_apply_q_df(Ud, nb, nb, Ke, w.tu, w.Uq, nb, k);
-  cta_apply_q_df(Vd, nb, nb, Ke, w.tv, w.Vq, nb, k);
+  cta_apply_q2_df(Ud, w.tu, w.Uq, Vd, w.tv, w.Vq, nb, nb, Ke, nb, k, w.vs);
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) {
     Uo[e] = df_to_scaled(w.Uq[e], 0);

@@ -549,6 +549,70 @@ int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, l
   return TLR_OK;
 }
 
+namespace {
+// descriptor q -> split descriptors 2q, 2q + 1 and GEMM descriptor q with fixed-size buffers
+__global__ void k_oz_from_gen(const GemmGen* __restrict__ g, int count, int k_min, int S, char* __restrict__ base,
+                              size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per, OzSrc* __restrict__ src,
+                              OzGemm* __restrict__ gem) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const GemmGen x = g[q];
+  char* p = base + (size_t)q * per;
+  uint16_t* sa = reinterpret_cast<uint16_t*>(p);
+  uint16_t* sb = reinterpret_cast<uint16_t*>(p + sa_bytes);
+  int* xa = reinterpret_cast<int*>(p + sa_bytes + sb_bytes);
+  int* xb = reinterpret_cast<int*>(p + sa_bytes + sb_bytes + xa_bytes);
+  const bool run = x.m > 0 && x.n > 0 && x.k >= k_min && x.k > 0;
+  OzSrc a, b;
+  a.X = x.A; a.ld = x.lda; a.col = x.tA ? 0 : 1; a.rows = run ? x.m : 0; a.depth = x.k; a.out = sa; a.ex = xa;
+  a.block_rows = OZ_BM;
+  b.X = x.B; b.ld = x.ldb; b.col = x.tB ? 1 : 0; b.rows = run ? x.n : 0; b.depth = x.k; b.out = sb; b.ex = xb;
+  b.block_rows = OZ_BN;
+  src[2 * q] = a;
+  src[2 * q + 1] = b;
+  OzGemm og;
+  const int nkb = (x.k + OZ_BK - 1) / OZ_BK;
+  og.a.sl = sa; og.a.ex = xa; og.a.rows = x.m; og.a.nkb = nkb;
+  og.b.sl = sb; og.b.ex = xb; og.b.rows = x.n; og.b.nkb = nkb;
+  og.C = x.C; og.ldc = x.ldc; og.m = run ? x.m : 0; og.n = run ? x.n : 0;
+  og.alpha = x.alpha; og.beta = x.beta; og.lower = x.lower;
+  gem[q] = og;
+}
+}  // namespace
+
+size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S) {
+  return align128(oz_slices_elems(max_m, max_k, OZ_BM, S) * 2) + align128(oz_slices_elems(max_n, max_k, OZ_BN, S) * 2) +
+         align128((size_t)round_up(max_m, OZ_BM) * 4) + align128((size_t)round_up(max_n, OZ_BN) * 4) +
+         2 * sizeof(OzSrc) + sizeof(OzGemm) + 64;
+}
+
+int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k, int k_min, int S, void* ws,
+                  size_t ws_bytes, long long* d_stat, cudaStream_t s) {
+  if (count <= 0) return TLR_OK;
+  const size_t sa = align128(oz_slices_elems(max_m, max_k, OZ_BM, S) * 2);
+  const size_t sb = align128(oz_slices_elems(max_n, max_k, OZ_BN, S) * 2);
+  const size_t xa = align128((size_t)round_up(max_m, OZ_BM) * 4);
+  const size_t xb = align128((size_t)round_up(max_n, OZ_BN) * 4);
+  const size_t per = sa + sb + xa + xb;
+  const size_t per_all = per + 2 * sizeof(OzSrc) + sizeof(OzGemm);
+  const int chunk = (int)std::min<size_t>(65535, ws_bytes > 512 ? (ws_bytes - 512) / per_all : 0);
+  if (chunk < 1) return TLR_ERR_OOM;
+  char* base = static_cast<char*>(ws);
+  for (int q0 = 0; q0 < count; q0 += chunk) {
+    const int cnt = std::min(chunk, count - q0);
+    char* descs = reinterpret_cast<char*>(align128(reinterpret_cast<size_t>(base + (size_t)cnt * per)));
+    OzSrc* src = reinterpret_cast<OzSrc*>(descs);
+    OzGemm* gem = reinterpret_cast<OzGemm*>(descs + align128((size_t)2 * cnt * sizeof(OzSrc)));
+    k_oz_from_gen<<<(cnt + 127) / 128, 128, 0, s>>>(d_g + q0, cnt, k_min, S, base, sa, sb, xa, per, src, gem);
+    TLR_LAUNCH_CHECK();
+    int rc = oz_split(src, 2 * cnt, std::max(max_m, max_n), max_k, S, s);
+    if (rc) return rc;
+    rc = oz_gemm(gem, cnt, max_m, max_n, S, d_stat, s);
+    if (rc) return rc;
+  }
+  return TLR_OK;
+}
+
 // Diagnostic entry point: one GEMM through the split and the tensor-core kernel, with
 // its own temporary buffers (cudaMalloc, synchronising).
 extern "C" int tlr_gemm_tc(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb, int tB,

@@ -61,6 +61,13 @@ size_t oz_slices_elems(int rows, int depth, int block_rows, int S);
 // ws (ws_bytes bytes, 128-byte aligned); entries with k = 0 only scale C by beta.  TLR_ERR_OOM when
 // one GEMM alone does not fit.  Time-outs are recorded in d_stat.
 int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, long long* d_stat, cudaStream_t s);
+// The same for descriptors in device memory (written by a kernel): every entry has m <= max_m,
+// n <= max_n, k <= max_k; slice buffers are sized for those bounds.  Entries with k < k_min are
+// skipped (left to the caller's CUDA-core path, which must skip k >= k_min).
+int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k, int k_min, int S, void* ws,
+                  size_t ws_bytes, long long* d_stat, cudaStream_t s);
+// bytes of workspace oz_run_device needs per descriptor for these bounds
+size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S);
 // split `count` operands (descriptors on the device); max_rows / max_depth bound the grid
 int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s);
 // batched GEMMs (descriptors on the device); tiles of the largest m x n; status words for time-outs

@@ -10,6 +10,7 @@
 #include <atomic>
 
 #include "recompress.cuh"
+#include "tcgemm.h"
 #include "tileops.h"
 
 namespace {
@@ -69,13 +70,18 @@ __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double ta
   double pf;  // product flops
   if (!X.dense && !Y.dense) {
     pf = 2.0 * nb * X.k * Y.k * 2.0;
-    cta_gemm_df(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);  // W = V_x^T U_y
+    // thin products for small ranks; 64 x 64-blocked ones once the blocks are mostly filled
+    const bool thin = X.k <= 48 && Y.k <= 48;
+    if (thin) cta_gemm_tn_thin(X.k, Y.k, nb, 1.0, X.V, Y.U, w.W, X.k);  // W = V_x^T U_y
+    else cta_gemm_df(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);
     if (Y.k <= X.k) {
-      cta_gemm_df(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
+      if (thin) cta_gemm_nn_thin(nb, Y.k, X.k, alpha, X.U, w.W, X.k, 0, Un);  // U_x W
+      else cta_gemm_df(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Un, nb);
       for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
       r = Y.k;
     } else {
-      cta_gemm_df(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Vn, nb);
+      if (thin) cta_gemm_nn_thin(nb, X.k, Y.k, 1.0, Y.V, w.W, X.k, 1, Vn);  // V_y W^T
+      else cta_gemm_df(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Vn, nb);
       for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
       r = X.k;
     }
@@ -100,16 +106,20 @@ __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double ta
 // an atomic counter (*ctr starts at 0), so a launch covers a whole phase and the
 // long items, listed first, overlap with the short ones.  Items touch distinct
 // target tiles and read only operand tiles that no item of the launch writes.
+// Every CTA has the same size, so an item's arithmetic does not depend on which
+// CTA takes it: results are bitwise reproducible.
 __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k, const int2* __restrict__ items,
                                                        int n_items, int* __restrict__ ctr, double eps,
                                                        const double* __restrict__ d_zeta, double zpow, int Kmax,
                                                        int trunc_cap, double* __restrict__ ws, size_t item_elems,
                                                        long long* __restrict__ st, double* __restrict__ flops) {
+  extern __shared__ dfloat vs_dyn[];  // 2 nb: staged reflectors of the recompression
   __shared__ double sh[TLR_THREADS / 32 + 2];
   __shared__ int shi[TLR_THREADS / 32 + 2];
   __shared__ int s_item;
   const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
   ItemWs w = item_ws(ws, item_elems, blockIdx.x, v.nb, Kmax, v.kcap);
+  w.vs = vs_dyn;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
     __syncthreads();
@@ -175,9 +185,9 @@ __global__ void k_upd_d_desc(TlrView v, int alg, int k, const int2* __restrict__
   d2[q] = g2;
 }
 
-__global__ void k_gemm_gen(const GemmGen* __restrict__ desc) {
+__global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
   const GemmGen g = desc[blockIdx.y];
-  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0) return;
+  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0 || g.k >= k_skip) return;
   cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
                      gridDim.x, g.lower);
 }
@@ -276,6 +286,7 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
   const int64_t tt = dtile_index(it.x, it.y);
   const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
   ItemWs w = item_ws(ws, item_elems, blockIdx.x, nb, Kmax, v.kcap);
+  w.vs = reinterpret_cast<dfloat*>(dsm);  // free after the cross approximation
   DenseEntry de{bufs + (size_t)blockIdx.x * nb * nb, nb};
   int conv = 0;
   const int k = cta_aca(de, nb, nb, nb, tau * 0.125, aca_max, w, dsm, sh, shi, &conv);
@@ -322,17 +333,25 @@ __global__ void k_copy_back(const GemmGen* __restrict__ desc, double* const* __r
     X[e] = g.C[e];
 }
 
-// resident CTAs of the persistent low-rank update kernel on the current device
-int resident_ctas() {
+// dynamic shared memory of the persistent low-rank update kernel (two staged reflectors)
+size_t upd_smem(int nb) { return 2 * (size_t)nb * sizeof(dfloat); }
+
+// resident CTAs of the persistent low-rank update kernel on the current device for tile size nb
+int resident_ctas(int nb) {
   static std::atomic<int> cached[64];
+  static std::atomic<int> cached_nb[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   const int c = cached[dev].load();
-  if (c > 0) return c;
+  if (c > 0 && cached_nb[dev].load() == nb) return c;
   int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_lr_gen, TLR_THREADS, 0) != cudaSuccess ||
+  if (upd_smem(nb) > 48 * 1024 &&
+      cudaFuncSetAttribute(k_upd_lr_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem(nb)) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_lr_gen, TLR_THREADS, upd_smem(nb)) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
+  cached_nb[dev].store(nb);
   cached[dev].store(std::max(per_sm, 1) * sms);
   return std::max(per_sm, 1) * sms;
 }
@@ -346,16 +365,39 @@ int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
 
 }  // namespace
 
-int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s) {
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip) {
   if (count <= 0) return TLR_OK;
   const int blocks = ((m + 63) / 64) * ((n + 63) / 64);
   for (int c0 = 0; c0 < count; c0 += 65535) {
     const int cnt = count - c0 < 65535 ? count - c0 : 65535;
-    k_gemm_gen<<<dim3(blocks, cnt), 256, 0, s>>>(d_desc + c0);
+    k_gemm_gen<<<dim3(blocks, cnt), 256, 0, s>>>(d_desc + c0, k_skip);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
 }
+
+namespace {
+// depth from which a batched product runs on the tensor cores (digit slices) instead of the CUDA cores
+constexpr int TC_MIN_DEPTH = 256;
+
+// doubles of tensor-core workspace per descriptor of an m x n x k batched product (0: CUDA cores only)
+size_t tc_item_doubles(const tlr_ctx* h, int m, int n, int k) {
+  const int S = tlr_tc_slices(h);
+  if (!S || k < TC_MIN_DEPTH) return 0;
+  return (oz_device_item_bytes(m, n, k, S) + 7) / 8;
+}
+
+// batched product of device descriptors (m, n, k bounds): depths >= TC_MIN_DEPTH on the tensor cores with
+// the workspace tc (tc_doubles), the others on the CUDA cores
+int tops_gemm_mixed(tlr_ctx* h, const GemmGen* d_desc, int count, int m, int n, int kmax, double* tc, size_t tc_doubles,
+                    cudaStream_t s) {
+  const int S = tlr_tc_slices(h);
+  if (!S || kmax < TC_MIN_DEPTH || !tc_doubles) return tops_gemm(d_desc, count, m, n, s);
+  int rc = oz_run_device(d_desc, count, m, n, kmax, TC_MIN_DEPTH, S, tc, tc_doubles * 8, h->d_stat, s);
+  if (rc) return rc;
+  return tops_gemm(d_desc, count, m, n, s, TC_MIN_DEPTH);
+}
+}  // namespace
 
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
                 int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve) {
@@ -363,7 +405,9 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     PhaseScope ps("update.dense_target", s);
     const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
     const size_t gd = (sizeof(GemmGen) + 7) / 8;
-    int chunk = chunk_of(h, per + 3 * gd, 16);
+    const int nc = h->kcap > h->nb ? h->nb : h->kcap;
+    const size_t tcd = std::max(tc_item_doubles(h, h->nb, nc, h->nb), tc_item_doubles(h, h->nb, h->nb, h->nb));
+    int chunk = chunk_of(h, per + 3 * gd + tcd, 64);
     if (chunk < 1) return TLR_ERR_OOM;
     for (int64_t q0 = 0; q0 < n_dn; q0 += chunk) {
       const int cnt = (int)(n_dn - q0 < chunk ? n_dn - q0 : chunk);
@@ -371,13 +415,18 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
       GemmGen* d1 = (GemmGen*)(h->scratch + (size_t)cnt * gd + 1);
       GemmGen* d2 = (GemmGen*)(h->scratch + 2 * ((size_t)cnt * gd + 1));
       double* ws = h->scratch + 3 * ((size_t)cnt * gd + 1);
+      // tensor-core workspace after the items' buffers, 128-byte aligned
+      double* tc = ws + (size_t)cnt * per + 16;
+      tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
+      const size_t tc_avail = (size_t)(h->scratch + h->scratch_elems - tc);
       k_upd_d_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dn + q0, cnt, d0, d1, d2, ws, per);
       TLR_LAUNCH_CHECK();
-      int rc = tops_gemm(d0, cnt, h->nb, h->kcap > h->nb ? h->nb : h->kcap, s);
+      // stage 0 (a dense factor times a thin one, depth nb) and stage 2 (dense x dense, depth nb)
+      int rc = tops_gemm_mixed(h, d0, cnt, h->nb, nc, h->nb, tc, tcd ? tc_avail : 0, s);
       if (rc) return rc;
-      rc = tops_gemm(d1, cnt, h->nb, h->kcap > h->nb ? h->nb : h->kcap, s);
+      rc = tops_gemm(d1, cnt, h->nb, nc, s);
       if (rc) return rc;
-      rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
+      rc = tops_gemm_mixed(h, d2, cnt, h->nb, h->nb, h->nb, tc, tcd ? tc_avail : 0, s);
       if (rc) return rc;
     }
   }
@@ -386,13 +435,13 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     const size_t ie = tlr_item_elems(h->nb, h->kcap);
     const int chunk = chunk_of(h, ie, 0);
     if (chunk < 1) return TLR_ERR_OOM;
-    const int slots = std::max(resident_ctas() - std::max(reserve, 0), 1);
+    const int slots = std::max(resident_ctas(h->nb) - std::max(reserve, 0), 1);
     const int grid = (int)std::min<int64_t>(n_lr, std::min(slots, chunk));
     TLR_CUDA_TRY(cudaMemsetAsync(h->d_ctr, 0, sizeof(int), s));
     if (g_tlr_prof.enabled) tlr_prof_begin(s);
-    k_upd_lr_gen<<<grid, TLR_THREADS, 0, s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
-                                              2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie, h->d_stat,
-                                              g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
+    k_upd_lr_gen<<<grid, TLR_THREADS, upd_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
+                                                            2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie,
+                                                            h->d_stat, g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
     TLR_LAUNCH_CHECK();
     if (g_tlr_prof.enabled) tlr_prof_end(s);
   }
@@ -411,8 +460,9 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   const size_t nn = (size_t)h->nb * h->nb;
   const size_t ie = tlr_item_elems(h->nb, h->kcap);
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
-  const size_t per = tops_dd_item_elems(h);
-  const int chunk = ws_elems > 16 ? (int)std::min<size_t>((ws_elems - 16) / per, 65535) : 0;
+  const size_t tcd = tc_item_doubles(h, h->nb, h->nb, h->nb);
+  const size_t per = tops_dd_item_elems(h) + tcd;
+  const int chunk = ws_elems > 64 ? (int)std::min<size_t>((ws_elems - 64) / per, 65535) : 0;
   if (chunk < 1) return TLR_ERR_OOM;
   const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
   if (smem > 48 * 1024)
@@ -424,9 +474,12 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
     GemmGen* d2 = (GemmGen*)(ws_base + (size_t)cnt * gd + 1);
     double* bufs = ws_base + 2 * (size_t)cnt * gd + 2;
     double* ws = bufs + (size_t)cnt * nn;
+    double* tc = ws + (size_t)cnt * ie + 16;
+    tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
+    const size_t tc_avail = tcd ? (size_t)(ws_base + ws_elems - tc) : 0;
     k_dd_prep<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dd + q0, cnt, d1, d2, bufs);
     TLR_LAUNCH_CHECK();
-    int rc = tops_gemm(d1, cnt, h->nb, h->nb, s);
+    int rc = tops_gemm_mixed(h, d1, cnt, h->nb, h->nb, h->nb, tc, tc_avail, s);
     if (rc) return rc;
     rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
     if (rc) return rc;
@@ -448,19 +501,23 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
     if (total <= 0) continue;
     const size_t tmp_elems = pass == 0 ? nb * (size_t)h->kcap : nb * nb;
     const int ncols_max = pass == 0 ? h->kcap : h->nb;
-    const int chunk = chunk_of(h, tmp_elems + gd, 64);
+    const size_t tcd = tc_item_doubles(h, h->nb, ncols_max, h->nb);
+    const int chunk = chunk_of(h, tmp_elems + gd + tcd, 128);
     if (chunk < 1) return TLR_ERR_OOM;
     for (int q0 = 0; q0 < total; q0 += chunk) {
       const int cnt = total - q0 < chunk ? total - q0 : chunk;
       GemmGen* desc = (GemmGen*)h->scratch;
       double** dst = (double**)(h->scratch + (size_t)cnt * (gd - 1) + 8);
       double* tmp = h->scratch + (size_t)cnt * gd + 16;
+      double* tc = tmp + (size_t)cnt * tmp_elems + 16;
+      tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
+      const size_t tc_avail = tcd ? (size_t)(h->scratch + h->scratch_elems - tc) : 0;
       k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, m_stride, m_by, pass == 0 ? transM : transM_dense,
                                                       items + q0, cnt,
                                                       pass == 0 ? which : 2, dense_right, alpha, tmp, tmp_elems,
                                                       desc, dst);
       TLR_LAUNCH_CHECK();
-      int rc = tops_gemm(desc, cnt, h->nb, ncols_max, s);
+      int rc = tops_gemm_mixed(h, desc, cnt, h->nb, ncols_max, h->nb, tc, tc_avail, s);
       if (rc) return rc;
       k_copy_back<<<dim3(32, cnt), 256, 0, s>>>(desc, dst);
       TLR_LAUNCH_CHECK();

@@ -38,5 +38,6 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
 // X = T^{-1} for a lower triangular nb x nb tile (X fully written)
 int tops_trinv(const double* T, int nb, double* X, cudaStream_t s);
 // batched general GEMM from a device descriptor array
-int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s);
+// (descriptors with k >= k_skip are left out: another path computes them)
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30);
 
