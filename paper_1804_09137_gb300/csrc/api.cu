@@ -142,7 +142,8 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk};
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk,
+                  h->gpart};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->aux) cudaStreamDestroy(h->aux);
@@ -155,6 +156,7 @@ void free_ctx(tlr_ctx* h) {
   free(h->kindz);
   free(h->h_zlist);
   free(h->zoff);
+  free(h->hslotz);
   delete h;
 }
 
@@ -783,8 +785,9 @@ extern "C" int tlr_loglik_grad(tlr_handle h, const double* z, double* d_ll, doub
     TLR_CUDA_TRY(cudaMemcpyAsync(a, w, h->npad * sizeof(double), cudaMemcpyDeviceToDevice, s));
     TRY(tlr_bwd_solve(h, a, s));
   }
-  TRY(tlr_inverse(h, s));
-  {
+  int fused = 0;
+  TRY(tlr_inverse(h, s, a, d_grad3, &fused));
+  if (!fused) {
     PhaseScope ps("grad_fused", s);
     TRY(tlr_grad_fused(h, a, d_grad3, s));
   }

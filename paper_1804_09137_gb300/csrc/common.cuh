@@ -123,6 +123,9 @@ struct tlr_ctx {
   // copy of the inverse's dense sources (diagonal and dense tiles) read by LAUUM
   double* msave;
   size_t msave_elems;
+  int* hslotz;        // host copy of the inverse's dense slots
+  double* gpart;      // partial sums of the gradient reduced inside LAUUM
+  size_t gpart_elems;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -315,7 +318,13 @@ int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s);
 int tlr_reduce_loglik(tlr_ctx* h, const double* w, double* out3, cudaStream_t s);
-int tlr_inverse(tlr_ctx* h, cudaStream_t s);
+// TRTRI + LAUUM; with alpha = Sigma^{-1} z (sorted) and out3 given and tensor-core products enabled,
+// the gradient's beta and nu entries are reduced inside LAUUM into out3[1], out3[2] (*fused = 1)
+// instead of forming Sigma^{-1}
+int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha = nullptr, double* out3 = nullptr,
+                int* fused = nullptr);
+// out2[0] = sum part[2 i], out2[1] = sum part[2 i + 1] over i < count, in a fixed order (ws: 512 doubles)
+int tlr_sum_pairs(const double* part, int64_t count, double* out2, double* ws, cudaStream_t s);
 int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s);
 int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s);
 int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,

@@ -123,7 +123,30 @@ __global__ void k_sum3_stage(const double* __restrict__ part, int64_t cnt, doubl
   if (threadIdx.x == 0) { out[3 * blockIdx.x] = s0; out[3 * blockIdx.x + 1] = s1; out[3 * blockIdx.x + 2] = s2; }
 }
 
+__global__ void k_sum2_stage(const double* __restrict__ part, int64_t cnt, double* __restrict__ out) {
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  double s0 = 0.0, s1 = 0.0;
+  const int64_t per = (cnt + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(cnt, b0 + per);
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    s0 += part[2 * i];
+    s1 += part[2 * i + 1];
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) { out[2 * blockIdx.x] = s0; out[2 * blockIdx.x + 1] = s1; }
+}
+
 }  // namespace
+
+int tlr_sum_pairs(const double* part, int64_t count, double* out2, double* ws, cudaStream_t s) {
+  const int nstage = 256;
+  k_sum2_stage<<<nstage, TLR_THREADS, 0, s>>>(part, count, ws);
+  TLR_LAUNCH_CHECK();
+  k_sum2_stage<<<1, TLR_THREADS, 0, s>>>(ws, nstage, out2);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
 
 // out3 = (dl/dsigma2, dl/dbeta, dl/dnu); alpha = Sigma^{-1} z in sorted order
 int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s) {

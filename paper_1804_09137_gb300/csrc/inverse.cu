@@ -124,15 +124,23 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   // a low-rank tile is materialised and recompressed instead (phases *_DD).
   // every tile owns dense slot t: L^{-1}'s dense tiles use it during TRTRI, and
   // every tile of Sigma^{-1} is accumulated densely there during LAUUM
+  // (with the gradient fused into the products Sigma^{-1} is never stored: the dense tiles of L^{-1}
+  // get compact slots instead)
+  const bool compact = tlr_tc_slices_opt(h) > 0;
   std::vector<int> slot(std::max<int64_t>(T, 1), -1);
   int nd = 0;
   for (int64_t t = 0; t < T; ++t)
-    if (K[t]) { slot[t] = (int)t; ++nd; }
-  if (T > h->dcapz) {
+    if (K[t]) { slot[t] = compact ? nd : (int)t; ++nd; }
+  free(h->hslotz);
+  h->hslotz = (int*)malloc(std::max<int64_t>(T, 1) * sizeof(int));
+  if (!h->hslotz) return TLR_ERR_OOM;
+  memcpy(h->hslotz, slot.data(), std::max<int64_t>(T, 1) * sizeof(int));
+  const int64_t pool_want = compact ? std::max(nd, 1) : std::max<int64_t>(T, 1);
+  if (pool_want > h->dcapz) {
     if (h->dpoolz) cudaFree(h->dpoolz);
     h->dpoolz = nullptr;
     h->dcapz = 0;
-    const int want = (int)std::max<int64_t>(T, 1);
+    const int want = (int)pool_want;
     if (cudaMalloc((void**)&h->dpoolz, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return TLR_ERR_OOM;
@@ -267,7 +275,7 @@ static int seg_copy(const CopySeg* d_segs, int64_t n, cudaStream_t s) {
 // of depth sum(rank) written once; dense x dense products are added afterwards, one
 // GEMM per tile and launch.  Z overwrites the dense sources' slots, so those (and the
 // diagonal) are read from a copy.  Workspace: h->scratch (descriptors, G, panels).
-static int lauum_left(tlr_ctx* h, cudaStream_t s) {
+static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3) {
   const int nt = h->nt, nb = h->nb;
   const int64_t T = h->ntiles;
   const size_t nn = (size_t)nb * nb;
@@ -281,7 +289,11 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
   int nd = 0;
   for (int64_t t = 0; t < T; ++t)
     if (K[t]) dix[t] = nd++;
-  const size_t msave_want = (size_t)(nt + nd) * nn;
+  // fused: Sigma^{-1} is never stored; the tiles of each target are reduced into the gradient by the
+  // tensor-core epilogue, and the dense sources are read where TRTRI left them (Dz, compact dense pool)
+  const int S = tlr_tc_slices(h);
+  const bool fused = S > 0 && alpha && out3;
+  const size_t msave_want = fused ? 0 : (size_t)(nt + nd) * nn;
   if (msave_want > h->msave_elems) {
     if (h->msave) cudaFree(h->msave);
     h->msave = nullptr;
@@ -294,6 +306,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
   }
   auto isD = [&](int p, int q) { return p == q || K[tile_index(p, q)]; };
   auto Msrc = [&](int p, int q) -> const double* {
+    if (fused) return p == q ? h->Dz + (size_t)p * nn : h->dpoolz + (size_t)h->hslotz[tile_index(p, q)] * nn;
     return p == q ? h->msave + (size_t)p * nn : h->msave + (size_t)(nt + dix[tile_index(p, q)]) * nn;
   };
   auto Uof = [&](int p, int q) -> const double* { return h->Uz + (size_t)tile_index(p, q) * nb * h->kcap; };
@@ -304,7 +317,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
   };
   static_assert(sizeof(GemmGen) % 8 == 0 && sizeof(CopySeg) % 8 == 0, "descriptor regions are 8-byte padded");
   const size_t gd = sizeof(GemmGen) / 8, cd = sizeof(CopySeg) / 8;
-  {  // dense sources and diagonal tiles into the copy
+  if (!fused) {  // dense sources and diagonal tiles into the copy
     std::vector<CopySeg> cs;
     cs.push_back({h->Dz, h->msave, (int64_t)nt * (int64_t)nn});
     for (int64_t t = 0; t < T; ++t)
@@ -316,12 +329,14 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
   // targets (m, n), m >= n, and their depth
   std::vector<int2> tg;
   std::vector<int64_t> depth, gel;
+  std::vector<int> ndd;  // dense x dense products per target
   for (int m = 0; m < nt; ++m)
     for (int n = 0; n <= m; ++n) {
       int64_t d = 0, g = 0;
+      int cdd = 0;
       for (int k = m; k < nt; ++k) {
         const bool dm = isD(k, m), dn = isD(k, n);
-        if (dm && dn) continue;
+        if (dm && dn) { ++cdd; continue; }
         if (!dm && !dn) {
           const int a = rnk(k, m), c = rnk(k, n);
           if (a == 0 || c == 0) continue;
@@ -334,10 +349,10 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
       tg.push_back(make_int2(m, n));
       depth.push_back(d);
       gel.push_back(g);
+      ndd.push_back(cdd);
     }
   // tensor-core path of the stacked-panel products: bf16 slices of both panels, row exponents,
   // split and GEMM descriptors, per target tile (doubles of workspace)
-  const int S = tlr_tc_slices(h);
   const int rows_a = (nb + OZ_BM - 1) / OZ_BM * OZ_BM, rows_b = (nb + OZ_BN - 1) / OZ_BN * OZ_BN;
   const size_t od = (2 * sizeof(OzSrc) + sizeof(OzGemm) + 7) / 8;
   auto slice_dbl = [&](int64_t d) -> size_t {
@@ -345,12 +360,34 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     return (oz_slices_elems(nb, (int)d, OZ_BM, S) + oz_slices_elems(nb, (int)d, OZ_BN, S)) / 4 +
            (size_t)(rows_a + rows_b + 1) / 2 + od + 48;
   };
+  auto pad = [](int64_t d) { return (d + OZ_BK - 1) / OZ_BK * OZ_BK; };
+  // depth of a fused target's operands: its panel and one segment per dense x dense product
+  auto fdepth = [&](size_t q) { return pad(depth[q]) + (int64_t)ndd[q] * pad(nb); };
+  auto tgt_slices = [&](size_t q) -> size_t {
+    return fused ? slice_dbl(fdepth(q)) + (size_t)ndd[q] * (2 * sizeof(OzSrc) + 7) / 8 : slice_dbl(depth[q]);
+  };
+  // partial sums of the fused gradient: eight per CTA tile of every target
+  const int tiles_per = ((nb + OZ_BM - 1) / OZ_BM) * ((nb + OZ_BN - 1) / OZ_BN);
+  if (fused) {
+    const size_t want = (size_t)tg.size() * tiles_per * 8;
+    if (want > h->gpart_elems) {
+      if (h->gpart) cudaFree(h->gpart);
+      h->gpart = nullptr;
+      h->gpart_elems = 0;
+      if (cudaMalloc((void**)&h->gpart, want * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return TLR_ERR_OOM;
+      }
+      h->gpart_elems = want;
+    }
+    TLR_CUDA_TRY(cudaMemsetAsync(h->gpart, 0, want * sizeof(double), s));
+  }
   // one target alone must fit (with the reserve for a full-depth product): grow the workspace if not
   {
     size_t worst = 0;
     for (size_t q = 0; q < tg.size(); ++q) {
       const size_t per = (size_t)(nt - tg[q].x) * (3 * gd + cd + 2) + gd + (size_t)gel[q] +
-                         2 * (size_t)nb * depth[q] + 8 + slice_dbl(depth[q]);
+                         2 * (size_t)nb * depth[q] + 8 + tgt_slices(q);
       worst = std::max(worst, per);
     }
     worst += 64 + slice_dbl(nb);
@@ -377,7 +414,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     while (b1 < tg.size()) {
       const int m = tg[b1].x;
       const size_t per = (size_t)(nt - m) * (3 * gd + cd + 2) + gd + (size_t)gel[b1] + 2 * (size_t)nb * depth[b1] + 8 +
-                         slice_dbl(depth[b1]);
+                         tgt_slices(b1);
       if (b1 > b0 && need + per > budget) break;
       need += per;
       ++b1;
@@ -412,7 +449,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     GemmGen* dbig = dg2 + n_g2;
     GemmGen* ddd = dbig + nbig;
     size_t n_dd = 0;
-    for (size_t q = b0; q < b1; ++q)
+    for (size_t q = b0; q < b1 && !fused; ++q)
       for (int k = tg[q].x; k < nt; ++k) n_dd += isD(k, tg[q].x) && isD(k, tg[q].y);
     CopySeg* dcs = (CopySeg*)(ddd + n_dd);
     double* Gw = base + ((size_t)(n_g1 + n_g1b + n_g2 + nbig + n_dd) * gd + n_cs * cd + 8);
@@ -431,6 +468,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     int mx_g = 1, mx_r = 1;
     size_t goff = 0;
     double* P = Pw;
+    std::vector<std::vector<int>> ddk(b1 - b0);  // fused: the dense x dense sources of each target
     for (size_t q = b0; q < b1; ++q) {
       const int m = tg[q].x, n = tg[q].y;
       double* Ap = P;
@@ -440,6 +478,10 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
       for (int k = m; k < nt; ++k) {
         const bool dm = isD(k, m), dn = isD(k, n);
         if (dm && dn) {
+          if (fused) {
+            ddk[q - b0].push_back(k);
+            continue;
+          }
           if ((int)gdd.size() <= r_dd) gdd.emplace_back();
           gdd[r_dd++].push_back(gemm(nb, nb, nb, Msrc(k, m), nb, 1, Msrc(k, n), nb, 0, Zdst(m, n), nb, 1.0));
           continue;
@@ -479,7 +521,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
         }
       }
       if (off != depth[q]) return TLR_ERR_STATE;
-      gbig.push_back(gemm(nb, nb, (int)off, Ap, nb, 0, Bp, nb, 1, Zdst(m, n), nb, 0.0));
+      gbig.push_back(gemm(nb, nb, (int)off, Ap, nb, 0, Bp, nb, 1, fused ? nullptr : Zdst(m, n), nb, 0.0));
       P += 2 * (size_t)nb * depth[q];
     }
     // one upload of descriptors and copy segments, in the order of the device layout
@@ -509,7 +551,74 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
       else ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
       ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s));
     }
-    {
+    if (fused) {
+      // each target: operand A = [panel A | M_km^T ...], B = [panel B | M_kn^T ...] as k segments,
+      // reduced into the gradient by the epilogue (no tile of Sigma^{-1} is written)
+      PhaseScope ps("lauum.gemm_grad", s);
+      auto align = [](char* p) { return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127); };
+      char* sp = tcw;
+      std::vector<OzSrc> src;
+      std::vector<OzGemm> gem;
+      std::vector<std::pair<int*, size_t>> zero_ex;
+      int max_depth = 1;
+      for (size_t q = b0; q < b1; ++q) {
+        const GemmGen& gb = gbig[q - b0];
+        const int m = tg[q].x, n = tg[q].y;
+        const int64_t dtot = fdepth(q);
+        const int nkb = (int)(dtot / OZ_BK);
+        OzGemm og;
+        memset(&og, 0, sizeof(og));
+        og.m = nb; og.n = nb; og.ldc = nb; og.alpha = 1.0; og.beta = 0.0;
+        og.mode = 1; og.diag = m == n; og.lower = m == n;
+        og.p0a = (int64_t)m * nb; og.p0b = (int64_t)n * nb;
+        og.part_off = (int64_t)q * tiles_per;
+        if (nkb > 0) {
+          sp = align(sp);
+          uint16_t* sa = reinterpret_cast<uint16_t*>(sp);
+          sp += oz_slices_elems(nb, (int)dtot, OZ_BM, S) * 2;
+          uint16_t* sb = reinterpret_cast<uint16_t*>(sp);
+          sp += oz_slices_elems(nb, (int)dtot, OZ_BN, S) * 2;
+          int* xa = reinterpret_cast<int*>(sp);
+          sp += rows_a * sizeof(int);
+          int* xb = reinterpret_cast<int*>(sp);
+          sp += rows_b * sizeof(int);
+          zero_ex.push_back({xa, (size_t)rows_a});
+          zero_ex.push_back({xb, (size_t)rows_b});
+          int kb = 0;
+          if (gb.k > 0) {  // the panels: element (a, c) at Ap[c nb + a], (b, c) at Bp[c nb + b]
+            src.push_back({gb.A, nb, 1, nb, gb.k, sa, xa, OZ_BM, kb, nkb, 1});
+            src.push_back({gb.B, nb, 1, nb, gb.k, sb, xb, OZ_BN, kb, nkb, 1});
+            kb += (int)(pad(gb.k) / OZ_BK);
+            max_depth = std::max(max_depth, gb.k);
+          }
+          for (int k : ddk[q - b0]) {  // M_km^T M_kn: (a, c) at M_km[a nb + c], (b, c) at M_kn[b nb + c]
+            src.push_back({Msrc(k, m), nb, 0, nb, nb, sa, xa, OZ_BM, kb, nkb, 1});
+            src.push_back({Msrc(k, n), nb, 0, nb, nb, sb, xb, OZ_BN, kb, nkb, 1});
+            kb += (int)(pad(nb) / OZ_BK);
+            max_depth = std::max(max_depth, nb);
+          }
+          og.a = {sa, xa, nb, nkb};
+          og.b = {sb, xb, nb, nkb};
+        }
+        gem.push_back(og);
+      }
+      sp = align(sp);
+      OzSrc* dsrc = reinterpret_cast<OzSrc*>(sp);
+      sp += src.size() * sizeof(OzSrc);
+      sp = align(sp);
+      OzGemm* dgem = reinterpret_cast<OzGemm*>(sp);
+      sp += gem.size() * sizeof(OzGemm);
+      if (sp > reinterpret_cast<char*>(base + budget)) return TLR_ERR_OOM;
+      for (auto& z : zero_ex) TLR_CUDA_TRY(cudaMemsetAsync(z.first, 0, z.second * sizeof(int), s));
+      if (!src.empty())
+        TLR_CUDA_TRY(cudaMemcpyAsync(dsrc, src.data(), src.size() * sizeof(OzSrc), cudaMemcpyHostToDevice, s));
+      TLR_CUDA_TRY(cudaMemcpyAsync(dgem, gem.data(), gem.size() * sizeof(OzGemm), cudaMemcpyHostToDevice, s));
+      if (!src.empty()) ZTRY(oz_split(dsrc, (int)src.size(), nb, max_depth, S, s));
+      OzGradCtx gx;
+      memset(&gx, 0, sizeof(gx));
+      gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;
+      ZTRY(oz_gemm(dgem, (int)gem.size(), nb, nb, S, h->d_stat, s, &gx));
+    } else {
       PhaseScope ps("lauum.gemm", s);
       if (S) ZTRY(oz_run_host(gbig.data(), (int)gbig.size(), S, tcw, tcw_bytes, h->d_stat, s));
       else ZTRY(tops_gemm(dbig, (int)nbig, nb, nb, s));
@@ -523,7 +632,9 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s) {
     }
     b0 = b1;
   }
-  if (T > 0) {
+  if (fused) {  // dl/dbeta, dl/dnu from the partial sums, in a fixed order
+    ZTRY(tlr_sum_pairs(h->gpart, (int64_t)tg.size() * tiles_per * 4, out3 + 1, h->scratch, s));
+  } else if (T > 0) {
     k_mark_all_dense<<<256, 256, 0, s>>>(h->dslotz, T);
     TLR_LAUNCH_CHECK();
   }
@@ -562,7 +673,7 @@ struct InverseScope {  // marks the handle as forming the inverse for the scope'
 };
 }  // namespace
 
-int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
+int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, int* fused) {
   InverseScope scope(h);
   ZTRY(ensure_z(h));
   if (!h->zplan_valid) ZTRY(zplan(h, s));
@@ -643,7 +754,8 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s) {
     TLR_LAUNCH_CHECK();
   }
   // ---- LAUUM
-  { PhaseScope ps("lauum", s); ZTRY(lauum_left(h, s)); }
+  if (fused) *fused = tlr_tc_slices(h) > 0 && alpha && out3;
+  { PhaseScope ps("lauum", s); ZTRY(lauum_left(h, s, alpha, out3)); }
   h->zplan_valid = 0;  // the device tile kinds of Z changed: the next inverse re-plans
   return TLR_OK;
 }

@@ -173,7 +173,8 @@ __global__ void k_oz_rowexp(const OzSrc* __restrict__ srcs) {
     int E = 0;
     if (r < d.rows)
       for (int k = 0; k < d.depth; ++k) E = max(E, dexp(d.X[(size_t)k * d.ld + r]));
-    d.ex[r] = E;
+    if (d.multi) atomicMax(&d.ex[r], E);
+    else d.ex[r] = E;
   } else {  // element (r, k) at X[r * ld + k]: a warp per row
     const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (r >= rows_pad) return;
@@ -181,7 +182,10 @@ __global__ void k_oz_rowexp(const OzSrc* __restrict__ srcs) {
     if (r < d.rows)
       for (int k = lane; k < d.depth; k += 32) E = max(E, dexp(d.X[(size_t)r * d.ld + k]));
     for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
-    if (lane == 0) d.ex[r] = E;
+    if (lane == 0) {
+      if (d.multi) atomicMax(&d.ex[r], E);
+      else d.ex[r] = E;
+    }
   }
 }
 
@@ -224,8 +228,8 @@ __global__ void k_oz_split(const OzSrc* __restrict__ srcs) {
       w[s][j >> 1] |= h << (16 * (j & 1));
     }
   }
-  const int nkb = depth_pad / OZ_BK;
-  const int rb = r / BR, rr = r % BR, kb = (q * 8) / OZ_BK, kq = ((q * 8) % OZ_BK) / 8;
+  const int nkb = d.nkb > 0 ? d.nkb : depth_pad / OZ_BK;
+  const int rb = r / BR, rr = r % BR, kb = d.kb0 + (q * 8) / OZ_BK, kq = ((q * 8) % OZ_BK) / 8;
   const size_t tile = (size_t)BR * OZ_BK;  // bf16 per slice tile
   const size_t in_tile = (size_t)((rr >> 3) * (OZ_BK / 8) + kq) * 64 + (size_t)(rr & 7) * 8;
 #pragma unroll
@@ -238,7 +242,7 @@ __global__ void k_oz_split(const OzSrc* __restrict__ srcs) {
 // ------------------------------------------------------------------ GEMM
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restrict__ descs, int tiles_m,
-                                                           long long* __restrict__ st) {
+                                                           long long* __restrict__ st, const OzGradCtx gx) {
   using Sh = OzShape<S>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const OzGemm g = descs[blockIdx.y];
@@ -389,7 +393,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restr
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (ok) {
+    if (ok && g.mode == 1) {
+      // gradient: (alpha_a alpha_b - Z_ab) dC/dbeta, dC/dnu over this tile's entries, one partial per warp
+      const int a = r0 + row;
+      const int64_t pa = g.p0a + a;
+      double g1 = 0.0, g2 = 0.0;
+      if (a < g.m && pa < gx.n) {
+        const int ea = nkb > 0 ? g.a.ex[a] : 0;
+        const double xa = gx.x[pa], ya = gx.y[pa], wa = gx.alpha[pa];
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) {
+          const int b = c0 + j;
+          const int64_t pb = g.p0b + b;
+          if (b < g.n && pb < gx.n && (!g.diag || a > b)) {
+            const int eb = nkb > 0 ? g.b.ex[b] : 0;
+            const double zab =
+                (ea == 0 || eb == 0) ? 0.0 : df_to_scaled(df_norm(hi[j], lo[j]), (ea - 1022) + (eb - 1022));
+            const double rr = pt_dist(gx.mp, xa, ya, gx.x[pb], gx.y[pb]);
+            if (rr > 0.0) {
+              double t;
+              const int jt = tab_locate(rr, gx.mp.e_lo, &t);
+              if (jt >= 0 && jt < TAB_NINT) {  // below the table the derivatives vanish
+                const double w = wa * gx.alpha[pb] - zab;
+                g1 = fma(w, tab_poly(gx.tab + (size_t)(TAB_NINT + jt) * TAB_NC, t), g1);
+                g2 = fma(w, tab_poly(gx.tab + (size_t)(2 * TAB_NINT + jt) * TAB_NC, t), g2);
+              }
+            }
+          }
+        }
+      }
+      g1 = warp_sum(g1);
+      g2 = warp_sum(g2);
+      if (lane == 0) {
+        double* p = gx.part + 8 * (g.part_off + blockIdx.x) + 2 * qtr;
+        p[0] = g1;
+        p[1] = g2;
+      }
+    }
+    if (ok && g.mode == 0) {
       const int r = r0 + row;
       const int ea = (r < g.m && nkb > 0) ? g.a.ex[r] : 0;
 #pragma unroll
@@ -434,7 +475,11 @@ int launch_split(const OzSrc* d_src, int count, int max_rows, int max_depth, cud
 }
 
 template <int S>
-int launch_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, long long* d_stat, cudaStream_t s) {
+int launch_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, long long* d_stat, cudaStream_t s,
+                const OzGradCtx* gctx) {
+  OzGradCtx gx;
+  if (gctx) gx = *gctx;
+  else memset(&gx, 0, sizeof(gx));
   static bool attr_set[64] = {false};
   int dev = 0;
   TLR_CUDA_TRY(cudaGetDevice(&dev));
@@ -445,7 +490,7 @@ int launch_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, long long
   const int tm = (max_m + OZ_BM - 1) / OZ_BM, tn = (max_n + OZ_BN - 1) / OZ_BN;
   for (int c0 = 0; c0 < count; c0 += 65535) {
     const int cnt = std::min(65535, count - c0);
-    k_oz_gemm<S><<<dim3(tm * tn, cnt), OZ_THREADS, OzShape<S>::SMEM, s>>>(d_desc + c0, tm, d_stat);
+    k_oz_gemm<S><<<dim3(tm * tn, cnt), OZ_THREADS, OzShape<S>::SMEM, s>>>(d_desc + c0, tm, d_stat, gx);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
@@ -467,12 +512,13 @@ int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, 
   }
 }
 
-int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s) {
+int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s,
+            const OzGradCtx* gctx) {
   if (count <= 0) return TLR_OK;
   switch (S) {
-    case 4: return launch_gemm<4>(d_desc, count, max_m, max_n, d_stat, s);
-    case 5: return launch_gemm<5>(d_desc, count, max_m, max_n, d_stat, s);
-    case 6: return launch_gemm<6>(d_desc, count, max_m, max_n, d_stat, s);
+    case 4: return launch_gemm<4>(d_desc, count, max_m, max_n, d_stat, s, gctx);
+    case 5: return launch_gemm<5>(d_desc, count, max_m, max_n, d_stat, s, gctx);
+    case 6: return launch_gemm<6>(d_desc, count, max_m, max_n, d_stat, s, gctx);
     default: return -1;
   }
 }

@@ -35,7 +35,10 @@ struct OzSplit {
 };
 
 // Source description of one operand for the split: element (r, k) of the rows x depth
-// matrix is X[k * ld + r] (col = 1) or X[r * ld + k] (col = 0).
+// matrix is X[k * ld + r] (col = 1) or X[r * ld + k] (col = 0).  An operand may be made of
+// several segments along k (multi = 1), each split into its own k blocks kb0 .. of an operand
+// with nkb blocks in all; the row exponents are then the maximum over the segments (ex zeroed
+// by the caller before the split, all segments of an operand in the same oz_split call).
 struct OzSrc {
   const double* X;
   int ld;
@@ -45,14 +48,37 @@ struct OzSrc {
   uint16_t* out;  // slices destination (oz_slices_elems(rows, depth, block_rows, S) bf16 values)
   int* ex;        // rows exponents
   int block_rows; // OZ_BM for the A operand, OZ_BN for the B operand
+  int kb0 = 0;    // first k block of this segment
+  int nkb = 0;    // k blocks of the whole operand (0: this segment alone)
+  int multi = 0;  // 1: one of several segments (exponents by atomic maximum)
 };
 
+// What the epilogue does with op(A) op(B): mode 0 writes C = beta C + alpha op(A) op(B); mode 1
+// (the likelihood gradient, tile (ta, tb) of Sigma^{-1} = op(A) op(B)) adds
+//   sum over its entries (a, b) [strictly below the diagonal when diag] of
+//   (alpha_a alpha_b - Z_ab) dC/dtheta_p(|s_a - s_b|),  p = beta, nu,
+// with the derivatives regenerated from the Matern table, into part[2 (part_off + tile)].
 struct OzGemm {
   OzSplit a, b;
   double* C;
   int ldc, m, n;
   double alpha, beta;
   int lower;  // only entries with row >= column are written
+  int mode = 0;
+  int diag = 0;
+  int64_t p0a = 0, p0b = 0;  // first sorted point of the row / column tile (mode 1)
+  int64_t part_off = 0;      // first partial slot of this item (mode 1)
+};
+
+// Shared inputs of the gradient epilogue (mode 1).
+struct OzGradCtx {
+  const double* x;      // sorted coordinates
+  const double* y;
+  const double* alpha;  // Sigma^{-1} z in sorted order
+  const double* tab;    // Matern table
+  MaternParams mp;
+  int64_t n;            // points
+  double* part;         // partial sums, 2 per CTA tile
 };
 
 size_t oz_slices_elems(int rows, int depth, int block_rows, int S);
@@ -71,4 +97,5 @@ size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S);
 // split `count` operands (descriptors on the device); max_rows / max_depth bound the grid
 int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s);
 // batched GEMMs (descriptors on the device); tiles of the largest m x n; status words for time-outs
-int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s);
+int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s,
+            const OzGradCtx* gctx = nullptr);
