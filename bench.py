@@ -37,6 +37,24 @@ UNIT = "evals/s"
 THETA = (1.0, 0.3, 1.0)
 # float64 peak of the GB300 derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# double-float ceiling of the float32 pipe: 152 SMs x 128 lanes x 2.07 GHz, about 12 float32 instructions per
+# float64-accurate multiply-add (2 flops)
+FF32_CEIL_TFLOPS = 152 * 128 * 2.07e9 / 12 * 2 / 1e12
+BF16_FALLBACK_TFLOPS = 1700.0  # sustained dense bf16 of an earlier GB300 measurement (no measured file)
+
+
+def bf16_peak():
+    """Sustained dense bf16 TFLOP/s from MEASURED_PEAKS.json (driver-written), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("bf16_tflops_sustained", "bf16_tflops"):
+            if isinstance(d.get(key), (int, float)):
+                return float(d[key]), f"measured ({key}, MEASURED_PEAKS.json)"
+    except (OSError, ValueError):
+        pass
+    return BF16_FALLBACK_TFLOPS, "fallback (1.7 PFLOP/s sustained, earlier GB300 measurement)"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22400.json")
 KERNEL_SOURCES = ["tileops.cu", "recompress.cuh", "tile.cuh"]
 
@@ -192,7 +210,10 @@ def main_config(a, n, m_new, parallelism):
 
 PRECISION = {"storage": "f64", "potrf_trsv_logdet_quadform_gradient_sums": "f64",
              "tile_gemm_householder_qr": "float32 pairs (double-float: ~48-bit significand, float32 exponent "
-                                         "range)"}
+                                         "range)",
+             "inverse_depth_ge_256_contractions": "bf16 tensor cores (tcgen05) on 6 digit slices per float64 "
+                                                  "operand, exact float32 accumulation of the leading slice "
+                                                  "groups: ~1e-12 of the operands' scale"}
 
 
 def run_reference(a):
@@ -579,6 +600,7 @@ def main():
     clk = clocks.stop()
     launches = T.launch_count() - l0
     prof = T.profile_read()
+    prof_tc = T.profile_read_tc()
     T.profile(False)
     ms = e0.elapsed_time(e1) / a.steps
     h.check()
@@ -631,7 +653,16 @@ def main():
             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
             "kernel": "k_upd_lr_gen", "launches": prof["launches"], "kernel_ms_per_step": prof["ms"] / a.steps,
             "peak_source": "float64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured "
-                           "1.19 TFLOP/s)"}
+                           "1.19 TFLOP/s)",
+            "frac_of_ff32_ceiling": (achieved / FF32_CEIL_TFLOPS) if achieved else None,
+            "ff32_ceiling": FF32_CEIL_TFLOPS}
+    # the tensor-core GEMM of the inverse (bf16 slice products): MMA flops / its device time
+    bpk, bsrc = bf16_peak()
+    tc_ach = prof_tc["flops"] / (prof_tc["ms"] * 1e-3) / 1e12 if prof_tc["ms"] > 0 else None
+    roof_tc = {"bound": "tensor", "kernel": "k_oz_gemm", "achieved": tc_ach, "peak": bpk, "unit": "TFLOP/s",
+               "frac": (tc_ach / bpk) if tc_ach else None, "peak_source": bsrc, "launches": prof_tc["launches"],
+               "kernel_ms_per_step": prof_tc["ms"] / a.steps, "mma_flops_per_step": prof_tc["flops"] / a.steps,
+               "traffic": None}
 
     accuracy = None
     if dense is not None:
@@ -650,11 +681,11 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+ff32", "precision": PRECISION,
+            "dtype": "f64+ff32+bf16x6", "precision": PRECISION,
             "data": "synthetic (jittered grid; z = L e drawn from the exact model by the dense path)"
                     if dense is not None else "synthetic (jittered grid; z drawn from the TLR model)",
             "config": main_config(a, n, len(xn_h), "replicas" if world > 1 else "single"),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "dense_fp64_gpu": dense, "accuracy": accuracy, "deterministic_across_steps": deterministic,
             "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes)},
             "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,

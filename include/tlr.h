@@ -273,6 +273,11 @@ int tlr_profile(int enable);
  * Synchronises the device. */
 int tlr_profile_read(int64_t* launches, double* ms, double* flops);
 
+/* The same for the tensor-core GEMM (k_oz_gemm, every launch while profiling
+ * is enabled): launches, summed device time (ms) and the bf16 tensor-core
+ * flops issued (2 M N K of every slice-pair MMA).  Synchronises the device. */
+int tlr_profile_read_tc(int64_t* launches, double* ms, double* flops);
+
 #ifdef __cplusplus
 }
 #endif

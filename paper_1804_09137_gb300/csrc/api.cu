@@ -44,6 +44,22 @@ void tlr_prof_end(cudaStream_t s) {
 }
 
 namespace {
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_ev_tc;  // tensor-core GEMM launches
+}  // namespace
+
+void tlr_prof_tc_begin(cudaStream_t s) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, s);
+  g_ev_tc.push_back({a, b});
+}
+
+void tlr_prof_tc_end(cudaStream_t s) {
+  if (!g_ev_tc.empty()) cudaEventRecord(g_ev_tc.back().second, s);
+}
+
+namespace {
 struct PhaseRec {
   const char* name;
   cudaEvent_t a, b;
@@ -613,16 +629,33 @@ int tlr_launch_count(int64_t* count) {
 
 int tlr_profile(int enable) {
   if (!g_tlr_prof.d_flops) {
-    if (cudaMalloc((void**)&g_tlr_prof.d_flops, sizeof(double)) != cudaSuccess) return TLR_ERR_OOM;
+    if (cudaMalloc((void**)&g_tlr_prof.d_flops, 2 * sizeof(double)) != cudaSuccess) return TLR_ERR_OOM;
   }
   TLR_CUDA_TRY(cudaDeviceSynchronize());
-  TLR_CUDA_TRY(cudaMemset(g_tlr_prof.d_flops, 0, sizeof(double)));
+  TLR_CUDA_TRY(cudaMemset(g_tlr_prof.d_flops, 0, 2 * sizeof(double)));
   for (auto& e : g_ev) g_ev_free.push_back(e);
   g_ev.clear();
+  for (auto& e : g_ev_tc) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+  g_ev_tc.clear();
   for (auto& r : g_ph) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   g_ph.clear();
   g_ph_open.clear();
   g_tlr_prof.enabled = enable ? 1 : 0;
+  return TLR_OK;
+}
+
+int tlr_profile_read_tc(int64_t* launches, double* ms, double* flops) {
+  TLR_CUDA_TRY(cudaDeviceSynchronize());
+  double tot = 0.0;
+  for (auto& e : g_ev_tc) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) tot += t;
+  }
+  double fl[2] = {0.0, 0.0};
+  if (g_tlr_prof.d_flops) TLR_CUDA_TRY(cudaMemcpy(fl, g_tlr_prof.d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
+  if (launches) *launches = (int64_t)g_ev_tc.size();
+  if (ms) *ms = tot;
+  if (flops) *flops = fl[1];
   return TLR_OK;
 }
 

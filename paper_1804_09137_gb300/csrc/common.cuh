@@ -283,6 +283,9 @@ struct TlrProfile {
 extern thread_local TlrProfile g_tlr_prof;  // per host thread
 void tlr_prof_begin(cudaStream_t s);
 void tlr_prof_end(cudaStream_t s);
+// the same for the tensor-core GEMM (its MMA flops accumulate in d_flops[1])
+void tlr_prof_tc_begin(cudaStream_t s);
+void tlr_prof_tc_end(cudaStream_t s);
 // per-phase device time (events around each phase when profiling is enabled)
 void tlr_phase_begin(const char* name, cudaStream_t s);
 void tlr_phase_end(cudaStream_t s);

@@ -242,7 +242,8 @@ __global__ void k_oz_split(const OzSrc* __restrict__ srcs) {
 // ------------------------------------------------------------------ GEMM
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restrict__ descs, int tiles_m,
-                                                           long long* __restrict__ st, const OzGradCtx gx) {
+                                                           long long* __restrict__ st, const OzGradCtx gx,
+                                                           double* __restrict__ mma_flops) {
   using Sh = OzShape<S>;
   extern __shared__ __align__(1024) uint8_t smem[];
   const OzGemm g = descs[blockIdx.y];
@@ -359,6 +360,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restr
         tc_commit(&acc_full[buf]);  // the chunk's accumulators are complete
       }
       tc_commit(done);  // every product issued has completed
+      if (mma_flops && nkb > 0)  // tensor-core work of this tile: S (S + 1) / 2 slice pairs
+        atomicAdd(mma_flops, 2.0 * OZ_BM * OZ_BN * OZ_BK * (double)nkb * (S * (S + 1) / 2));
     }
   } else {
     // ---------------- epilogue: warps 2..5, TMEM lane quarter warp % 4
@@ -488,10 +491,13 @@ int launch_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, long long
     attr_set[dev] = true;
   }
   const int tm = (max_m + OZ_BM - 1) / OZ_BM, tn = (max_n + OZ_BN - 1) / OZ_BN;
+  double* fl = g_tlr_prof.enabled ? g_tlr_prof.d_flops + 1 : nullptr;
   for (int c0 = 0; c0 < count; c0 += 65535) {
     const int cnt = std::min(65535, count - c0);
-    k_oz_gemm<S><<<dim3(tm * tn, cnt), OZ_THREADS, OzShape<S>::SMEM, s>>>(d_desc + c0, tm, d_stat, gx);
+    if (fl) tlr_prof_tc_begin(s);
+    k_oz_gemm<S><<<dim3(tm * tn, cnt), OZ_THREADS, OzShape<S>::SMEM, s>>>(d_desc + c0, tm, d_stat, gx, fl);
     TLR_LAUNCH_CHECK();
+    if (fl) tlr_prof_tc_end(s);
   }
   return TLR_OK;
 }

@@ -44,7 +44,7 @@ EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
            "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
            "tlr_loglik_grad_batched", "tlr_predict_var",
-           "tlr_profile_read", "tlr_gemm_tc"]
+           "tlr_profile_read", "tlr_gemm_tc", "tlr_profile_read_tc"]
 
 
 def lib():
@@ -81,6 +81,7 @@ def lib():
     L.tlr_loglik_dense_noalloc.argtypes = [i64, vp, vp, vp, TlrTheta, vp, vp]
     L.tlr_profile_phases.argtypes = [C.c_char_p, i64]
     L.tlr_profile_read.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
+    L.tlr_profile_read_tc.argtypes = [C.POINTER(i64), C.POINTER(d), C.POINTER(d)]
     ci = C.c_int
     L.tlr_gemm_tc.argtypes = [ci, ci, ci, vp, ci, ci, vp, ci, ci, vp, ci, d, d, ci, vp]
     for name in EXPORTS:
@@ -258,6 +259,13 @@ def profile(enable: bool):
 def profile_read():
     n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
     _check("tlr_profile_read", lib().tlr_profile_read(C.byref(n), C.byref(ms), C.byref(fl)))
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value}
+
+
+def profile_read_tc():
+    """Tensor-core GEMM launches, their device time (ms) and bf16 MMA flops since profile(True)."""
+    n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
+    _check("tlr_profile_read_tc", lib().tlr_profile_read_tc(C.byref(n), C.byref(ms), C.byref(fl)))
     return {"launches": n.value, "ms": ms.value, "flops": fl.value}
 
 
