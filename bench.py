@@ -82,7 +82,7 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
-    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy", "accuracy36k"],
+    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy", "accuracy36k", "config4"],
                    help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent "
                         "regions; n40k: TLR vs dense likelihood at n = 40,000 and kriging of 10% held out")
     p.add_argument("--regions", type=int, default=512)
@@ -472,6 +472,68 @@ def run_accuracy36k(a):
                       "values": res}), flush=True)
 
 
+def run_config4(a):
+    """The mixed-precision configuration: 500 x 500 jittered grid (n = 250,000), theta = (1, 0.1, 0.5),
+    nb = 2000, eps = 1e-7, l only.  z = L e from a tighter TLR factor (eps = 1e-9, double-float), whose l
+    is the reference (the dense path would need 250 GB and the CPU TLR reference is out of reach at this
+    size).  One evaluation each with precision 5 (tensor-core contractions of depth >= 256 in the
+    Cholesky, 5 bf16 slices) and precision 1 (double-float on the CUDA cores)."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_1804_09137_gb300 import inputs
+    from paper_1804_09137_gb300 import tlr as T
+
+    theta = (1.0, 0.1, 0.5)
+    side, nb, cap = 500, 2000, 256
+    dev = torch.device("cuda")
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(side)
+    xo, yo = t64(x), t64(y)
+    res = {}
+    h = T.Handle(xo, yo, nb=nb, eps=1e-9, rank_cap=cap, precision=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.factor(theta)
+    torch.cuda.synchronize()
+    z = h.sample(t64(inputs.standard_normal(len(x))))
+    ref = h.loglik(z).cpu().numpy()
+    h.check()
+    res["ref_eps1e-9"] = {"loglik": float(ref[0]), "factor_s": time.perf_counter() - t0, "ranks": h.rank_stats()}
+    h.close()
+    del h
+    torch.cuda.empty_cache()
+    log("reference", res["ref_eps1e-9"])
+    for prec in (5, 1):
+        h = T.Handle(xo, yo, nb=nb, eps=a.eps, rank_cap=cap, precision=prec)
+        for rep in range(2):  # the second evaluation is timed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.factor(theta)
+            out = h.loglik(z)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        h.check()
+        o = out.cpu().numpy()
+        res[f"precision{prec}"] = {"loglik": float(o[0]), "seconds": secs,
+                                   "rel_err_vs_ref": abs(float(o[0]) - float(ref[0])) / abs(float(ref[0])),
+                                   "ranks": h.rank_stats(), "tiles": h.tile_counts()}
+        log(prec, res[f"precision{prec}"])
+        h.close()
+        del h
+        torch.cuda.empty_cache()
+    line = {"metric": "loglik evals/s at n=250k (500^2 grid), nb=2000, eps=1e-7, mixed precision",
+            "value": 1.0 / res["precision5"]["seconds"], "unit": "evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": res["precision5"]["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+ff32+bf16x5", "data": "synthetic (z from the eps = 1e-9 TLR factor)",
+            "config": {"workload": "matern_tlr_n250000_nb2000_eps1e-7_theta1-0.1-0.5", "n": len(x), "nb": nb,
+                       "eps": a.eps, "rank_cap": cap},
+            "double_float_seconds": res["precision1"]["seconds"], "result": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_()
     if a.workload == "accuracy" and a.impl != "reference":
@@ -480,6 +542,8 @@ def main():
         return run_n40k(a)
     if a.workload == "accuracy36k" and a.impl != "reference":
         return run_accuracy36k(a)
+    if a.workload == "config4" and a.impl != "reference":
+        return run_config4(a)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "regions":

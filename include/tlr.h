@@ -71,9 +71,12 @@ typedef struct {
  * with the diagonal inverses, the stacked-panel products of Sigma^{-1}): 0 =
  * default, bf16 tensor cores (tcgen05) on 6 digit slices of every float64
  * operand, about 1e-12 of the operands' scale (see tlr_gemm_tc); 1 = double-float
- * on the CUDA cores (about 2^-44), no tensor cores; 4, 5, 6 = tensor cores with
- * that many slices (4: about 1e-9).  The Cholesky factorization and dense mode
- * (eps < 0) always use double-float. */
+ * on the CUDA cores (about 2^-44), no tensor cores; 4, 5, 6 = mixed precision:
+ * tensor cores with that many slices (4: about 1e-9) in the gradient's inverse
+ * and also in the Cholesky factorization's contractions of depth >= 256 (the
+ * triangular transforms with L_kk^{-1} and the dense-target updates).  With
+ * precision 0 and 1 the Cholesky uses double-float; dense mode (eps < 0) always
+ * does. */
 typedef struct {
   int nb;
   double eps;

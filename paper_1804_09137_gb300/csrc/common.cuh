@@ -297,16 +297,21 @@ struct PhaseScope {
 
 // ------------------------------------------------------------ host helpers
 double tlr_host_digamma(double x);  // psi(x), x > 0 (host)
-// digit slices of the tensor-core contractions for the handle's precision option (0: none).  Only the
-// gradient's inverse uses them: the Cholesky's products with the explicit diagonal-tile inverses
-// amplify the rounding of their operands' scale (with tensor-core products the l error at eps = 1e-9
-// exceeded 1e-8 relative), and dense mode, the exact full-tile comparator, stays in double-float.
+// digit slices of the tensor-core contractions for the handle's precision option (0: none).  By
+// default (precision 0) only the gradient's inverse uses them: the Cholesky's products with the
+// explicit diagonal-tile inverses amplify the rounding of their operands' scale (with tensor-core
+// products the l error at eps = 1e-9 exceeded 1e-8 relative).  precision 4..6 (the mixed-precision
+// mode) also runs the Cholesky's contractions of depth >= 256 on the tensor cores.  Dense mode, the
+// exact full-tile comparator, stays in double-float.
 static inline int tlr_tc_slices_opt(const tlr_ctx* h) {  // the option alone (workspace sizing)
   const int p = h->opts.precision;
   if (h->dense) return 0;
   return p == 0 ? 6 : (p == 1 ? 0 : p);
 }
-static inline int tlr_tc_slices(const tlr_ctx* h) { return h->in_inverse ? tlr_tc_slices_opt(h) : 0; }
+static inline int tlr_tc_slices(const tlr_ctx* h) {
+  if (h->in_inverse) return tlr_tc_slices_opt(h);
+  return (!h->dense && h->opts.precision >= 4) ? h->opts.precision : 0;
+}
 int tlr_build_table(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_diag(tlr_ctx* h, cudaStream_t s);
 int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t s);

@@ -133,9 +133,7 @@ int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s) {
   const int chunk = chunk_for(h, ie);
   if (chunk < 1) return TLR_ERR_OOM;
   const size_t smem = 2 * (size_t)nb * sizeof(double) + (size_t)nb * sizeof(int);
-  if (smem > 48 * 1024)
-    if (cudaFuncSetAttribute(k_aca_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return TLR_ERR_CUDA;
+  if (tlr_smem_optin((const void*)k_aca_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
   int aca_max = h->dense_rank + 8;
   if (aca_max > Kmax) aca_max = Kmax;
   const TlrView v = view_of(h);

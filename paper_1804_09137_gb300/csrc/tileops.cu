@@ -345,9 +345,7 @@ int resident_ctas(int nb) {
   const int c = cached[dev].load();
   if (c > 0 && cached_nb[dev].load() == nb) return c;
   int per_sm = 0, sms = 0;
-  if (upd_smem(nb) > 48 * 1024 &&
-      cudaFuncSetAttribute(k_upd_lr_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem(nb)) != cudaSuccess)
-    return 0;
+  if (tlr_smem_optin((const void*)k_upd_lr_gen, upd_smem(nb)) != TLR_OK) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_lr_gen, TLR_THREADS, upd_smem(nb)) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
@@ -399,6 +397,14 @@ int tops_gemm_mixed(tlr_ctx* h, const GemmGen* d_desc, int count, int m, int n, 
 }
 }  // namespace
 
+int tlr_smem_optin(const void* f, size_t dyn) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return TLR_ERR_CUDA;
+  if (a.sharedSizeBytes + dyn <= 48 * 1024) return TLR_OK;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess ? TLR_OK
+                                                                                                        : TLR_ERR_CUDA;
+}
+
 int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
                 int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve) {
   if (n_dn > 0) {
@@ -449,8 +455,10 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
 }
 
 size_t tops_dd_item_elems(const tlr_ctx* h) {
+  // the item's product, recompression buffers and descriptors, its tensor-core slices (if any) and alignment
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
-  return (size_t)h->nb * h->nb + tlr_item_elems(h->nb, h->kcap) + 2 * gd;
+  return (size_t)h->nb * h->nb + tlr_item_elems(h->nb, h->kcap) + 2 * gd + tc_item_doubles(h, h->nb, h->nb, h->nb) +
+         32;
 }
 
 int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
@@ -461,13 +469,11 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   const size_t ie = tlr_item_elems(h->nb, h->kcap);
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
   const size_t tcd = tc_item_doubles(h, h->nb, h->nb, h->nb);
-  const size_t per = tops_dd_item_elems(h) + tcd;
+  const size_t per = tops_dd_item_elems(h);
   const int chunk = ws_elems > 64 ? (int)std::min<size_t>((ws_elems - 64) / per, 65535) : 0;
   if (chunk < 1) return TLR_ERR_OOM;
   const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
-  if (smem > 48 * 1024)
-    if (cudaFuncSetAttribute(k_dd_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return TLR_ERR_CUDA;
+  if (tlr_smem_optin((const void*)k_dd_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
   for (int64_t q0 = 0; q0 < n_dd; q0 += chunk) {
     const int cnt = (int)(n_dd - q0 < chunk ? n_dd - q0 : chunk);
     GemmGen* d1 = (GemmGen*)ws_base;

@@ -37,6 +37,9 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
                size_t m_stride = 0, int m_by = 0);
 // X = T^{-1} for a lower triangular nb x nb tile (X fully written)
 int tops_trinv(const double* T, int nb, double* X, cudaStream_t s);
+// Allows kernel f to start with dyn bytes of dynamic shared memory: above the default 48 KB per block
+// (static plus dynamic) the kernel must opt in.  TLR_OK or TLR_ERR_CUDA.
+int tlr_smem_optin(const void* f, size_t dyn);
 // batched general GEMM from a device descriptor array
 // (descriptors with k >= k_skip are left out: another path computes them)
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30);

@@ -84,13 +84,13 @@ def _golden(name):
         return json.load(fh)[name]
 
 
-def _run(T, g, eps, rank_cap, dense_rank):
+def _run(T, g, eps, rank_cap, dense_rank, precision=0):
     x, y = inputs.jittered_grid(g["side"], n=g["subset"])
     x, y = x * g["scale"], y * g["scale"]
     theta = tuple(g["theta"])
     z = DN.sample(x, y, theta, inputs.standard_normal(len(x)))
     nb = g["nb"]
-    h = T.Handle(dev(x), dev(y), nb=nb, eps=eps, rank_cap=rank_cap, dense_rank=dense_rank)
+    h = T.Handle(dev(x), dev(y), nb=nb, eps=eps, rank_cap=rank_cap, dense_rank=dense_rank, precision=precision)
     assert h.nt >= 5 and len(x) % nb != 0  # several tiles, the last one ragged
     h.factor(theta)
     zt = dev(z)
@@ -127,6 +127,20 @@ def test_working_eps_loglik_and_gradient_match_oracle(T, name, rank_cap, dense_r
     assert err9 <= max(0.1 * err7, 1e-8 * np.linalg.norm(gref)), (err9, err7)
     tol9 = max(1e-8 * abs(g["loglik"]), abs(g["tlr_ref"]["1e-09"][0] - g["loglik"]))
     assert abs(ll9 - g["loglik"]) <= tol9, (ll9, g["loglik"], tol9)
+
+
+@pytest.mark.parametrize("precision", [5, 1])
+def test_other_precisions_stay_within_the_working_eps_budget(T, precision):
+    """precision 5 (mixed: 5 bf16 slices, tensor cores also in the Cholesky) and 1 (double-float only) at
+    eps = 1e-7 on the nb = 900 case: l within the same budget as the default, the gradient's MLE shift
+    within 1 % of theta."""
+    g = _golden("nb900")
+    gref = np.array(g["grad"])
+    out, ll, grad, _ = _run(T, g, 1e-7, 256, 0, precision)
+    tol = max(1e-6 * abs(g["loglik"]), abs(g["tlr_ref"]["1e-07"][0] - g["loglik"]))
+    assert abs(ll - g["loglik"]) <= tol, (ll, g["loglik"], tol)
+    shift = -np.linalg.solve(np.array(g["hessian"]), grad - gref)
+    assert np.all(np.abs(shift) <= 0.01 * np.abs(np.array(g["theta"]))), (grad, gref, shift)
 
 
 def test_sigma2_derivative_matches_finite_differences_of_gpu_loglik(T):
