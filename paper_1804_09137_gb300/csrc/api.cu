@@ -86,6 +86,10 @@ void tlr_phase_end(cudaStream_t s) {
 
 // digamma by upward recurrence to x >= 10 and the asymptotic series
 // psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
+void tlr_note_oom(const char* file, int line) {
+  if (getenv("TLR_VERBOSE")) fprintf(stderr, "tlr: out of memory at %s:%d\n", file, line);
+}
+
 double tlr_host_digamma(double x) {
   double r = 0.0;
   while (x < 10.0) { r -= 1.0 / x; x += 1.0; }
@@ -150,7 +154,7 @@ int dmalloc(T** p, size_t count) {
   if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return TLR_ERR_OOM;
+    TLR_RETURN_OOM();
   }
   return TLR_OK;
 }
@@ -158,7 +162,7 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk,
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop,
                   h->gpart};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -275,7 +279,7 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->scratch, ws);
   if (rc != TLR_OK) {
     free_ctx(h);
-    return TLR_ERR_OOM;
+    TLR_RETURN_OOM();
   }
   *out = h;
   return TLR_OK;
@@ -629,7 +633,7 @@ int tlr_launch_count(int64_t* count) {
 
 int tlr_profile(int enable) {
   if (!g_tlr_prof.d_flops) {
-    if (cudaMalloc((void**)&g_tlr_prof.d_flops, 2 * sizeof(double)) != cudaSuccess) return TLR_ERR_OOM;
+    if (cudaMalloc((void**)&g_tlr_prof.d_flops, 2 * sizeof(double)) != cudaSuccess) TLR_RETURN_OOM();
   }
   TLR_CUDA_TRY(cudaDeviceSynchronize());
   TLR_CUDA_TRY(cudaMemset(g_tlr_prof.d_flops, 0, 2 * sizeof(double)));
@@ -702,7 +706,7 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
   }
   free(h->kind);
   h->kind = (char*)calloc(std::max<int64_t>(T, 1), 1);
-  if (!h->kind) return TLR_ERR_OOM;
+  if (!h->kind) TLR_RETURN_OOM();
   for (int64_t t = 0; t < T; ++t) h->kind[t] = h->dense || rk[t] < 0 || rk[t] > h->dense_rank;
   for (int k = 0; k < nt; ++k)  // symbolic right-looking fill closure
     for (int j = k + 1; j < nt; ++j)
@@ -721,7 +725,7 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
     if (cudaMalloc((void**)&h->dpool, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       h->dpool = nullptr;
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->dcap = want;
   }
@@ -749,6 +753,10 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
           auto r = [&](int p, int q) { return h->kind[tile_index(p, q)] ? h->nb : rk[tile_index(p, q)]; };
           auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(t.y, k)); return K * K; };
           std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
+          // items with a dense operand first: their products are formed by a batched GEMM before the launch
+          std::stable_partition(L.begin() + b, L.end(), [&](int2 t) {
+            return h->kind[tile_index(t.x, k)] || h->kind[tile_index(t.y, k)];
+          });
         }
       }
     }
@@ -765,7 +773,7 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
     if (cudaMalloc((void**)&h->d_list, len * sizeof(int2)) != cudaSuccess) {
       cudaGetLastError();
       h->list_cap = 0;
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->list_cap = len;
   }
@@ -773,7 +781,7 @@ int tlr_plan(tlr_ctx* h, cudaStream_t s) {
   free(h->plan_off);
   h->h_list = (int2*)malloc(len * sizeof(int2));
   h->plan_off = (int64_t*)malloc(off.size() * sizeof(int64_t));
-  if (!h->h_list || !h->plan_off) return TLR_ERR_OOM;
+  if (!h->h_list || !h->plan_off) TLR_RETURN_OOM();
   if (!L.empty()) memcpy(h->h_list, L.data(), L.size() * sizeof(int2));
   memcpy(h->plan_off, off.data(), off.size() * sizeof(int64_t));
   if (!L.empty())

@@ -126,6 +126,10 @@ struct tlr_ctx {
   int* hslotz;        // host copy of the inverse's dense slots
   double* gpart;      // partial sums of the gradient reduced inside LAUUM
   size_t gpart_elems;
+  // products of the low-rank updates with a dense operand, formed by a batched GEMM before the
+  // persistent update kernel (nb x kcap per item, with descriptors and tensor-core workspace)
+  double* dop;
+  size_t dop_elems;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -297,6 +301,13 @@ struct PhaseScope {
 
 // ------------------------------------------------------------ host helpers
 double tlr_host_digamma(double x);  // psi(x), x > 0 (host)
+// records where a call ran out of memory (printed to stderr when TLR_VERBOSE is set)
+void tlr_note_oom(const char* file, int line);
+#define TLR_RETURN_OOM()               \
+  do {                                 \
+    tlr_note_oom(__FILE__, __LINE__);  \
+    return TLR_ERR_OOM;                \
+  } while (0)
 // digit slices of the tensor-core contractions for the handle's precision option (0: none).  By
 // default (precision 0) only the gradient's inverse uses them: the Cholesky's products with the
 // explicit diagonal-tile inverses amplify the rounding of their operands' scale (with tensor-core

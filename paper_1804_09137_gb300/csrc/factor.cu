@@ -131,7 +131,7 @@ int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s) {
   const int nb = h->nb, kcap = h->kcap, Kmax = 2 * kcap;
   const size_t ie = tlr_item_elems(nb, kcap);
   const int chunk = chunk_for(h, ie);
-  if (chunk < 1) return TLR_ERR_OOM;
+  if (chunk < 1) TLR_RETURN_OOM();
   const size_t smem = 2 * (size_t)nb * sizeof(double) + (size_t)nb * sizeof(int);
   if (tlr_smem_optin((const void*)k_aca_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
   int aca_max = h->dense_rank + 8;
@@ -177,7 +177,7 @@ static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {
   const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
   const size_t desc_elems = (sizeof(GemmDesc) * (size_t)items + 7) / 8 + 1;
   const int chunk = chunk_for(h, per, desc_elems);
-  if (chunk < 1) return TLR_ERR_OOM;
+  if (chunk < 1) TLR_RETURN_OOM();
   GemmDesc* desc = (GemmDesc*)h->scratch;
   double* ws = h->scratch + desc_elems;
   const int mb = (h->nb + 63) / 64;
@@ -193,8 +193,15 @@ static int launch_syrk(tlr_ctx* h, int k, cudaStream_t s) {
 
 static int launch_updates(tlr_ctx* h, int k, cudaStream_t s) {
   const int64_t* off = h->plan_off + (size_t)k * PLAN_PH;
-  return tops_update(h, view_of(h), ALG_CHOL, k, h->d_list + off[PH_UPD_LR], off[PH_UPD_LR + 1] - off[PH_UPD_LR],
-                     h->d_list + off[PH_UPD_D], off[PH_UPD_D + 1] - off[PH_UPD_D], h->opts.eps, nullptr, 0.0, s);
+  const int64_t n_lr = off[PH_UPD_LR + 1] - off[PH_UPD_LR];
+  // leading items with a dense operand (partitioned first by the plan)
+  int64_t ndop = 0;
+  if (h->kind) {
+    const int2* hl = h->h_list + off[PH_UPD_LR];
+    while (ndop < n_lr && (h->kind[tile_index(hl[ndop].x, k)] || h->kind[tile_index(hl[ndop].y, k)])) ++ndop;
+  }
+  return tops_update(h, view_of(h), ALG_CHOL, k, h->d_list + off[PH_UPD_LR], n_lr, ndop, h->d_list + off[PH_UPD_D],
+                     off[PH_UPD_D + 1] - off[PH_UPD_D], h->opts.eps, nullptr, 0.0, s);
 }
 
 int tlr_factor(tlr_ctx* h, cudaStream_t s) {

@@ -157,7 +157,7 @@ int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s
   const int64_t pairs = (int64_t)h->nt * (h->nt + 1) / 2;
   const int64_t cnt = pairs * mb * mb;
   const int nstage = 256;
-  if ((size_t)(3 * cnt + 3 * nstage) > h->scratch_elems) return TLR_ERR_OOM;
+  if ((size_t)(3 * cnt + 3 * nstage) > h->scratch_elems) TLR_RETURN_OOM();
   double* part = h->scratch;
   double* stage = h->scratch + 3 * cnt;
   if (pairs > 65535) return TLR_ERR_STATE;  // nt up to 361

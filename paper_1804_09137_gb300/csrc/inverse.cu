@@ -105,7 +105,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   const int64_t T = h->ntiles;
   free(h->kindz);
   h->kindz = (char*)calloc(std::max<int64_t>(T, 1), 1);
-  if (!h->kindz) return TLR_ERR_OOM;
+  if (!h->kindz) TLR_RETURN_OOM();
   char* K = h->kindz;
   // Z keeps the factor's dense tiles; a low-rank factor tile whose rank exceeds
   // 2/5 of dense_rank is also made dense in Z (inverse ranks run about 3.5 times
@@ -133,7 +133,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     if (K[t]) { slot[t] = compact ? nd : (int)t; ++nd; }
   free(h->hslotz);
   h->hslotz = (int*)malloc(std::max<int64_t>(T, 1) * sizeof(int));
-  if (!h->hslotz) return TLR_ERR_OOM;
+  if (!h->hslotz) TLR_RETURN_OOM();
   memcpy(h->hslotz, slot.data(), std::max<int64_t>(T, 1) * sizeof(int));
   const int64_t pool_want = compact ? std::max(nd, 1) : std::max<int64_t>(T, 1);
   if (pool_want > h->dcapz) {
@@ -143,7 +143,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     const int want = (int)pool_want;
     if (cudaMalloc((void**)&h->dpoolz, (size_t)want * h->nb * h->nb * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->dcapz = want;
   }
@@ -166,6 +166,8 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
         auto r = [&](int p, int q) { return kd(p, q) ? h->nb : std::max(rk[tile_index(p, q)], 1); };
         auto est = [&](int2 t) { const int K = r(t.x, t.y) + std::min(r(t.x, k), r(k, t.y)); return K * K; };
         std::stable_sort(L.begin() + b, L.end(), [&](int2 a, int2 c) { return est(a) > est(c); });
+        // items with a dense operand first: their products are formed by a batched GEMM before the launch
+        std::stable_partition(L.begin() + b, L.end(), [&](int2 t) { return kd(t.x, k) || kd(k, t.y); });
       }
     }
   }
@@ -198,7 +200,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     if (cudaMalloc((void**)&h->d_zlist, len * sizeof(int2)) != cudaSuccess) {
       cudaGetLastError();
       h->zlist_cap = 0;
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->zlist_cap = len;
   }
@@ -206,7 +208,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
   free(h->zoff);
   h->h_zlist = (int2*)malloc(len * sizeof(int2));
   h->zoff = (int64_t*)malloc(off.size() * sizeof(int64_t));
-  if (!h->h_zlist || !h->zoff) return TLR_ERR_OOM;
+  if (!h->h_zlist || !h->zoff) TLR_RETURN_OOM();
   if (!L.empty()) memcpy(h->h_zlist, L.data(), L.size() * sizeof(int2));
   memcpy(h->zoff, off.data(), off.size() * sizeof(int64_t));
   if (!L.empty())
@@ -228,7 +230,7 @@ static int ensure_z(tlr_ctx* h) {
   ok = ok && cudaMalloc((void**)&h->dslotz, T * sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
-    return TLR_ERR_OOM;
+    TLR_RETURN_OOM();
   }
   return TLR_OK;
 }
@@ -300,7 +302,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
     h->msave_elems = 0;
     if (cudaMalloc((void**)&h->msave, msave_want * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->msave_elems = msave_want;
   }
@@ -322,7 +324,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
     cs.push_back({h->Dz, h->msave, (int64_t)nt * (int64_t)nn});
     for (int64_t t = 0; t < T; ++t)
       if (K[t]) cs.push_back({h->dpoolz + (size_t)t * nn, h->msave + (size_t)(nt + dix[t]) * nn, (int64_t)nn});
-    if (cs.size() * cd > h->scratch_elems) return TLR_ERR_OOM;
+    if (cs.size() * cd > h->scratch_elems) TLR_RETURN_OOM();
     TLR_CUDA_TRY(cudaMemcpyAsync(h->scratch, cs.data(), cs.size() * sizeof(CopySeg), cudaMemcpyHostToDevice, s));
     ZTRY(seg_copy((const CopySeg*)h->scratch, (int64_t)cs.size(), s));
   }
@@ -376,7 +378,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       h->gpart_elems = 0;
       if (cudaMalloc((void**)&h->gpart, want * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
-        return TLR_ERR_OOM;
+        TLR_RETURN_OOM();
       }
       h->gpart_elems = want;
     }
@@ -399,7 +401,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       const size_t want = worst + worst / 4;
       if (cudaMalloc((void**)&h->scratch, want * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
-        return TLR_ERR_OOM;
+        TLR_RETURN_OOM();
       }
       h->scratch_elems = want;
     }
@@ -419,7 +421,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       need += per;
       ++b1;
     }
-    if (need > budget) return TLR_ERR_OOM;
+    if (need > budget) TLR_RETURN_OOM();
     std::vector<GemmGen> g1, g1b, g2, gbig;
     std::vector<std::vector<GemmGen>> gdd;
     std::vector<CopySeg> cs;
@@ -454,7 +456,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
     CopySeg* dcs = (CopySeg*)(ddd + n_dd);
     double* Gw = base + ((size_t)(n_g1 + n_g1b + n_g2 + nbig + n_dd) * gd + n_cs * cd + 8);
     double* Pw = Gw + g_tot + 8;
-    if ((size_t)(Pw + p_tot - base) > budget) return TLR_ERR_OOM;
+    if ((size_t)(Pw + p_tot - base) > budget) TLR_RETURN_OOM();
     GemmGen z0;
     memset(&z0, 0, sizeof(z0));
     z0.alpha = 1.0; z0.beta = 0.0;
@@ -608,7 +610,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       sp = align(sp);
       OzGemm* dgem = reinterpret_cast<OzGemm*>(sp);
       sp += gem.size() * sizeof(OzGemm);
-      if (sp > reinterpret_cast<char*>(base + budget)) return TLR_ERR_OOM;
+      if (sp > reinterpret_cast<char*>(base + budget)) TLR_RETURN_OOM();
       for (auto& z : zero_ex) TLR_CUDA_TRY(cudaMemsetAsync(z.first, 0, z.second * sizeof(int), s));
       if (!src.empty())
         TLR_CUDA_TRY(cudaMemcpyAsync(dsrc, src.data(), src.size() * sizeof(OzSrc), cudaMemcpyHostToDevice, s));
@@ -657,7 +659,7 @@ static int ensure_aux(tlr_ctx* h, int items) {
     h->scratch_dd_elems = 0;
     if (cudaMalloc((void**)&h->scratch_dd, want * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
-      return TLR_ERR_OOM;
+      TLR_RETURN_OOM();
     }
     h->scratch_dd_elems = want;
   }
@@ -737,7 +739,14 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, i
                           h->scratch_dd_elems));
     }
     { PhaseScope ps("trtri.update", s);
-      ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s,
+      // leading items of the low-rank list with a dense operand (partitioned first by the plan)
+      int64_t ndop = 0;
+      {
+        const int2* hl = h->h_zlist + off[ZP_T2_LR];
+        const char* K = h->kindz;
+        while (ndop < N(ZP_T2_LR) && (K[tile_index(hl[ndop].x, k)] || K[tile_index(k, hl[ndop].y)])) ++ndop;
+      }
+      ZTRY(tops_update(h, z, ALG_TRTRI, k, L(ZP_T2_LR), N(ZP_T2_LR), ndop, L(ZP_T2_D), N(ZP_T2_D), eps, d_zeta, 0.5, s,
                        std::min(ndd, 32))); }
     if (ndd > 0) {
       TLR_CUDA_TRY(cudaEventRecord(h->ev_join, h->aux));

@@ -548,7 +548,7 @@ int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, l
     size_t need = 256;
     int q1 = q0;
     while (q1 < count && need + oz_item_bytes(g[q1], S) <= ws_bytes) need += oz_item_bytes(g[q1++], S);
-    if (q1 == q0) return TLR_ERR_OOM;
+    if (q1 == q0) TLR_RETURN_OOM();
     std::vector<OzSrc> src;
     std::vector<OzGemm> gem;
     char* p = base;
@@ -587,7 +587,7 @@ int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, l
     dp += align128(src.size() * sizeof(OzSrc));
     OzGemm* dgem = reinterpret_cast<OzGemm*>(dp);
     dp += align128(gem.size() * sizeof(OzGemm));
-    if (dp > base + ws_bytes) return TLR_ERR_OOM;
+    if (dp > base + ws_bytes) TLR_RETURN_OOM();
     if (!src.empty())
       TLR_CUDA_TRY(cudaMemcpyAsync(dsrc, src.data(), src.size() * sizeof(OzSrc), cudaMemcpyHostToDevice, s));
     if (!gem.empty())
@@ -648,7 +648,7 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
   const size_t per = sa + sb + xa + xb;
   const size_t per_all = per + 2 * sizeof(OzSrc) + sizeof(OzGemm);
   const int chunk = (int)std::min<size_t>(65535, ws_bytes > 512 ? (ws_bytes - 512) / per_all : 0);
-  if (chunk < 1) return TLR_ERR_OOM;
+  if (chunk < 1) TLR_RETURN_OOM();
   char* base = static_cast<char*>(ws);
   for (int q0 = 0; q0 < count; q0 += chunk) {
     const int cnt = std::min(chunk, count - q0);

@@ -49,7 +49,7 @@ __device__ __forceinline__ void operands(const TlrView& v, int alg, int a, int b
 // one item: target tile += alpha op(X) op(Y), then recompression; w is this CTA's workspace
 __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double tau, int Kmax, int trunc_cap,
                             ItemWs& w, long long* __restrict__ st, double* __restrict__ flops, double* sh,
-                            int* shi) {
+                            int* shi, const double* __restrict__ pre) {
   const int nb = v.nb;
   const int64_t tt = dtile_index(it.x, it.y);
   Opnd X, Y;
@@ -85,14 +85,16 @@ __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double ta
       for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
       r = X.k;
     }
-  } else if (X.dense) {
-    pf = 2.0 * nb * nb * Y.k;
-    cta_gemm_df(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
+  } else if (X.dense) {  // U part alpha op(X) U_y: staged by the batched GEMM (pre) or formed here
+    pf = pre ? 0.0 : 2.0 * nb * nb * Y.k;
+    if (pre) for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Un[e] = pre[e];
+    else cta_gemm_df(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Un, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * Y.k; e += blockDim.x) Vn[e] = Y.V[e];
     r = Y.k;
-  } else {
-    pf = 2.0 * nb * nb * X.k;
-    cta_gemm_df(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
+  } else {  // V part op(Y)^T V_x, likewise
+    pf = pre ? 0.0 : 2.0 * nb * nb * X.k;
+    if (pre) for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Vn[e] = pre[e];
+    else cta_gemm_df(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Vn, nb);
     for (size_t e = threadIdx.x; e < (size_t)nb * X.k; e += blockDim.x) Un[e] = alpha * X.U[e];
     r = X.k;
   }
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k
                                                        int n_items, int* __restrict__ ctr, double eps,
                                                        const double* __restrict__ d_zeta, double zpow, int Kmax,
                                                        int trunc_cap, double* __restrict__ ws, size_t item_elems,
-                                                       long long* __restrict__ st, double* __restrict__ flops) {
+                                                       long long* __restrict__ st, double* __restrict__ flops,
+                                                       const double* __restrict__ pre, int n_pre) {
   extern __shared__ dfloat vs_dyn[];  // 2 nb: staged reflectors of the recompression
   __shared__ double sh[TLR_THREADS / 32 + 2];
   __shared__ int shi[TLR_THREADS / 32 + 2];
@@ -126,9 +129,33 @@ __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k
     const int q = s_item;
     __syncthreads();  // every thread holds q before thread 0 takes the next one
     if (q >= n_items) break;
-    upd_lr_item(v, alg, k, items[q], tau, Kmax, trunc_cap, w, st, flops, sh, shi);
+    upd_lr_item(v, alg, k, items[q], tau, Kmax, trunc_cap, w, st, flops, sh, shi,
+                q < n_pre ? pre + (size_t)q * v.nb * v.kcap : nullptr);
     __syncthreads();  // the workspace is reused by the next item
   }
+}
+
+// items q < cnt with one dense operand: the product that the update kernel would form with the
+// dense tile, P_q = alpha op(X) U_y (X dense) or op(Y)^T V_x (Y dense), nb x rank into slot q of P
+// (nb x kcap each); other items get an empty descriptor
+__global__ void k_dop_desc(TlrView v, int alg, int k, const int2* __restrict__ items, int cnt, double* __restrict__ P,
+                           GemmGen* __restrict__ d) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const int2 it = items[q];
+  const int nb = v.nb;
+  Opnd X, Y;
+  double alpha;
+  operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
+  GemmGen g;
+  g.A = g.B = nullptr; g.C = P + (size_t)q * nb * v.kcap; g.m = g.n = g.k = 0;
+  g.lda = g.ldb = g.ldc = nb; g.tA = g.tB = 0; g.alpha = 1.0; g.beta = 0.0; g.lower = 0;
+  if (X.k > 0 && Y.k > 0 && X.dense != Y.dense) {
+    g.m = nb; g.k = nb; g.B = X.dense ? Y.U : X.V;
+    if (X.dense) { g.n = Y.k; g.A = X.A; g.tA = X.tA; g.alpha = alpha; }
+    else { g.n = X.k; g.A = Y.A; g.tA = !Y.tA; }
+  }
+  d[q] = g;
 }
 
 // dense target C += alpha op(X) op(Y) as three batched GEMM stages per item:
@@ -405,8 +432,43 @@ int tlr_smem_optin(const void* f, size_t dyn) {
                                                                                                         : TLR_ERR_CUDA;
 }
 
-int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
-                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve) {
+// the products of the first n_dop low-rank items with the dense operand, into h->dop (batched GEMM, on the
+// tensor cores where the handle's precision allows); false when the buffer cannot be had (the update
+// kernel then forms them itself)
+static int stage_dense_operand_products(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr,
+                                        int64_t n_dop, cudaStream_t s, bool* staged) {
+  *staged = false;
+  const size_t slot = (size_t)h->nb * h->kcap;
+  const size_t gd = (sizeof(GemmGen) + 7) / 8;
+  const size_t tcd = tc_item_doubles(h, h->nb, h->kcap, h->nb);
+  const int64_t tc_items = std::min<int64_t>(n_dop, 16);  // the tensor-core workspace is reused in chunks
+  const size_t want = (size_t)n_dop * (slot + gd) + (size_t)tc_items * tcd + 64;
+  if (want > h->dop_elems) {
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h->dop) cudaFree(h->dop);
+    h->dop = nullptr;
+    h->dop_elems = 0;
+    if (cudaMalloc((void**)&h->dop, (want + want / 4) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return TLR_OK;
+    }
+    h->dop_elems = want + want / 4;
+  }
+  GemmGen* d = (GemmGen*)(h->dop + (size_t)n_dop * slot);
+  double* tc = h->dop + (size_t)n_dop * (slot + gd) + 16;
+  tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
+  const size_t tc_avail = tcd ? (size_t)(h->dop + h->dop_elems - tc) : 0;
+  k_dop_desc<<<(unsigned)((n_dop + 127) / 128), 128, 0, s>>>(v, alg, k, d_lr, (int)n_dop, h->dop, d);
+  TLR_LAUNCH_CHECK();
+  int rc = tops_gemm_mixed(h, d, (int)n_dop, h->nb, h->kcap, h->nb, tc, tc_avail, s);
+  if (rc) return rc;
+  *staged = true;
+  return TLR_OK;
+}
+
+int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, int64_t n_dop,
+                const int2* d_dn, int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s,
+                int reserve) {
   if (n_dn > 0) {
     PhaseScope ps("update.dense_target", s);
     const size_t per = (size_t)h->kcap * h->kcap + (size_t)h->nb * h->kcap;
@@ -414,7 +476,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     const int nc = h->kcap > h->nb ? h->nb : h->kcap;
     const size_t tcd = std::max(tc_item_doubles(h, h->nb, nc, h->nb), tc_item_doubles(h, h->nb, h->nb, h->nb));
     int chunk = chunk_of(h, per + 3 * gd + tcd, 64);
-    if (chunk < 1) return TLR_ERR_OOM;
+    if (chunk < 1) TLR_RETURN_OOM();
     for (int64_t q0 = 0; q0 < n_dn; q0 += chunk) {
       const int cnt = (int)(n_dn - q0 < chunk ? n_dn - q0 : chunk);
       GemmGen* d0 = (GemmGen*)h->scratch;
@@ -440,14 +502,22 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     PhaseScope ps("update.lowrank_target", s);
     const size_t ie = tlr_item_elems(h->nb, h->kcap);
     const int chunk = chunk_of(h, ie, 0);
-    if (chunk < 1) return TLR_ERR_OOM;
+    if (chunk < 1) TLR_RETURN_OOM();
     const int slots = std::max(resident_ctas(h->nb) - std::max(reserve, 0), 1);
     const int grid = (int)std::min<int64_t>(n_lr, std::min(slots, chunk));
+    bool staged = false;
+    if (n_dop > 0) {
+      PhaseScope ps2("update.dense_operand", s);
+      const int rc = stage_dense_operand_products(h, v, alg, k, d_lr, std::min(n_dop, n_lr), s, &staged);
+      if (rc) return rc;
+    }
     TLR_CUDA_TRY(cudaMemsetAsync(h->d_ctr, 0, sizeof(int), s));
     if (g_tlr_prof.enabled) tlr_prof_begin(s);
     k_upd_lr_gen<<<grid, TLR_THREADS, upd_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
                                                             2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie,
-                                                            h->d_stat, g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr);
+                                                            h->d_stat, g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr,
+                                                            staged ? h->dop : nullptr,
+                                                            staged ? (int)std::min(n_dop, n_lr) : 0);
     TLR_LAUNCH_CHECK();
     if (g_tlr_prof.enabled) tlr_prof_end(s);
   }
@@ -471,7 +541,7 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   const size_t tcd = tc_item_doubles(h, h->nb, h->nb, h->nb);
   const size_t per = tops_dd_item_elems(h);
   const int chunk = ws_elems > 64 ? (int)std::min<size_t>((ws_elems - 64) / per, 65535) : 0;
-  if (chunk < 1) return TLR_ERR_OOM;
+  if (chunk < 1) TLR_RETURN_OOM();
   const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
   if (tlr_smem_optin((const void*)k_dd_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
   for (int64_t q0 = 0; q0 < n_dd; q0 += chunk) {
@@ -509,7 +579,7 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
     const int ncols_max = pass == 0 ? h->kcap : h->nb;
     const size_t tcd = tc_item_doubles(h, h->nb, ncols_max, h->nb);
     const int chunk = chunk_of(h, tmp_elems + gd + tcd, 128);
-    if (chunk < 1) return TLR_ERR_OOM;
+    if (chunk < 1) TLR_RETURN_OOM();
     for (int q0 = 0; q0 < total; q0 += chunk) {
       const int cnt = total - q0 < chunk ? total - q0 : chunk;
       GemmGen* desc = (GemmGen*)h->scratch;

@@ -18,9 +18,11 @@ struct GemmGen {
 };
 
 // low-rank targets (recompressed at tau = eps * zeta^zpow, zeta = *d_zeta or 1) and dense targets;
-// the persistent low-rank kernel leaves `reserve` CTA slots free for work on another stream
-int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, const int2* d_dn,
-                int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s, int reserve = 0);
+// the first n_dop low-rank items have a dense operand (their products are formed by a batched GEMM
+// first); the persistent low-rank kernel leaves `reserve` CTA slots free for work on another stream
+int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, int64_t n_lr, int64_t n_dop,
+                const int2* d_dn, int64_t n_dn, double eps, const double* d_zeta, double zpow, cudaStream_t s,
+                int reserve = 0);
 // low-rank targets whose two sources are both dense (materialise, ACA, recompress); workspace ws
 // (ws_elems doubles), h->scratch when null
 int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_dd, int64_t n_dd, double eps,
