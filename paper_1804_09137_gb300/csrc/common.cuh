@@ -45,6 +45,7 @@
 
 #define ST_CODE 0
 #define ST_INFO 1
+#define ST_BAR 3   // status word 3: grid-barrier counter of the one-launch tile Cholesky
 
 struct MaternParams {
   double sigma2, beta, nu;

@@ -1,148 +1,143 @@
-// Dense float64 Cholesky of one diagonal tile: blocked right-looking over
-// 32-column panels (panel POTRF in shared memory, row-parallel panel TRSM,
-// 64 x 64-blocked SYRK of the trailing lower triangle).
+// Dense Cholesky of one diagonal tile in one launch: a cooperative grid (every CTA
+// resident) walks the tile's 32-column panels right-looking, with two grid barriers
+// per panel:
+//   1. the CTAs that own rows below the panel (and CTA 0) factor the panel's 32 x 32
+//      diagonal block in float64 (one warp, a row per lane, in shared memory),
+//      CTA 0 stores it, and each CTA solves its share of the panel rows
+//      (A[r, panel] <- A[r, panel] L_pp^{-T}, a row per warp, float64);
+//   2. the trailing lower triangle is updated in 64 x 64 blocks spread over the CTAs
+//      (A22 <- A22 - P P^T with the products in double-float on the float32 pipe).
+// Only the lower triangle of the tile is read or defined afterwards; the strict upper
+// part of each 32 x 32 diagonal block is written as zero.  Every barrier wait is
+// bounded (about two seconds): a CTA that gives up records TLR_ERR_TIMEOUT and returns.
 #include "common.cuh"
+#include "recompress.cuh"
 
 namespace {
 
-constexpr int PB = 32;  // panel width of the tile Cholesky
+constexpr int PB = 32;                     // panel width of the tile Cholesky
+constexpr long long BAR_WAIT = 1ll << 32;  // clock cycles before a barrier wait gives up
 
-// unblocked Cholesky of the w x w diagonal block at (c0, c0), in shared memory
-__global__ void k_potrf_diag(double* __restrict__ A, int lda, int c0, int w, int64_t col0,
-                             long long* __restrict__ st) {
-  __shared__ double S[PB][PB + 1];
-  for (int id = threadIdx.x; id < w * w; id += blockDim.x) {
-    const int r = id % w, c = id / w;
-    S[r][c] = A[(size_t)(c0 + c) * lda + c0 + r];
-  }
+// grid-wide barrier on a counter zeroed before the launch: the i-th barrier completes when the
+// counter reaches i * gridDim.x; false when the wait gave up
+__device__ bool grid_barrier(unsigned int* bar, unsigned int& target, long long* st) {
+  __shared__ int s_ok;
   __syncthreads();
-  for (int c = 0; c < w; ++c) {
-    if (threadIdx.x == 0) {
-      double d = S[c][c];
-      if (!(d > 0.0)) {  // non-positive or NaN pivot
-        set_status(st, TLR_ERR_NOT_SPD, col0 + c0 + c + 1);
-        d = 1.0;
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    const long long t0 = clock64();
+    while (*(volatile unsigned int*)bar < target) {
+      if (clock64() - t0 > BAR_WAIT) {
+        set_status(st, TLR_ERR_TIMEOUT, 5);
+        ok = 0;
+        break;
       }
-      S[c][c] = sqrt(d);
+      __nanosleep(64);
     }
-    __syncthreads();
-    const double inv = 1.0 / S[c][c];
-    for (int r = c + 1 + threadIdx.x; r < w; r += blockDim.x) S[r][c] *= inv;
-    __syncthreads();
-    for (int id = threadIdx.x; id < w * w; id += blockDim.x) {
-      const int r = id % w, q = id / w;
-      if (q > c && r >= q) S[r][q] -= S[r][c] * S[q][c];
-    }
-    __syncthreads();
-  }
-  for (int id = threadIdx.x; id < w * w; id += blockDim.x) {
-    const int r = id % w, c = id / w;
-    A[(size_t)(c0 + c) * lda + c0 + r] = (r >= c) ? S[r][c] : 0.0;
-  }
-}
-
-// rows r >= c0 + w of the panel: A[r, c0:c0+w] <- A[r, c0:c0+w] L_pp^{-T}
-__global__ void k_trsm_panel(double* __restrict__ A, int lda, int nrows, int c0, int w) {
-  __shared__ double L[PB][PB + 1];
-  for (int id = threadIdx.x; id < w * w; id += blockDim.x) {
-    const int r = id % w, c = id / w;
-    L[r][c] = A[(size_t)(c0 + c) * lda + c0 + r];
+    __threadfence();
+    s_ok = ok;
   }
   __syncthreads();
-  const int r = c0 + w + blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  double xr[PB];
-#pragma unroll
-  for (int c = 0; c < PB; ++c) xr[c] = (c < w) ? A[(size_t)(c0 + c) * lda + r] : 0.0;
-#pragma unroll
-  for (int c = 0; c < PB; ++c) {
-    if (c < w) {
-      double s = xr[c];
-#pragma unroll
-      for (int l = 0; l < PB; ++l)
-        if (l < c) s -= xr[l] * L[c][l];
-      xr[c] = s / L[c][c];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < PB; ++c)
-    if (c < w) A[(size_t)(c0 + c) * lda + r] = xr[c];
+  return s_ok != 0;
 }
 
-// C[r0:r0+64, q0:q0+64] -= A[r0:.., 0:K] * B[q0:.., 0:K]^T  (column major, 256 threads)
-// rows >= mrows / cols >= mcols are ignored
-__device__ __forceinline__ void tile_gemm_nt_sub(const double* __restrict__ A, int lda, const double* __restrict__ B,
-                                                 int ldb, double* __restrict__ C, int ldc, int r0, int q0, int mrows,
-                                                 int mcols, int K, bool lower_only) {
-  __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64 + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int id = threadIdx.x; id < 64 * 16; id += 256) {
-      const int a = id & 63, kk = id >> 6;
-      const int ra = r0 + a, qb = q0 + a, kc = k0 + kk;
-      As[kk][a] = (ra < mrows && kc < K) ? A[(size_t)kc * lda + ra] : 0.0;
-      Bs[kk][a] = (qb < mcols && kc < K) ? B[(size_t)kc * ldb + qb] : 0.0;
+__global__ void __launch_bounds__(256, 2) k_potrf_tile(double* __restrict__ A, int lda, int nb, int64_t col0,
+                                                       long long* __restrict__ st, unsigned int* __restrict__ bar) {
+  __shared__ double Ls[PB][PB + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned int target = 0;
+  for (int c0 = 0; c0 < nb; c0 += PB) {
+    const int w = nb - c0 < PB ? nb - c0 : PB;
+    const int c1 = c0 + w;
+    const int below = nb - c1;
+    const int per = (below + gridDim.x - 1) / gridDim.x;  // panel rows per CTA
+    const int r_lo = blockIdx.x * per;
+    const int r_hi = below < r_lo + per ? below : r_lo + per;
+    if (blockIdx.x == 0 || r_lo < r_hi) {
+      if (warp == 0) {
+        // lane r owns row r of the diagonal block in shared memory (identity beyond w)
+        for (int q = 0; q < PB; ++q)
+          Ls[lane][q] = (lane < w && q < w) ? A[(size_t)(c0 + q) * lda + c0 + lane] : (lane == q ? 1.0 : 0.0);
+        __syncwarp();
+        for (int c = 0; c < w; ++c) {
+          double d = Ls[c][c];
+          if (!(d > 0.0)) {  // non-positive or NaN pivot
+            if (blockIdx.x == 0 && lane == 0) set_status(st, TLR_ERR_NOT_SPD, col0 + c0 + c + 1);
+            d = 1.0;
+          }
+          const double l = sqrt(d);
+          __syncwarp();
+          if (lane == c) Ls[c][c] = l;
+          else if (lane > c && lane < w) Ls[lane][c] /= l;
+          __syncwarp();
+          if (lane > c && lane < w) {
+            const double lrc = Ls[lane][c];
+            for (int q = c + 1; q <= lane; ++q) Ls[lane][q] = fma(-lrc, Ls[q][c], Ls[lane][q]);
+          }
+          __syncwarp();
+        }
+        for (int q = lane + 1; q < PB; ++q) Ls[lane][q] = 0.0;
+      }
+      __syncthreads();
+      if (blockIdx.x == 0)
+        for (int id = threadIdx.x; id < w * w; id += blockDim.x) {
+          const int r = id % w, c = id / w;
+          A[(size_t)(c0 + c) * lda + c0 + r] = Ls[r][c];
+        }
+      // panel rows of this CTA, a warp per row: lane c holds column c, forward substitution over the columns
+      for (int rr = r_lo + warp; rr < r_hi; rr += blockDim.x >> 5) {
+        const int r = c1 + rr;
+        double x = lane < w ? A[(size_t)(c0 + lane) * lda + r] : 0.0;
+        for (int c = 0; c < w; ++c) {
+          const double xc = __shfl_sync(0xffffffffu, x, c) / Ls[c][c];
+          if (lane == c) x = xc;
+          else if (lane > c) x = fma(-xc, Ls[lane][c], x);
+        }
+        if (lane < w) A[(size_t)(c0 + lane) * lda + r] = x;
+      }
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
+    if (below <= 0) break;
+    if (!grid_barrier(bar, target, st)) return;
+    // A22 -= P P^T over the lower blocks of the trailing matrix, P = A[c1:, c0:c1]
+    const double* P = A + (size_t)c0 * lda + c1;
+    cta_gemm_df_blocks(below, below, w, -1.0, P, lda, 0, P, lda, 1, 1.0, A + (size_t)c1 * lda + c1, lda, blockIdx.x,
+                       gridDim.x, 1);
+    if (!grid_barrier(bar, target, st)) return;
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = r0 + ty + 16 * i, q = q0 + tx + 16 * j;
-      if (r < mrows && q < mcols && (!lower_only || r >= q)) C[(size_t)q * ldc + r] -= acc[i][j];
-    }
 }
 
-// trailing update of the tile Cholesky: lower blocks of A[c1:, c1:] -= P P^T, P = A[c1:, c0:c1]
-__global__ void k_syrk_trailing(double* __restrict__ A, int lda, int nrows, int c0, int w) {
-  const int c1 = c0 + w;
-  // decode lower block (bi >= bj) from blockIdx.x
-  const int t = blockIdx.x;
-  int bi = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-  while (bi * (bi + 1) / 2 > t) --bi;
-  const int bj = t - bi * (bi + 1) / 2;
-  const double* P = A + (size_t)c0 * lda + c1;
-  double* C = A + (size_t)c1 * lda + c1;
-  tile_gemm_nt_sub(P, lda, P, lda, C, lda, 64 * bi, 64 * bj, nrows - c1, nrows - c1, w, true);
+// resident CTAs of k_potrf_tile on the current device (cached per device)
+int potrf_max_grid() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cached[dev] > 0) return cached[dev];
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_potrf_tile, 256, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  cached[dev] = per_sm * sms;
+  return cached[dev];
 }
 
 }  // namespace
 
 int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s) {
-  for (int c0 = 0; c0 < nb; c0 += PB) {
-    const int w = nb - c0 < PB ? nb - c0 : PB;
-    k_potrf_diag<<<1, 256, 0, s>>>(A, lda, c0, w, col0, h->d_stat);
-    TLR_LAUNCH_CHECK();
-    const int below = nb - c0 - w;
-    if (below > 0) {
-      k_trsm_panel<<<(below + 127) / 128, 128, 0, s>>>(A, lda, nb, c0, w);
-      TLR_LAUNCH_CHECK();
-      const int T = (below + 63) / 64;
-      k_syrk_trailing<<<T * (T + 1) / 2, 256, 0, s>>>(A, lda, nb, c0, w);
-      TLR_LAUNCH_CHECK();
-    }
-  }
+  if (nb <= 0) return TLR_OK;
+  const int maxg = potrf_max_grid();
+  if (maxg < 1) return TLR_ERR_CUDA;
+  // one CTA per 64 x 64 block of the first panel's trailing update, within what stays resident
+  const int t = (nb - PB + 63) / 64;
+  int grid = t > 0 ? t * (t + 1) / 2 : 1;
+  if (grid > maxg) grid = maxg;
+  long long* st = h->d_stat;
+  unsigned int* bar = reinterpret_cast<unsigned int*>(h->d_stat + ST_BAR);
+  TLR_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned int), s));
+  void* args[] = {&A, &lda, &nb, &col0, &st, &bar};
+  TLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_potrf_tile, dim3(grid), dim3(256), args, 0, s));
+  TLR_LAUNCH_CHECK();
   return TLR_OK;
 }
-

@@ -117,7 +117,9 @@ __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
 
 size_t tlr_item_elems(int nb, int kcap) {
   const size_t Kmax = 2 * (size_t)kcap;
-  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax;
+  // factors, products, cores, scalars and exponents, and the blocked QR's T factors (8-byte entries)
+  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax +
+         2 * (Kmax + QR_PBMAX) * QR_PBMAX;
 }
 
 static int chunk_for(const tlr_ctx* h, size_t per_item, size_t reserve = 0) {

@@ -652,7 +652,7 @@ static int ensure_aux(tlr_ctx* h, int items) {
     TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
-  const size_t want = (size_t)items * tops_dd_item_elems(h) + 16;
+  const size_t want = (size_t)items * tops_dd_item_elems(h) + 64;  // tops_update_dd keeps 64 back
   if (want > h->scratch_dd_elems) {
     if (h->scratch_dd) cudaFree(h->scratch_dd);
     h->scratch_dd = nullptr;
