@@ -84,12 +84,12 @@ void tlr_phase_end(cudaStream_t s) {
   g_ph_open.pop_back();
 }
 
-// digamma by upward recurrence to x >= 10 and the asymptotic series
-// psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
 void tlr_note_oom(const char* file, int line) {
   if (getenv("TLR_VERBOSE")) fprintf(stderr, "tlr: out of memory at %s:%d\n", file, line);
 }
 
+// digamma by upward recurrence to x >= 10 and the asymptotic series
+// psi(x) ~ ln x - 1/(2x) - sum_k B_2k / (2k x^2k)  (Abramowitz & Stegun 6.3.18)
 double tlr_host_digamma(double x) {
   double r = 0.0;
   while (x < 10.0) { r -= 1.0 / x; x += 1.0; }

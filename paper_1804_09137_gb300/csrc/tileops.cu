@@ -8,6 +8,8 @@
 // tile); dense targets get C += P Q^T by batched 64 x 64-block GEMM.
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "recompress.cuh"
 #include "tcgemm.h"
@@ -380,21 +382,26 @@ int upd_qr_pb(int nb) {
 size_t upd_smem(int nb) { return 2 * (size_t)nb * sizeof(dfloat) * std::max(upd_qr_pb(nb), 1); }
 
 // resident CTAs of the persistent low-rank update kernel on the current device for tile size nb
+// (remembered per device and tile size; handles on several host threads may use different sizes)
 int resident_ctas(int nb) {
-  static std::atomic<int> cached[64];
-  static std::atomic<int> cached_nb[64];
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> memo;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  const int c = cached[dev].load();
-  if (c > 0 && cached_nb[dev].load() == nb) return c;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find({dev, nb});
+    if (it != memo.end()) return it->second;
+  }
   int per_sm = 0, sms = 0;
   if (tlr_smem_optin((const void*)k_upd_lr_gen, upd_smem(nb)) != TLR_OK) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_upd_lr_gen, TLR_THREADS, upd_smem(nb)) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
-  cached_nb[dev].store(nb);
-  cached[dev].store(std::max(per_sm, 1) * sms);
-  return std::max(per_sm, 1) * sms;
+  const int r = std::max(per_sm, 1) * sms;
+  std::lock_guard<std::mutex> lock(mu);
+  memo[{dev, nb}] = r;
+  return r;
 }
 
 int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
@@ -441,11 +448,20 @@ int tops_gemm_mixed(tlr_ctx* h, const GemmGen* d_desc, int count, int m, int n, 
 }  // namespace
 
 int tlr_smem_optin(const void* f, size_t dyn) {
+  // the limit is raised once per device and kernel to all the shared memory a block may have, so that
+  // callers on several host threads with different sizes never lower it under one another's launch
   cudaFuncAttributes a;
   if (cudaFuncGetAttributes(&a, f) != cudaSuccess) return TLR_ERR_CUDA;
   if (a.sharedSizeBytes + dyn <= 48 * 1024) return TLR_OK;
-  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess ? TLR_OK
-                                                                                                        : TLR_ERR_CUDA;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return TLR_ERR_CUDA;
+  const int most = optin - (int)a.sharedSizeBytes;
+  if ((int)dyn > most) return TLR_ERR_CUDA;
+  if (a.maxDynamicSharedSizeBytes >= most) return TLR_OK;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most) == cudaSuccess ? TLR_OK
+                                                                                                   : TLR_ERR_CUDA;
 }
 
 // the products of the first n_dop low-rank items with the dense operand, into h->dop (batched GEMM, on the
