@@ -639,6 +639,7 @@ def main():
         log(f"warmup {i}: {time.perf_counter() - t0:.2f} s")
     h.check()
     tlr_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+    mem = h.memory()  # the handle's own account: arenas, their used part, workspaces
     stream = torch.cuda.current_stream()
     clocks = Clocks(local)
 
@@ -751,7 +752,7 @@ def main():
             "config": main_config(a, n, len(xn_h), "replicas" if world > 1 else "single"),
             "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "dense_fp64_gpu": dense, "accuracy": accuracy, "deterministic_across_steps": deterministic,
-            "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes)},
+            "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes), "handle": mem},
             "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,
                        "tiles": counts, "inverse": inv}}
     print(json.dumps(line), flush=True)

@@ -15,19 +15,24 @@
  *    enqueued on `stream` has finished.  The library never frees caller memory.
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *    stream.  Calls enqueue work on it and return without synchronising, except
- *    tlr_create / tlr_destroy / tlr_status / tlr_rank_stats, which synchronise.
+ *    tlr_create / tlr_destroy / tlr_status / tlr_rank_stats / tlr_memory, which
+ *    synchronise, and tlr_compress / tlr_potrf / tlr_loglik_grad, which
+ *    synchronise once to check that the low-rank storage sufficed.
  *  - Vectors indexed by point (z, e, outputs) are in the CALLER's point order;
  *    the internal Morton permutation is applied and undone inside.
  *  - Return value: TLR_OK (0); -i when argument i (1-based) is invalid (nothing
  *    is enqueued); a positive TLR_ERR_* code otherwise.  Failures that happen on
  *    the device (non-SPD pivot, rank cap overflow, wait time-out) are recorded in
  *    the handle and reported by tlr_status after the stream has drained.
- *  - The library owns its tile storage, allocated with cudaMalloc in tlr_create;
- *    the gradient's inverse (Sigma^{-1}, about nt(nt+1)/2 dense tiles) and a
- *    second stream with its workspace are allocated by the first
- *    tlr_loglik_grad (TLR_ERR_OOM when that fails); a dense pool
- *    grows in tlr_compress when more tiles turn dense.  Everything is released
- *    by tlr_destroy.
+ *  - The library owns its tile storage, allocated with cudaMalloc in tlr_create.
+ *    The low-rank factors live in rank-packed arenas (each tile a block of about
+ *    1.25 times its rank in columns, a new block when its rank outgrows it): an
+ *    arena that runs out is enlarged and the operation repeated inside
+ *    tlr_compress, tlr_potrf (from regenerated tiles) or tlr_loglik_grad.  The
+ *    gradient's inverse L^{-1} (its own arena and dense tiles) and a second
+ *    stream with its workspace are allocated by the first tlr_loglik_grad; a
+ *    dense pool grows in tlr_compress when more tiles turn dense.  TLR_ERR_OOM
+ *    when an allocation fails.  Everything is released by tlr_destroy.
  */
 #ifndef TLR_H_
 #define TLR_H_
@@ -248,6 +253,13 @@ int tlr_loglik_dense_noalloc(int64_t n, const double* x, const double* y, const 
  * TLR_ERR_TIMEOUT when a device-side wait gave up. */
 int tlr_gemm_tc(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb, int tB, double* C,
                 int ldc, double alpha, double beta, int slices, tlr_stream_t stream);
+
+/* Device memory held by the handle, in bytes: *total (everything it has
+ * allocated), *arenas (the rank-packed low-rank arenas of L and of the
+ * inverse), *arena_used (the part of them handed out to tiles) and *workspace
+ * (batched-kernel, update and gradient workspaces).  Any output may be NULL.
+ * Synchronises. */
+int tlr_memory(tlr_handle h, int64_t* total, int64_t* arenas, int64_t* arena_used, int64_t* workspace);
 
 /* Rank statistics of the low-rank tiles of the inverse Sigma^{-1} built by the
  * last tlr_loglik_grad, and its number of dense off-diagonal tiles.

@@ -162,7 +162,7 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop,
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop, h->off, h->cap, h->top, h->offz, h->capz, h->topz,
                   h->gpart};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -237,15 +237,21 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   if (h->dense_rank > 2 * h->kcap - 8) h->dense_rank = std::max(1, 2 * h->kcap - 8);
 
   const size_t nb = h->nb;
-  const size_t slot = nb * (size_t)h->kcap;
   const int64_t cnp = (int64_t)h->cap_nt * h->nb, ct = h->cap_ntiles;
   int rc = TLR_OK;
   rc |= dmalloc(&h->x, cnp);
   rc |= dmalloc(&h->y, cnp);
   rc |= dmalloc(&h->perm, n);
   rc |= dmalloc(&h->D, (size_t)h->cap_nt * nb * nb);
-  rc |= dmalloc(&h->U, h->dense ? 1 : (size_t)ct * slot);
-  rc |= dmalloc(&h->V, h->dense ? 1 : (size_t)ct * slot);
+  // rank-packed arenas: room for 32 columns a tile to start with; compression, the factorization and
+  // the inverse enlarge them (and repeat) when the ranks need more
+  h->kws = 2 * h->kcap;
+  h->arena = h->dense ? 1 : std::max<int64_t>(ct, 1) * (int64_t)nb * std::min(h->kcap, 32);
+  rc |= dmalloc(&h->U, (size_t)h->arena);
+  rc |= dmalloc(&h->V, (size_t)h->arena);
+  rc |= dmalloc(&h->off, ct);
+  rc |= dmalloc(&h->cap, ct);
+  rc |= dmalloc(&h->top, 1);
   rc |= dmalloc(&h->rank, ct);
   rc |= dmalloc(&h->dslot, ct);
   rc |= dmalloc(&h->tab, TAB_ELEMS);
@@ -259,9 +265,11 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   // workspace: low-rank update items, SYRK items, table nodes, gradient partials
   const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap);
   const int64_t max_items = std::max<int64_t>(ct, 1);
-  const int64_t chunk = std::min<int64_t>(max_items, 912);
+  // one item workspace per resident CTA of the persistent update kernel (compression takes as many tiles
+  // a launch)
+  const int64_t chunk = std::min<int64_t>(max_items, h->dense ? 912 : std::max(tops_resident_ctas(h->nb), 64));
   size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
-  ws = std::max(ws, (size_t)std::min<int64_t>(max_items, 912) * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
+  ws = std::max(ws, (size_t)chunk * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
   ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->cap_nt * (h->cap_nt + 1) / 2 + 16));
   // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
   const size_t mb = (nb + 63) / 64;
@@ -285,6 +293,59 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   return TLR_OK;
 }
 
+
+int tlr_arena_alloc(double** U, double** V, int64_t* arena, int64_t need) {
+  if (need <= *arena) return TLR_OK;
+  if (*U) cudaFree(*U);
+  if (*V) cudaFree(*V);
+  *U = *V = nullptr;
+  *arena = 0;
+  const int64_t want = need + need / 4;
+  if (cudaMalloc((void**)U, (size_t)want * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)V, (size_t)want * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (*U) cudaFree(*U);
+    *U = nullptr;
+    TLR_RETURN_OOM();
+  }
+  *arena = want;
+  return TLR_OK;
+}
+
+int tlr_take_grow(tlr_ctx* h, cudaStream_t s, const unsigned long long* d_top, int64_t* need) {
+  long long st[2];
+  unsigned long long top = 0;
+  TLR_CUDA_TRY(cudaMemcpyAsync(st, h->d_stat, sizeof(st), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaMemcpyAsync(&top, d_top, sizeof(top), cudaMemcpyDeviceToHost, s));
+  TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  *need = 0;
+  if (st[ST_CODE] != TLR_ST_GROW) return TLR_OK;
+  TLR_CUDA_TRY(cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s));
+  *need = (int64_t)top;  // every block asked for, the failed ones included
+  return TLR_OK;
+}
+
+namespace {
+// compression into a fresh arena: every tile starts without columns
+int compress_fresh(tlr_ctx* h, double eps, cudaStream_t s) {
+  if (h->ntiles <= 0) return TLR_OK;
+  TLR_CUDA_TRY(cudaMemsetAsync(h->cap, 0, h->ntiles * sizeof(int), s));
+  TLR_CUDA_TRY(cudaMemsetAsync(h->top, 0, sizeof(unsigned long long), s));
+  return tlr_compress_tiles(h, eps, s);
+}
+
+// compression with the arena enlarged and the compression repeated while it runs out
+int compress_grow(tlr_ctx* h, double eps, cudaStream_t s) {
+  for (int attempt = 0;; ++attempt) {
+    TRY(compress_fresh(h, eps, s));
+    int64_t need = 0;
+    TRY(tlr_take_grow(h, s, h->top, &need));
+    if (need == 0) return TLR_OK;
+    if (attempt >= 4) TLR_RETURN_OOM();
+    TRY(tlr_arena_alloc(&h->U, &h->V, &h->arena, std::max(need, 2 * h->arena)));
+  }
+}
+}  // namespace
 
 extern "C" {
 
@@ -371,7 +432,7 @@ int tlr_compress(tlr_handle h, double eps, tlr_stream_t stream) {
   h->opts.eps = eps;
   {
     PhaseScope ps("compress", s);
-    if (h->ntiles > 0) TRY(tlr_compress_tiles(h, eps, s));
+    TRY(compress_grow(h, eps, s));
   }
   {
     PhaseScope ps("plan", s);
@@ -386,7 +447,20 @@ int tlr_potrf(tlr_handle h, tlr_stream_t stream) {
   if (h->state != 2) return TLR_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   h->last_stream = s;
-  TRY(tlr_factor(h, s));
+  // the factor's ranks can outgrow the arena: then it is enlarged and the factorization repeated
+  // from regenerated tiles (one synchronisation at the end to check)
+  for (int attempt = 0;; ++attempt) {
+    TRY(tlr_factor(h, s));
+    if (h->dense) break;
+    int64_t need = 0;
+    TRY(tlr_take_grow(h, s, h->top, &need));
+    if (need == 0) break;
+    if (attempt >= 4) TLR_RETURN_OOM();
+    TRY(tlr_arena_alloc(&h->U, &h->V, &h->arena, std::max(need, 2 * h->arena)));
+    TRY(tlr_gen_diag(h, s));
+    TRY(compress_grow(h, h->opts.eps, s));
+    TRY(tlr_plan(h, s));
+  }
   h->state = 3;
   return TLR_OK;
 }
@@ -539,7 +613,6 @@ int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, int* 
     *k = h->nb;
   } else {
     const int64_t t = tile_index(i, j);
-    const size_t slot = nb * h->kcap;
     int r = 0;
     TLR_CUDA_TRY(cudaMemcpyAsync(&r, h->rank + t, sizeof(int), cudaMemcpyDeviceToHost, s));
     TLR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -553,8 +626,11 @@ int tlr_get_tile(tlr_handle h, int i, int j, double* U, double* V, int* k, int* 
                                    cudaMemcpyDeviceToDevice, s));
     } else if (r > 0) {
       *dense = 0;
-      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      TLR_CUDA_TRY(cudaMemcpyAsync(V, h->V + t * slot, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      int64_t o = 0;
+      TLR_CUDA_TRY(cudaMemcpyAsync(&o, h->off + t, sizeof(o), cudaMemcpyDeviceToHost, s));
+      TLR_CUDA_TRY(cudaStreamSynchronize(s));
+      TLR_CUDA_TRY(cudaMemcpyAsync(U, h->U + o, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TLR_CUDA_TRY(cudaMemcpyAsync(V, h->V + o, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     if (!dense_tile) *dense = 0;
     *k = r;
@@ -598,6 +674,30 @@ int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t
   if (kmax) *kmax = mx;
   if (kmean) *kmean = nlr > 0 ? sum / nlr : 0.0;
   if (n_dense) *n_dense = h->ndensez;
+  return TLR_OK;
+}
+
+int tlr_memory(tlr_handle h, int64_t* total, int64_t* arenas, int64_t* arena_used, int64_t* workspace) {
+  if (!h) return -1;
+  TLR_CUDA_TRY(cudaStreamSynchronize(h->last_stream));
+  unsigned long long top = 0, topz = 0;
+  if (h->top) TLR_CUDA_TRY(cudaMemcpy(&top, h->top, sizeof(top), cudaMemcpyDeviceToHost));
+  if (h->topz) TLR_CUDA_TRY(cudaMemcpy(&topz, h->topz, sizeof(topz), cudaMemcpyDeviceToHost));
+  const double d = sizeof(double);
+  const double nn = (double)h->nb * h->nb, ct = (double)std::max<int64_t>(h->cap_ntiles, 1);
+  const double cnp = (double)h->cap_nt * h->nb;
+  const double ar = 2.0 * d * ((double)h->arena + (double)h->arenaz);
+  const double ws = d * ((double)h->scratch_elems + (double)h->scratch_dd_elems + (double)h->dop_elems +
+                         (double)h->gpart_elems + (double)h->msave_elems);
+  double fixed = d * (2 * cnp + 4 * cnp + (double)h->nb + TAB_ELEMS + h->red_len + 4) + 4.0 * h->cap_n + 16.0;
+  fixed += d * 2 * h->cap_nt * nn + ct * (4 + 4 + 8 + 4) + 8;               // D, linv, rank, dslot, off, cap
+  fixed += d * (double)h->dcap * nn + 8.0 * (double)h->list_cap;            // dense pool, plan lists
+  if (h->Dz) fixed += d * h->cap_nt * nn + ct * (4 + 4 + 8 + 4) + 8 + d * (double)h->dcapz * nn +
+                      8.0 * (double)h->zlist_cap;
+  if (total) *total = (int64_t)(fixed + ar + ws);
+  if (arenas) *arenas = (int64_t)ar;
+  if (arena_used) *arena_used = (int64_t)(2.0 * d * ((double)top + (h->Dz ? (double)topz : 0.0)));
+  if (workspace) *workspace = (int64_t)ws;
   return TLR_OK;
 }
 

@@ -46,6 +46,9 @@
 #define ST_CODE 0
 #define ST_INFO 1
 #define ST_BAR 3   // status word 3: grid-barrier counter of the one-launch tile Cholesky
+// internal status code (never returned to a caller): a low-rank arena or an update workspace was too
+// small; the host enlarges it and repeats the operation
+#define TLR_ST_GROW 100
 
 struct MaternParams {
   double sigma2, beta, nu;
@@ -71,8 +74,13 @@ struct tlr_ctx {
   double* y;
   int* perm;       // perm[s] = caller index of sorted point s (n entries)
   double* D;       // nt dense diagonal tiles, nb x nb column-major
-  double* U;       // ntiles slots, nb x kcap column-major (dense mode: nb x nb tile in U)
+  double* U;       // rank-packed arenas of the low-rank factors (arena entries each; see tile.cuh)
   double* V;
+  int64_t* off;    // ntiles: first arena entry of each tile's columns
+  int* cap;        // ntiles: columns reserved there
+  unsigned long long* top;  // arena entries handed out (device counter)
+  int64_t arena;   // arena size in entries
+  int kws;         // concatenated-rank bound of the update workspaces (at most 2 kcap)
   int* rank;       // ntiles ranks (-1 after compression: not compressible below dense_rank)
   int* dslot;      // ntiles dense-pool slot or -1 (low rank)
   double* dpool;   // dense off-diagonal tiles, nb x nb each
@@ -88,6 +96,10 @@ struct tlr_ctx {
   double* Dz;
   double* Uz;
   double* Vz;
+  int64_t* offz;   // the inverse's arena layout, as for L
+  int* capz;
+  unsigned long long* topz;
+  int64_t arenaz;
   int* rankz;
   int* dslotz;
   double* dpoolz;
@@ -330,6 +342,13 @@ int tlr_gen_dense_tiles(tlr_ctx* h, const int2* d_items, int count, cudaStream_t
 int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s);
 int tlr_factor(tlr_ctx* h, cudaStream_t s);
 int tlr_plan(tlr_ctx* h, cudaStream_t s);
+// low-rank arenas: (re)allocate a pair for at least `need` entries (contents discarded)
+int tlr_arena_alloc(double** U, double** V, int64_t* arena, int64_t need);
+// CTAs of the persistent low-rank update kernel resident on the current device for tile size nb
+int tops_resident_ctas(int nb);
+// after a synchronisation: *need = the entries the arena counter d_top asked for when an arena or a
+// workspace ran out during the work enqueued so far (status reset), else 0
+int tlr_take_grow(tlr_ctx* h, cudaStream_t s, const unsigned long long* d_top, int64_t* need);
 int tlr_rebind(tlr_ctx* h, int64_t n, const double* x, const double* y, cudaStream_t s);
 int tlr_alloc(int64_t cap_n, const tlr_opts* opts, tlr_ctx** out);
 size_t tlr_item_elems(int nb, int kcap);

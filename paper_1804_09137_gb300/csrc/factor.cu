@@ -56,7 +56,7 @@ __global__ void k_aca_compress(const double* __restrict__ tab, const MaternParam
     return;
   }
   __syncthreads();
-  const int kr = cta_recompress(w, nb, k, eps, v.kcap, trunc_cap, tileU(v, t), tileV(v, t), st, t, sh, shi);
+  const int kr = cta_recompress(w, nb, k, eps, v.kcap, trunc_cap, v, t, st, sh, shi);
   if (threadIdx.x == 0) v.rank[t] = kr;
 }
 
@@ -117,9 +117,7 @@ __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
 
 size_t tlr_item_elems(int nb, int kcap) {
   const size_t Kmax = 2 * (size_t)kcap;
-  // factors, products, cores, scalars and exponents, and the blocked QR's T factors (8-byte entries)
-  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax +
-         2 * (Kmax + QR_PBMAX) * QR_PBMAX;
+  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax;
 }
 
 static int chunk_for(const tlr_ctx* h, size_t per_item, size_t reserve = 0) {

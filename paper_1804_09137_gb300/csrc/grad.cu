@@ -153,6 +153,7 @@ int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s
   TlrView z;
   z.nb = h->nb; z.nt = h->nt; z.kcap = h->kcap;
   z.D = h->Dz; z.U = h->Uz; z.V = h->Vz; z.rank = h->rankz; z.dslot = h->dslotz; z.dpool = h->dpoolz;
+  z.off = h->offz; z.cap = h->capz; z.top = h->topz; z.arena = h->arenaz;
   const int mb = (h->nb + 63) / 64;
   const int64_t pairs = (int64_t)h->nt * (h->nt + 1) / 2;
   const int64_t cnt = pairs * mb * mb;

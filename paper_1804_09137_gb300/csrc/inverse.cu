@@ -97,8 +97,15 @@ static TlrView zview(const tlr_ctx* h) {
   TlrView v;
   v.nb = h->nb; v.nt = h->nt; v.kcap = h->kcap;
   v.D = h->Dz; v.U = h->Uz; v.V = h->Vz; v.rank = h->rankz; v.dslot = h->dslotz; v.dpool = h->dpoolz;
+  v.off = h->offz; v.cap = h->capz; v.top = h->topz; v.arena = h->arenaz;
   return v;
 }
+
+#define ZTRY_OOM(x)                \
+  do {                             \
+    int rc_ = (x);                 \
+    if (rc_ != TLR_OK) return rc_; \
+  } while (0)
 
 static int zplan(tlr_ctx* h, cudaStream_t s) {
   const int nt = h->nt;
@@ -148,6 +155,33 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
     h->dcapz = want;
   }
   h->ndensez = nd;
+  // Z's arena: the low-rank tiles packed by their factor ranks (with room to grow), plus headroom for
+  // the blocks that TRTRI's higher ranks take
+  {
+    std::vector<int64_t> zo(std::max<int64_t>(T, 1), 0);
+    std::vector<int> zc(std::max<int64_t>(T, 1), 0);
+    int64_t pos = 0;
+    for (int64_t t = 0; t < T; ++t) {
+      if (K[t] || rk[t] <= 0) continue;
+      int c = rk[t] + rk[t] / 4 + 8;
+      c = std::min((c + 7) & ~7, h->kcap);
+      zo[t] = pos;
+      zc[t] = c;
+      pos += (int64_t)c * h->nb;
+    }
+    const int64_t need = h->dense ? 1 : 3 * pos + std::max<int64_t>(T, 1) * h->nb * 8;
+    if (need > h->arenaz) {
+      TLR_CUDA_TRY(cudaStreamSynchronize(s));
+      ZTRY_OOM(tlr_arena_alloc(&h->Uz, &h->Vz, &h->arenaz, need));
+    }
+    const unsigned long long top = (unsigned long long)pos;
+    if (T > 0) {
+      TLR_CUDA_TRY(cudaMemcpyAsync(h->offz, zo.data(), T * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      TLR_CUDA_TRY(cudaMemcpyAsync(h->capz, zc.data(), T * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    TLR_CUDA_TRY(cudaMemcpyAsync(h->topz, &top, sizeof(top), cudaMemcpyHostToDevice, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors die here
+  }
   std::vector<int2> L;
   std::vector<int64_t> off((size_t)nt * ZPH + ZG + 1, 0);
   for (int k = 0; k < nt; ++k) {
@@ -221,13 +255,14 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
 
 static int ensure_z(tlr_ctx* h) {
   if (h->Dz) return TLR_OK;
-  const size_t nb = h->nb, slot = nb * h->kcap;
+  const size_t nb = h->nb;
   const size_t T = std::max<int64_t>(h->cap_ntiles, 1);
   bool ok = cudaMalloc((void**)&h->Dz, (size_t)h->cap_nt * nb * nb * sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&h->Uz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&h->Vz, (h->dense ? 1 : T * slot) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&h->rankz, T * sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&h->dslotz, T * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->offz, T * sizeof(int64_t)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->capz, T * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&h->topz, sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     TLR_RETURN_OOM();
@@ -311,8 +346,13 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
     if (fused) return p == q ? h->Dz + (size_t)p * nn : h->dpoolz + (size_t)h->hslotz[tile_index(p, q)] * nn;
     return p == q ? h->msave + (size_t)p * nn : h->msave + (size_t)(nt + dix[tile_index(p, q)]) * nn;
   };
-  auto Uof = [&](int p, int q) -> const double* { return h->Uz + (size_t)tile_index(p, q) * nb * h->kcap; };
-  auto Vof = [&](int p, int q) -> const double* { return h->Vz + (size_t)tile_index(p, q) * nb * h->kcap; };
+  std::vector<int64_t> zoff(std::max<int64_t>(T, 1), 0);
+  if (T > 0) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(zoff.data(), h->offz, T * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  auto Uof = [&](int p, int q) -> const double* { return h->Uz + zoff[tile_index(p, q)]; };
+  auto Vof = [&](int p, int q) -> const double* { return h->Vz + zoff[tile_index(p, q)]; };
   auto rnk = [&](int p, int q) { return rk[tile_index(p, q)]; };
   auto Zdst = [&](int m, int n) -> double* {
     return m == n ? h->Dz + (size_t)n * nn : h->dpoolz + (size_t)tile_index(m, n) * nn;
@@ -675,8 +715,10 @@ struct InverseScope {  // marks the handle as forming the inverse for the scope'
 };
 }  // namespace
 
-int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, int* fused) {
-  InverseScope scope(h);
+// one attempt; *grow > 0 (the entries Z's arena was asked for) when TRTRI ran out of arena, and then
+// the caller enlarges it and starts again
+static int inverse_once(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, int* fused, int64_t* grow) {
+  *grow = 0;
   ZTRY(ensure_z(h));
   if (!h->zplan_valid) ZTRY(zplan(h, s));
   const int nt = h->nt, nb = h->nb;
@@ -694,11 +736,8 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, i
       // one grid row per tile (gridDim.y), offset via pointer arithmetic is not possible: launch per chunk
       const int64_t cnt = std::min<int64_t>(65535, h->ntiles - t0);
       TlrView fo = f, zo = z;
-      fo.rank = f.rank + t0; fo.dslot = f.dslot + t0;
-      zo.rank = z.rank + t0; zo.dslot = z.dslot + t0;
-      fo.U = f.U ? f.U + (size_t)t0 * nb * h->kcap : f.U; fo.V = f.V ? f.V + (size_t)t0 * nb * h->kcap : f.V;
-      zo.U = z.U ? z.U + (size_t)t0 * nb * h->kcap : z.U; zo.V = z.V ? z.V + (size_t)t0 * nb * h->kcap : z.V;
-      if (h->dense) { fo.U = f.U; fo.V = f.V; zo.U = z.U; zo.V = z.V; }
+      fo.rank = f.rank + t0; fo.dslot = f.dslot + t0; fo.off = f.off + t0; fo.cap = f.cap + t0;
+      zo.rank = z.rank + t0; zo.dslot = z.dslot + t0; zo.off = z.off + t0; zo.cap = z.cap + t0;
       k_copy_to_z<<<dim3(8, (unsigned)cnt), 256, 0, s>>>(fo, zo, cnt);
       TLR_LAUNCH_CHECK();
     }
@@ -762,9 +801,23 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, i
     k_copy<<<1024, 256, 0, s>>>(h->linv, h->Dz, (int64_t)nt * nn);
     TLR_LAUNCH_CHECK();
   }
+  // TRTRI's ranks can outgrow Z's arena: checked before LAUUM reads Z
+  h->zplan_valid = 0;  // the device tile kinds and layout of Z changed: the next inverse re-plans
+  ZTRY(tlr_take_grow(h, s, h->topz, grow));
+  if (*grow > 0) return TLR_OK;
   // ---- LAUUM
   if (fused) *fused = tlr_tc_slices(h) > 0 && alpha && out3;
   { PhaseScope ps("lauum", s); ZTRY(lauum_left(h, s, alpha, out3)); }
-  h->zplan_valid = 0;  // the device tile kinds of Z changed: the next inverse re-plans
   return TLR_OK;
+}
+
+int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, int* fused) {
+  InverseScope scope(h);
+  for (int attempt = 0;; ++attempt) {
+    int64_t grow = 0;
+    ZTRY(inverse_once(h, s, alpha, out3, fused, &grow));
+    if (grow == 0) return TLR_OK;
+    if (attempt >= 4) TLR_RETURN_OOM();
+    ZTRY(tlr_arena_alloc(&h->Uz, &h->Vz, &h->arenaz, std::max(grow, 2 * h->arenaz)));
+  }
 }

@@ -4,13 +4,11 @@
 // factors) by an eps-truncated rank-revealing factorization: Householder QR of
 // both factors (double-float), the small core M = R_u R_v^T, column-pivoted QR of
 // M stopped when the trailing block's Frobenius norm is <= eps (spectral error
-// <= eps), and both orthogonal factors applied back.  One CTA of 256 threads per
-// tile; workspace in global memory (L2).
+// <= eps), and both orthogonal factors applied back into tile t's block of the
+// rank-packed arenas.  One CTA of 256 threads per tile; workspace in global memory (L2).
 #pragma once
 #include "df.cuh"
 #include "tile.cuh"
-
-#define QR_PBMAX 8  // widest panel of the blocked Householder QR
 
 namespace {
 
@@ -27,10 +25,7 @@ struct ItemWs {  // per-item workspace layout (doubles)
   double* s;     // Kmax
   int* eu;       // Kmax column scale exponents of Up
   int* ev;       // Kmax column scale exponents of Vp
-  dfloat* Tq;    // T factors of the blocked QR: 2 x (Kmax + QR_PBMAX) QR_PBMAX double-floats
-  dfloat* vs;    // shared memory: two staged reflectors, 2 nb (the kernel's dynamic shared memory), or
-                 // two panels of pb reflectors, 2 pb nb, for the blocked QR
-  int pb;        // panel width of the blocked QR (0: column by column)
+  dfloat* vs;    // shared memory: two staged reflectors, 2 nb (the kernel's dynamic shared memory)
 };
 
 __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int slot, int nb, int Kmax, int kcap) {
@@ -48,10 +43,7 @@ __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int s
   w.s = p; p += Kmax;
   w.eu = (int*)p;
   w.ev = w.eu + Kmax;
-  p += Kmax;  // 2 Kmax ints
-  w.Tq = (dfloat*)p;
   w.vs = nullptr;
-  w.pb = 0;
   return w;
 }
 
@@ -285,226 +277,6 @@ __device__ void cta_apply_q2_df(const dfloat* __restrict__ A1, const double* __r
   __syncthreads();
 }
 
-// ---- blocked Householder QR (compact WY) in double-float --------------------------------
-// Q_p = H_c ... H_{c+w-1} = I - V T V^T for a panel of w <= QR_PBMAX reflectors (T upper triangular,
-// Schreiber and Van Loan, "A storage-efficient WY representation for products of Householder
-// transformations", SIAM J. Sci. Stat. Comput. 10, 1989).  The panel's reflectors are staged in shared
-// memory P with the unit diagonal and the zeros above it written out, so that the products with V run
-// over the rows c..m-1 uniformly.
-
-// column b (rows c..m-1): W = V^T b over the panel's w columns (P: w columns of m, rows c.. valid),
-// then W' = T^T W (trans = 1, factorization: Q_p^T b) or W' = T W (trans = 0: Q_p b), then b -= V W'
-__device__ __forceinline__ void panel_apply_col(dfloat* __restrict__ b, const dfloat* __restrict__ P, int m, int c,
-                                                int w, const dfloat* __restrict__ Tp, int pb, int trans, int lane) {
-  float s[QR_PBMAX], e[QR_PBMAX];
-#pragma unroll
-  for (int l = 0; l < QR_PBMAX; ++l) { s[l] = 0.f; e[l] = 0.f; }
-  int r = c + lane;
-  for (; r + 32 < m; r += 64) {
-    const dfloat b0 = b[r], b1 = b[r + 32];
-#pragma unroll
-    for (int l = 0; l < QR_PBMAX; ++l)
-      if (l < w) {
-        df_dot_add(s[l], e[l], P[(size_t)l * m + r], b0);
-        df_dot_add(s[l], e[l], P[(size_t)l * m + r + 32], b1);
-      }
-  }
-  if (r < m) {
-    const dfloat b0 = b[r];
-#pragma unroll
-    for (int l = 0; l < QR_PBMAX; ++l)
-      if (l < w) df_dot_add(s[l], e[l], P[(size_t)l * m + r], b0);
-  }
-  dfloat W[QR_PBMAX], Wp[QR_PBMAX];
-#pragma unroll
-  for (int l = 0; l < QR_PBMAX; ++l) W[l] = (l < w) ? df_warp_sum(df_norm(s[l], e[l])) : make_float2(0.f, 0.f);
-#pragma unroll
-  for (int i = 0; i < QR_PBMAX; ++i) {
-    float as = 0.f, ae = 0.f;
-    if (i < w) {
-      if (trans) {  // W'_i = sum_{l <= i} T[l, i] W_l
-#pragma unroll
-        for (int l = 0; l < QR_PBMAX; ++l)
-          if (l <= i) df_dot_add(as, ae, Tp[l + i * pb], W[l]);
-      } else {      // W'_i = sum_{l >= i} T[i, l] W_l
-#pragma unroll
-        for (int l = 0; l < QR_PBMAX; ++l)
-          if (l >= i && l < w) df_dot_add(as, ae, Tp[i + l * pb], W[l]);
-      }
-    }
-    Wp[i] = df_norm(as, ae);
-  }
-  for (r = c + lane; r < m; r += 32) {
-    float as = 0.f, ae = 0.f;
-#pragma unroll
-    for (int l = 0; l < QR_PBMAX; ++l)
-      if (l < w) df_dot_add(as, ae, P[(size_t)l * m + r], Wp[l]);
-    const dfloat x = df_norm(as, ae);
-    b[r] = df_add(b[r], make_float2(-x.x, -x.y));
-  }
-}
-
-// Householder QR of two m x K double-float matrices in lockstep, blocked: panels of pb <= QR_PBMAX
-// columns are factored in shared memory (P: 2 pb m double-floats) with the reflector arithmetic of
-// cta_geqr2_pair_df, their T factors (pb x pb, column-major, one per panel) go to T1 / T2, and the
-// columns right of a panel are updated once per panel (A <- Q_p^T A) instead of once per column.
-__device__ void cta_geqrf_pair_blk(dfloat* __restrict__ A1, double* __restrict__ tau1, dfloat* __restrict__ T1,
-                                   dfloat* __restrict__ A2, double* __restrict__ tau2, dfloat* __restrict__ T2,
-                                   int lda, int m, int K, int pb, dfloat* __restrict__ P) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nref = K < m ? K : m;
-  __shared__ dfloat sc_tau[2], sc_scal[2], red[2][TLR_MAX_WARPS];
-  __shared__ int sc_on[2];
-  __shared__ dfloat Ts[2][QR_PBMAX * QR_PBMAX];
-  __shared__ dfloat ys[2][QR_PBMAX * QR_PBMAX];
-  for (int c = 0; c < nref; c += pb) {
-    const int w = nref - c < pb ? nref - c : pb;
-    const int rows = m - c;
-    // stage the panel's columns (rows c..m-1) of both sides
-    for (int e = threadIdx.x; e < 2 * w * rows; e += blockDim.x) {
-      const int side = e / (w * rows), rem = e - side * w * rows, i = rem / rows, r = c + rem % rows;
-      P[(size_t)(side * pb + i) * m + r] = (side ? A2 : A1)[(size_t)(c + i) * lda + r];
-    }
-    __syncthreads();
-    for (int i = 0; i < w; ++i) {
-      const int cc = c + i;
-      dfloat* p1 = P + (size_t)i * m;
-      dfloat* p2 = P + (size_t)(pb + i) * m;
-      float ps1 = 0.f, pc1 = 0.f, ps2 = 0.f, pc2 = 0.f;
-      for (int r = cc + 1 + threadIdx.x; r < m; r += blockDim.x) {
-        df_dot_add(ps1, pc1, p1[r], p1[r]);
-        df_dot_add(ps2, pc2, p2[r], p2[r]);
-      }
-      const dfloat s1 = df_warp_sum(df_norm(ps1, pc1)), s2 = df_warp_sum(df_norm(ps2, pc2));
-      if (lane == 0) { red[0][warp] = s1; red[1][warp] = s2; }
-      __syncthreads();
-      if (threadIdx.x == 0 || threadIdx.x == 32) {  // the reflectors' scalars, in float64
-        const int side = threadIdx.x == 0 ? 0 : 1;
-        dfloat t = red[side][0];
-        for (int q = 1; q < nw; ++q) t = df_add(t, red[side][q]);
-        const double sig = df_to(t);
-        dfloat* a = side ? p2 : p1;
-        const double alpha = df_to(a[cc]);
-        double beta = alpha, tc = 0.0, scal = 1.0;
-        if (sig > 0.0) {
-          beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-          tc = (beta - alpha) / beta;
-          scal = 1.0 / (alpha - beta);
-        }
-        sc_on[side] = sig > 0.0;
-        sc_tau[side] = df_from(tc);
-        sc_scal[side] = df_from(scal);
-        (side ? tau2 : tau1)[cc] = tc;
-        a[cc] = df_from(beta);
-      }
-      __syncthreads();
-      const int on1 = sc_on[0], on2 = sc_on[1];
-      const dfloat sca1 = sc_scal[0], sca2 = sc_scal[1];
-      for (int r = cc + 1 + threadIdx.x; r < m; r += blockDim.x) {
-        if (on1) p1[r] = df_mul(p1[r], sca1);
-        if (on2) p2[r] = df_mul(p2[r], sca2);
-      }
-      __syncthreads();
-      // the panel's later columns (shared memory), both sides
-      const int n1 = on1 ? w - i - 1 : 0, n2 = on2 ? w - i - 1 : 0;
-      for (int jj = warp; jj < n1 + n2; jj += nw) {
-        const int side = jj < n1 ? 0 : 1;
-        const int j = i + 1 + (side ? jj - n1 : jj);
-        dfloat* b = P + (size_t)(side * pb + j) * m;
-        const dfloat* v = P + (size_t)(side * pb + i) * m;
-        const dfloat bc = b[cc];
-        const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(v, b, cc + 1, m, lane)), bc), sc_tau[side]);
-        if (lane == 0) b[cc] = df_add(bc, make_float2(-d.x, -d.y));
-        df_col_axpy(b, d, v, cc + 1, m, lane);
-      }
-      __syncthreads();
-    }
-    // write the panel back (R on and above the diagonal, reflectors below), then make the
-    // reflectors' structure explicit in P: zeros above the unit diagonal
-    for (int e = threadIdx.x; e < 2 * w * rows; e += blockDim.x) {
-      const int side = e / (w * rows), rem = e - side * w * rows, i = rem / rows, r = c + rem % rows;
-      dfloat* pv = P + (size_t)(side * pb + i) * m + r;
-      (side ? A2 : A1)[(size_t)(c + i) * lda + r] = *pv;
-      if (r <= c + i) *pv = make_float2(r == c + i ? 1.f : 0.f, 0.f);
-    }
-    __syncthreads();
-    // T factors: y_li = V_l^T v_i (l < i), T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] y_{0:i, i}
-    const int npair = w * (w - 1) / 2;
-    for (int q = warp; q < 2 * npair; q += nw) {
-      const int side = q / npair;
-      int t = q - side * npair, i = 1;
-      while (t >= i) { t -= i; ++i; }
-      const int l = t;
-      const dfloat* vl = P + (size_t)(side * pb + l) * m;
-      const dfloat* vi = P + (size_t)(side * pb + i) * m;
-      const dfloat y = df_warp_sum(df_col_dot(vl, vi, c, m, lane));
-      if (lane == 0) ys[side][l + i * QR_PBMAX] = y;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 || threadIdx.x == 32) {
-      const int side = threadIdx.x == 0 ? 0 : 1;
-      const double* tau = side ? tau2 : tau1;
-      dfloat* Tg = (side ? T2 : T1) + (size_t)c * pb;  // panel c / pb: pb x pb at offset (c / pb) pb^2
-      dfloat* Tl = Ts[side];
-      for (int i = 0; i < w; ++i) {
-        const dfloat ti = df_from(tau[c + i]);
-        for (int l = 0; l < i; ++l) {
-          float as = 0.f, ae = 0.f;
-          for (int q = l; q < i; ++q) df_dot_add(as, ae, Tl[l + q * pb], ys[side][q + i * QR_PBMAX]);
-          const dfloat x = df_mul(df_norm(as, ae), ti);
-          Tl[l + i * pb] = make_float2(-x.x, -x.y);
-        }
-        Tl[i + i * pb] = ti;
-        for (int l = i + 1; l < w; ++l) Tl[l + i * pb] = make_float2(0.f, 0.f);
-      }
-      for (int e = 0; e < w * pb; ++e) Tg[e] = Tl[e];
-    }
-    __syncthreads();
-    // columns right of the panel: A <- (I - V T^T V^T) A, rows c..m-1, warp per column, both sides
-    const int nr = K - c - w;
-    for (int jj = warp; jj < 2 * nr; jj += nw) {
-      const int side = jj < nr ? 0 : 1;
-      const int j = c + w + (side ? jj - nr : jj);
-      dfloat* b = (side ? A2 : A1) + (size_t)j * lda;
-      panel_apply_col(b, P + (size_t)side * pb * m, m, c, w, Ts[side], pb, 1, lane);
-    }
-    __syncthreads();
-  }
-}
-
-// B1 <- Q1 B1 and B2 <- Q2 B2 (double-float, ncol columns each) with Qi = H_0 ... H_{K-1} from
-// cta_geqrf_pair_blk (reflectors Ai, T factors Ti of panels of pb columns), panel by panel from the last:
-// B <- B - V_p T_p V_p^T B, the panel's reflectors staged in shared memory P (2 pb m double-floats)
-__device__ void cta_apply_q2_blk(const dfloat* __restrict__ A1, const dfloat* __restrict__ T1, dfloat* __restrict__ B1,
-                                 const dfloat* __restrict__ A2, const dfloat* __restrict__ T2, dfloat* __restrict__ B2,
-                                 int lda, int m, int K, int ldb, int ncol, int pb, dfloat* __restrict__ P) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nref = K < m ? K : m;
-  __shared__ dfloat Ts[2][QR_PBMAX * QR_PBMAX];
-  if (nref <= 0 || ncol <= 0) return;
-  for (int c = ((nref - 1) / pb) * pb; c >= 0; c -= pb) {
-    const int w = nref - c < pb ? nref - c : pb;
-    const int rows = m - c;
-    __syncthreads();  // the previous panel's readers are done
-    for (int e = threadIdx.x; e < 2 * w * rows; e += blockDim.x) {
-      const int side = e / (w * rows), rem = e - side * w * rows, i = rem / rows, r = c + rem % rows;
-      const dfloat a = (side ? A2 : A1)[(size_t)(c + i) * lda + r];
-      P[(size_t)(side * pb + i) * m + r] = r > c + i ? a : make_float2(r == c + i ? 1.f : 0.f, 0.f);
-    }
-    for (int e = threadIdx.x; e < 2 * pb * pb; e += blockDim.x) {
-      const int side = e / (pb * pb), q = e - side * pb * pb;
-      Ts[side][q] = (q < w * pb) ? (side ? T2 : T1)[(size_t)c * pb + q] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int jj = warp; jj < 2 * ncol; jj += nw) {
-      const int side = jj < ncol ? 0 : 1;
-      dfloat* b = (side ? B2 : B1) + (size_t)(side ? jj - ncol : jj) * ldb;
-      panel_apply_col(b, P + (size_t)side * pb * m, m, c, w, Ts[side], pb, 0, lane);
-    }
-  }
-  __syncthreads();
-}
-
 // C[0:m, 0:n] = beta C + alpha op(A) op(B) (op(X) = X^T when tX), column-major, in 64 x 64
 // blocks blk0, blk0 + nblk_step, ... (lower_only: blocks on or below the diagonal), with the
 // products accumulated in double-float (Dot2) on the float32 pipe; inputs are
@@ -665,9 +437,8 @@ __device__ void cta_gemm_nn_thin(int nb, int kb, int ka, double alpha, const dou
 
 // Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
 // singular values > eps.  Returns k (same in all threads).
-__device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, double* Uo,
-                              double* Vo, long long* st, long long info, double* sh, int* shi,
-                              double* flops = nullptr) {
+__device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, const TlrView& v,
+                              int64_t info, long long* st, double* sh, int* shi, double* flops = nullptr) {
   if (K == 0) return 0;
   dfloat* Ud = (dfloat*)w.Up;
   dfloat* Vd = (dfloat*)w.Vp;
@@ -692,9 +463,7 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     Vd[e] = df_from_scaled(w.Vp[e], -w.ev[j]);
   }
   __syncthreads();
-  const size_t tsz = (size_t)(K + QR_PBMAX) * QR_PBMAX;  // T factors of one side
-  if (w.pb > 0) cta_geqrf_pair_blk(Ud, w.tu, w.Tq, Vd, w.tv, w.Tq + tsz, nb, nb, K, w.pb, w.vs);
-  else cta_geqr2_pair_df(Ud, w.tu, Vd, w.tv, nb, nb, K, w.vs);
+  cta_geqr2_pair_df(Ud, w.tu, Vd, w.tv, nb, nb, K, w.vs);
   const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
   // R_u, R_v unscaled to float64 (Ke x K each, upper trapezoid) in the output buffers, then M = R_u R_v^T
   double* Ru = (double*)w.Uq;
@@ -807,6 +576,10 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
     if (!trunc_cap) set_status(st, TLR_ERR_RANK_CAP, info);
     k = kcap;
   }
+  // the tile's columns in the arena (a new block when k exceeds its reservation)
+  if (!cta_lr_reserve(v, info, k, st)) return 0;
+  double* Uo = tileU(v, info);
+  double* Vo = tileV(v, info);
   // U block = Q_M[:, :k] (Ke x k): apply the k reflectors of M to [I_k; 0]
   for (int j = 0; j < k; ++j)
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {
@@ -824,8 +597,7 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from_scaled(Uo[e], 0);
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
-  if (w.pb > 0) cta_apply_q2_blk(Ud, w.Tq, w.Uq, Vd, w.Tq + tsz, w.Vq, nb, nb, Ke, nb, k, w.pb, w.vs);
-  else cta_apply_q2_df(Ud, w.tu, w.Uq, Vd, w.tv, w.Vq, nb, nb, Ke, nb, k, w.vs);
+  cta_apply_q2_df(Ud, w.tu, w.Uq, Vd, w.tv, w.Vq, nb, nb, Ke, nb, k, w.vs);
   __syncthreads();
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) {
     Uo[e] = df_to_scaled(w.Uq[e], 0);

@@ -102,7 +102,7 @@ __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double ta
   }
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, pf);
-  const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, Ut, Vt, st, tt, sh, shi, flops);
+  const int kr = cta_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, flops);
   if (threadIdx.x == 0) v.rank[tt] = kr;
 }
 
@@ -117,15 +117,14 @@ __global__ void __launch_bounds__(256, 3) k_upd_lr_gen(TlrView v, int alg, int k
                                                        const double* __restrict__ d_zeta, double zpow, int Kmax,
                                                        int trunc_cap, double* __restrict__ ws, size_t item_elems,
                                                        long long* __restrict__ st, double* __restrict__ flops,
-                                                       const double* __restrict__ pre, int n_pre, int qr_pb) {
-  extern __shared__ dfloat vs_dyn[];  // staged reflectors / QR panels of the recompression (upd_smem)
+                                                       const double* __restrict__ pre, int n_pre) {
+  extern __shared__ dfloat vs_dyn[];  // 2 nb: staged reflectors of the recompression
   __shared__ double sh[TLR_THREADS / 32 + 2];
   __shared__ int shi[TLR_THREADS / 32 + 2];
   __shared__ int s_item;
   const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
   ItemWs w = item_ws(ws, item_elems, blockIdx.x, v.nb, Kmax, v.kcap);
   w.vs = vs_dyn;
-  w.pb = qr_pb;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
     __syncthreads();
@@ -322,7 +321,7 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
   const int k = cta_aca(de, nb, nb, nb, tau * 0.125, aca_max, w, dsm, sh, shi, &conv);
   if (!conv && !trunc_cap && threadIdx.x == 0) set_status(st, TLR_ERR_RANK_CAP, tt);
   __syncthreads();
-  const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, tileU(v, tt), tileV(v, tt), st, tt, sh, shi);
+  const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, v, tt, st, sh, shi);
   if (threadIdx.x == 0) v.rank[tt] = kr;
 }
 
@@ -363,23 +362,8 @@ __global__ void k_copy_back(const GemmGen* __restrict__ desc, double* const* __r
     X[e] = g.C[e];
 }
 
-// panel width of the blocked QR in the low-rank update kernel: QR_PBMAX while its two panels
-// (16 pb nb bytes) stay within 160 KB of shared memory, narrower for larger tiles; the environment
-// variable TLR_QR_PANEL (0 .. QR_PBMAX, 0: column-by-column QR) overrides it
-int upd_qr_pb(int nb) {
-  static int env = -2;
-  if (env == -2) {
-    const char* e = getenv("TLR_QR_PANEL");
-    env = e ? atoi(e) : -1;
-  }
-  if (env >= 0) return std::min(env, QR_PBMAX);
-  const int pb = (int)((size_t)160 * 1024 / (16 * (size_t)std::max(nb, 1)));
-  return std::max(1, std::min(pb, QR_PBMAX));
-}
-
-// dynamic shared memory of the persistent low-rank update kernel: two panels of the blocked QR
-// (or two staged reflectors of the column-by-column QR)
-size_t upd_smem(int nb) { return 2 * (size_t)nb * sizeof(dfloat) * std::max(upd_qr_pb(nb), 1); }
+// dynamic shared memory of the persistent low-rank update kernel (two staged reflectors)
+size_t upd_smem(int nb) { return 2 * (size_t)nb * sizeof(dfloat); }
 
 // resident CTAs of the persistent low-rank update kernel on the current device for tile size nb
 // (remembered per device and tile size; handles on several host threads may use different sizes)
@@ -412,6 +396,8 @@ int chunk_of(const tlr_ctx* h, size_t per_item, size_t reserve) {
 }
 
 }  // namespace
+
+int tops_resident_ctas(int nb) { return resident_ctas(nb); }
 
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip) {
   if (count <= 0) return TLR_OK;
@@ -549,8 +535,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
                                                             2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie,
                                                             h->d_stat, g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr,
                                                             staged ? h->dop : nullptr,
-                                                            staged ? (int)std::min(n_dop, n_lr) : 0,
-                                                            upd_qr_pb(h->nb));
+                                                            staged ? (int)std::min(n_dop, n_lr) : 0);
     TLR_LAUNCH_CHECK();
     if (g_tlr_prof.enabled) tlr_prof_end(s);
   }

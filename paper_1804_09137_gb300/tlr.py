@@ -42,7 +42,7 @@ _lib = None
 
 EXPORTS = ["tlr_create", "tlr_destroy", "tlr_matern_generate", "tlr_compress", "tlr_potrf", "tlr_loglik",
            "tlr_loglik_grad", "tlr_predict", "tlr_sample", "tlr_status", "tlr_rank_stats", "tlr_shape",
-           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
+           "tlr_get_tile", "tlr_get_perm", "tlr_tile_counts", "tlr_launch_count", "tlr_profile", "tlr_inverse_stats", "tlr_memory", "tlr_profile_phases", "tlr_loglik_dense_noalloc",
            "tlr_loglik_grad_batched", "tlr_predict_var",
            "tlr_profile_read", "tlr_gemm_tc", "tlr_profile_read_tc"]
 
@@ -74,6 +74,7 @@ def lib():
     L.tlr_tile_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.tlr_launch_count.argtypes = [C.POINTER(i64)]
     L.tlr_inverse_stats.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(i64)]
+    L.tlr_memory.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     L.tlr_profile.argtypes = [C.c_int]
     L.tlr_loglik_grad_batched.argtypes = [C.c_int, C.POINTER(i64), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                           C.POINTER(TlrTheta), C.POINTER(TlrOpts), vp, vp, C.POINTER(C.c_int),
@@ -218,6 +219,12 @@ class Handle:
         _check("tlr_inverse_stats", lib().tlr_inverse_stats(self._h, C.byref(kmin), C.byref(kmean), C.byref(kmax),
                                                             C.byref(nd)))
         return {"kmin": kmin.value, "kmean": kmean.value, "kmax": kmax.value, "dense": nd.value}
+
+    def memory(self):
+        """Device bytes held by the handle: total, low-rank arenas, their used part, workspaces."""
+        v = [C.c_int64() for _ in range(4)]
+        _check("tlr_memory", lib().tlr_memory(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("total", "arenas", "arena_used", "workspace"), (x.value for x in v)))
 
     def get_perm(self):
         p = torch.zeros(self.n, dtype=torch.int32, device=self.dev)

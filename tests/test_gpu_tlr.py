@@ -94,6 +94,31 @@ def test_loglik_small_eps_matches_dense(T, theta):
     assert abs(out[2] - q) <= 1e-8 * abs(q)
 
 
+def test_arena_grows_and_results_stay_exact(T):
+    """At eps = 1e-13 with dense_rank 80 the ranks outgrow the low-rank arena's starting size (32 columns a
+    tile): compression and the factorization enlarge it and repeat, and l and the gradient still match
+    the exact oracle."""
+    theta = (1.0, 0.1, 0.5)
+    x, y, z = problem(26, theta, n=650)
+    ll_ref, g_ref = DN.loglik_grad(x, y, z, theta)
+    h = T.Handle(dev(x), dev(y), nb=96, eps=1e-13, rank_cap=96, dense_rank=80)
+    m0 = h.memory()
+    h.factor(theta)
+    ll, g = h.loglik_grad(dev(z))
+    h.check()
+    m1 = h.memory()
+    assert h.rank_stats()["kmax"] > 32 and m1["arenas"] > m0["arenas"], (h.rank_stats(), m0, m1)
+    assert 0 < m1["arena_used"] <= m1["arenas"] < m1["total"]
+    ll, g = ll.cpu().numpy()[0], g.cpu().numpy()
+    assert abs(ll - ll_ref) <= 1e-9 * abs(ll_ref)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-6 * np.max(np.abs(g_ref)))
+    # a second evaluation on the enlarged arena gives the same numbers bit for bit
+    h.factor(theta)
+    ll2, g2 = h.loglik_grad(dev(z))
+    assert ll2.cpu().numpy()[0] == ll and np.array_equal(g2.cpu().numpy(), g)
+    h.close()
+
+
 @pytest.mark.parametrize("dense_rank", [4, 16, 120])
 def test_dense_threshold_does_not_change_result(T, dense_rank):
     theta = (1.0, 0.3, 1.0)
