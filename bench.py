@@ -82,10 +82,12 @@ def args_():
     p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tlr", choices=["tlr", "reference"])
-    p.add_argument("--workload", default="n90k", choices=["n90k", "regions", "n40k", "accuracy", "accuracy36k", "config4"],
+    p.add_argument("--workload", default="n90k",
+                   choices=["n90k", "regions", "n40k", "accuracy", "accuracy36k", "config4", "mc"],
                    help="n90k: the n = 90,000 TLR likelihood + gradient (default); regions: 512 independent "
                         "regions; n40k: TLR vs dense likelihood at n = 40,000 and kriging of 10% held out")
     p.add_argument("--regions", type=int, default=512)
+    p.add_argument("--mc-reps", type=int, default=2, help="replicates per beta of the reduced Monte Carlo")
     p.add_argument("--workers", type=int, default=8)
     p.add_argument("--side", type=int, default=300)
     p.add_argument("--nb", type=int, default=900)
@@ -289,6 +291,67 @@ def run_regions(a):
                        "l2": "inputs larger than L2"},
             "gpu_launches": int(T.launch_count() - l0), "clocks": clk,
             "result": {"failures": int(sum(v != 0 for v in st)), "ll_sum": float(ll.sum().item())}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mc(a):
+    """Reduced Monte Carlo of the maximum-likelihood estimate (Sec. VIII-D1): the 200 x 200 jittered grid
+    with 10% held out (n = 36,000 observed), theta0 = (1, beta, 0.5) for beta in {0.03, 0.1, 0.3},
+    --mc-reps replicates each with z drawn from the exact model (dense float64 factor of this library).
+    theta_hat by L-BFGS-B with the TLR likelihood and gradient (nb = 800, eps = 1e-9, rank cap 200) from a
+    fixed start, then by the dense float64 path started at the TLR estimate; reports both estimates,
+    their relative differences, the evaluations and the times."""
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_1804_09137_gb300 import inputs, mle
+    from paper_1804_09137_gb300 import tlr as T
+
+    dev = torch.device("cuda")
+    t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
+    x, y = inputs.jittered_grid(200)
+    obs, _ = inputs.holdout(len(x), len(x) // 10)
+    xo, yo = t64(x[obs]), t64(y[obs])
+    n = len(obs)
+    hd = T.Handle(xo, yo, nb=800, eps=-1.0)
+    ht = T.Handle(xo, yo, nb=800, eps=1e-9, rank_cap=200)
+    out = []
+    for beta in (0.03, 0.1, 0.3):
+        theta0 = (1.0, beta, 0.5)
+        hd.factor(theta0)
+        hd.check()
+        for r in range(a.mc_reps):
+            z = hd.sample(t64(inputs.standard_normal(n, seed=inputs.SEED + 1000 + r)))
+            start = (0.7, 1.5 * beta, 0.7)
+            t0 = time.perf_counter()
+            th_t, ll_t, info_t = mle.fit(ht, z, start, ftol=1e-12, gtol=1e-5)
+            t_t = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            th_d, ll_d, info_d = mle.fit(hd, z, th_t, ftol=1e-12, gtol=1e-5)
+            t_d = time.perf_counter() - t0
+            rel = [float(v) for v in np.abs(th_t - th_d) / np.abs(th_d)]
+            rec = {"beta": beta, "rep": r, "theta_tlr": [float(v) for v in th_t], "theta_dense": [float(v) for v in th_d],
+                   "rel_diff": rel, "loglik_tlr": ll_t, "loglik_dense": ll_d, "evals_tlr": info_t["evals"],
+                   "evals_dense": info_d["evals"], "seconds_tlr": t_t, "seconds_dense": t_d}
+            log("mc", rec)
+            out.append(rec)
+            # re-factor the dense handle at theta0 for the next draw
+            hd.factor(theta0)
+    ht.close()
+    hd.close()
+    worst = max(max(r["rel_diff"]) for r in out)
+    summary = {}
+    for beta in (0.03, 0.1, 0.3):
+        th = np.array([r["theta_tlr"] for r in out if r["beta"] == beta])
+        summary[str(beta)] = {"mean_theta_tlr": th.mean(axis=0).tolist(), "std_theta_tlr": th.std(axis=0).tolist()}
+    line = {"metric": "reduced Monte Carlo of theta_hat: TLR vs dense float64 MLE at n = 36,000",
+            "value": worst, "unit": "max relative difference of theta_hat components", "n_gpus": 1,
+            "higher_is_better": False, "data": "synthetic (z from the exact model)",
+            "config": {"workload": "mc_n36000_nb800_eps1e-9_cap200", "n": n, "reps_per_beta": a.mc_reps,
+                       "betas": [0.03, 0.1, 0.3]},
+            "within_1pct": bool(worst <= 0.01), "summary": summary, "runs": out}
     print(json.dumps(line), flush=True)
 
 
@@ -542,6 +605,8 @@ def main():
         return run_n40k(a)
     if a.workload == "accuracy36k" and a.impl != "reference":
         return run_accuracy36k(a)
+    if a.workload == "mc" and a.impl != "reference":
+        return run_mc(a)
     if a.workload == "config4" and a.impl != "reference":
         return run_config4(a)
     if a.impl == "reference":
@@ -698,6 +763,16 @@ def main():
            "d2h_bytes_per_step": int(out_h.numel() * 8)}
 
     result = out_h.numpy().copy()
+    # prediction variance at 4,000 new points (batched multi-right-hand-side solve), after the timed region
+    xv, yv = inputs.uniform_points(4000, seed=inputs.SEED + 11)
+    xv, yv = (torch.tensor(v, dtype=torch.float64, device=dev) for v in (xv, yv))
+    torch.cuda.synchronize()
+    t_var = time.perf_counter()
+    var4k = h.predict_var(xv, yv)
+    torch.cuda.synchronize()
+    t_var = time.perf_counter() - t_var
+    h.check()
+    pred_var = {"points": 4000, "seconds": t_var, "min": float(var4k.min().item()), "max": float(var4k.max().item())}
     ranks = h.rank_stats()
     counts = h.tile_counts()
     inv = h.inverse_stats()
@@ -753,6 +828,7 @@ def main():
             "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "dense_fp64_gpu": dense, "accuracy": accuracy, "deterministic_across_steps": deterministic,
             "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes), "handle": mem},
+            "prediction_variance": pred_var,
             "result": {"loglik": float(result[0]), "grad": [float(v) for v in result[1:4]], "ranks": ranks,
                        "tiles": counts, "inverse": inv}}
     print(json.dumps(line), flush=True)

@@ -153,8 +153,10 @@ int tlr_predict(tlr_handle h, const double* z_obs, int64_t m, const double* x_ne
  * covariance Sigma_11 - Sigma_12 Sigma_22^{-1} Sigma_21, its diagonal):
  * var_new[i] = sigma2 - |L^{-1} sigma_i|^2 with sigma_i the covariances between
  * new point i and the observed points, L the handle's factor.  x_new, y_new:
- * m doubles each; var_new: m doubles (device).  One tile forward solve on the
- * same factor per new point (sigma_i generated on the fly). */
+ * m doubles each; var_new: m doubles (device).  Up to 1,024 new points at a
+ * time: their covariance columns are generated and L^{-1} applied to all of
+ * them by one batched tile forward solve (three batched GEMM launches per
+ * tile column, workspace from the handle). */
 int tlr_predict_var(tlr_handle h, int64_t m, const double* x_new, const double* y_new,
                     double* var_new, tlr_stream_t stream);
 

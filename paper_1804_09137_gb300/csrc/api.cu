@@ -219,6 +219,49 @@ int bind_points(tlr_ctx* h, int64_t n, const std::vector<double>& hx, const std:
 }  // namespace
 
 // Allocate a handle with capacity for cap points (not yet bound to points).
+size_t tlr_scratch_want(const tlr_ctx* h) {
+  const size_t nb = h->nb;
+  const int64_t ct = h->cap_ntiles;
+  // workspace: low-rank update items, SYRK items, table nodes, gradient partials
+  const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap, h->kws);
+  const int64_t max_items = std::max<int64_t>(ct, 1);
+  // one item workspace per resident CTA of the persistent update kernel (compression takes as many tiles
+  // a launch)
+  const int64_t chunk = std::min<int64_t>(max_items, h->dense ? 912 : std::max(tops_resident_ctas(h->nb), 64));
+  size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
+  ws = std::max(ws, (size_t)chunk * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
+  ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->cap_nt * (h->cap_nt + 1) / 2 + 16));
+  // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
+  const size_t mb = (nb + 63) / 64;
+  ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->cap_nt * (h->cap_nt + 1) / 2 + 1024));
+  ws = std::max(ws, 2 * nb * nb + 4096);
+  // the inverse's stacked-panel products on the tensor cores: slices of one nb x nb x nb product
+  // next to two nb x nb panels and their descriptors
+  if (tlr_tc_slices_opt(h) > 0) {
+    const int S = tlr_tc_slices_opt(h);
+    const size_t tc = (oz_slices_elems(h->nb, h->nb, OZ_BM, S) + oz_slices_elems(h->nb, h->nb, OZ_BN, S)) / 4 +
+                      2 * nb * nb + 3 * (size_t)h->cap_nt * 64 + 65536;
+    ws = std::max(ws, tc);
+  }
+  return ws;
+}
+
+int tlr_widen(tlr_ctx* h) {
+  h->kws = 2 * h->kcap;
+  const size_t want = tlr_scratch_want(h);
+  if (want <= h->scratch_elems) return TLR_OK;
+  TLR_CUDA_TRY(cudaDeviceSynchronize());
+  cudaFree(h->scratch);
+  h->scratch = nullptr;
+  h->scratch_elems = 0;
+  if (cudaMalloc((void**)&h->scratch, want * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    TLR_RETURN_OOM();
+  }
+  h->scratch_elems = want;
+  return TLR_OK;
+}
+
 int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   tlr_ctx* h = new tlr_ctx();
   memset(h, 0, sizeof(*h));
@@ -245,7 +288,9 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->D, (size_t)h->cap_nt * nb * nb);
   // rank-packed arenas: room for 32 columns a tile to start with; compression, the factorization and
   // the inverse enlarge them (and repeat) when the ranks need more
-  h->kws = 2 * h->kcap;
+  // update workspaces for concatenated ranks up to kws (widened to 2 kcap, and the step repeated, when
+  // a larger one occurs); never below what compression's cross approximation may take
+  h->kws = std::min(2 * h->kcap, std::max(h->kcap, h->dense_rank + 8));
   h->arena = h->dense ? 1 : std::max<int64_t>(ct, 1) * (int64_t)nb * std::min(h->kcap, 32);
   rc |= dmalloc(&h->U, (size_t)h->arena);
   rc |= dmalloc(&h->V, (size_t)h->arena);
@@ -262,29 +307,8 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->d_vec, 4 * (size_t)cnp);
   h->red_len = 2 * h->cap_nt + 64;
   rc |= dmalloc(&h->d_red, h->red_len);
-  // workspace: low-rank update items, SYRK items, table nodes, gradient partials
-  const size_t ie = h->dense ? 0 : tlr_item_elems(h->nb, h->kcap);
-  const int64_t max_items = std::max<int64_t>(ct, 1);
-  // one item workspace per resident CTA of the persistent update kernel (compression takes as many tiles
-  // a launch)
-  const int64_t chunk = std::min<int64_t>(max_items, h->dense ? 912 : std::max(tops_resident_ctas(h->nb), 64));
-  size_t ws = std::max<size_t>((size_t)chunk * ie, (size_t)TAB_ELEMS);
-  ws = std::max(ws, (size_t)chunk * (nb * h->kcap + (size_t)h->kcap * h->kcap + 8));
-  ws = std::max(ws, (size_t)(2 * 8 * (int64_t)h->cap_nt * (h->cap_nt + 1) / 2 + 16));
-  // gradient partials: 3 per 64 x 64 block of the lower triangle; dense diagonal-tile workspace
-  const size_t mb = (nb + 63) / 64;
-  ws = std::max(ws, (size_t)(3 * mb * mb * (size_t)h->cap_nt * (h->cap_nt + 1) / 2 + 1024));
-  ws = std::max(ws, 2 * nb * nb + 4096);
-  // the inverse's stacked-panel products on the tensor cores: slices of one nb x nb x nb product
-  // next to two nb x nb panels and their descriptors
-  if (tlr_tc_slices_opt(h) > 0) {
-    const int S = tlr_tc_slices_opt(h);
-    const size_t tc = (oz_slices_elems(h->nb, h->nb, OZ_BM, S) + oz_slices_elems(h->nb, h->nb, OZ_BN, S)) / 4 +
-                      2 * nb * nb + 3 * (size_t)h->cap_nt * 64 + 65536;
-    ws = std::max(ws, tc);
-  }
-  h->scratch_elems = ws;
-  rc |= dmalloc(&h->scratch, ws);
+  h->scratch_elems = tlr_scratch_want(h);
+  rc |= dmalloc(&h->scratch, h->scratch_elems);
   if (rc != TLR_OK) {
     free_ctx(h);
     TLR_RETURN_OOM();
@@ -300,7 +324,7 @@ int tlr_arena_alloc(double** U, double** V, int64_t* arena, int64_t need) {
   if (*V) cudaFree(*V);
   *U = *V = nullptr;
   *arena = 0;
-  const int64_t want = need + need / 4;
+  const int64_t want = need;
   if (cudaMalloc((void**)U, (size_t)want * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)V, (size_t)want * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -319,13 +343,22 @@ int tlr_take_grow(tlr_ctx* h, cudaStream_t s, const unsigned long long* d_top, i
   TLR_CUDA_TRY(cudaMemcpyAsync(&top, d_top, sizeof(top), cudaMemcpyDeviceToHost, s));
   TLR_CUDA_TRY(cudaStreamSynchronize(s));
   *need = 0;
-  if (st[ST_CODE] != TLR_ST_GROW) return TLR_OK;
+  if (st[ST_CODE] != TLR_ST_GROW && st[ST_CODE] != TLR_ST_WIDEN) return TLR_OK;
   TLR_CUDA_TRY(cudaMemsetAsync(h->d_stat, 0, 4 * sizeof(long long), s));
-  *need = (int64_t)top;  // every block asked for, the failed ones included
+  // every block asked for, the failed ones included; -1: the update workspaces were too narrow
+  *need = st[ST_CODE] == TLR_ST_WIDEN ? -1 : (int64_t)top;
   return TLR_OK;
 }
 
 namespace {
+// after an arena ran out (need > 0: the entries asked for) or an update workspace was too narrow
+// (need < 0): the arena half as large again as asked for (at least 1.5 times its size), or the widest
+// workspaces
+int tlr_enlarge(tlr_ctx* h, int64_t need) {
+  if (need < 0) return tlr_widen(h);
+  return tlr_arena_alloc(&h->U, &h->V, &h->arena, std::max(need + need / 2, h->arena + h->arena / 2));
+}
+
 // compression into a fresh arena: every tile starts without columns
 int compress_fresh(tlr_ctx* h, double eps, cudaStream_t s) {
   if (h->ntiles <= 0) return TLR_OK;
@@ -342,7 +375,7 @@ int compress_grow(tlr_ctx* h, double eps, cudaStream_t s) {
     TRY(tlr_take_grow(h, s, h->top, &need));
     if (need == 0) return TLR_OK;
     if (attempt >= 4) TLR_RETURN_OOM();
-    TRY(tlr_arena_alloc(&h->U, &h->V, &h->arena, std::max(need, 2 * h->arena)));
+    TRY(tlr_enlarge(h, need));
   }
 }
 }  // namespace
@@ -456,7 +489,7 @@ int tlr_potrf(tlr_handle h, tlr_stream_t stream) {
     TRY(tlr_take_grow(h, s, h->top, &need));
     if (need == 0) break;
     if (attempt >= 4) TLR_RETURN_OOM();
-    TRY(tlr_arena_alloc(&h->U, &h->V, &h->arena, std::max(need, 2 * h->arena)));
+    TRY(tlr_enlarge(h, need));
     TRY(tlr_gen_diag(h, s));
     TRY(compress_grow(h, h->opts.eps, s));
     TRY(tlr_plan(h, s));

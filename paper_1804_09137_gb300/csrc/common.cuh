@@ -49,6 +49,9 @@
 // internal status code (never returned to a caller): a low-rank arena or an update workspace was too
 // small; the host enlarges it and repeats the operation
 #define TLR_ST_GROW 100
+// internal status code: an update item's concatenated rank exceeded the workspaces' bound h->kws; the host
+// widens the workspaces to the largest possible (2 kcap) and repeats the operation
+#define TLR_ST_WIDEN 101
 
 struct MaternParams {
   double sigma2, beta, nu;
@@ -349,9 +352,15 @@ int tops_resident_ctas(int nb);
 // after a synchronisation: *need = the entries the arena counter d_top asked for when an arena or a
 // workspace ran out during the work enqueued so far (status reset), else 0
 int tlr_take_grow(tlr_ctx* h, cudaStream_t s, const unsigned long long* d_top, int64_t* need);
+// after tlr_take_grow reported a workspace bound exceeded (*need < 0): widen kws to 2 kcap and grow the
+// workspace
+int tlr_widen(tlr_ctx* h);
 int tlr_rebind(tlr_ctx* h, int64_t n, const double* x, const double* y, cudaStream_t s);
 int tlr_alloc(int64_t cap_n, const tlr_opts* opts, tlr_ctx** out);
-size_t tlr_item_elems(int nb, int kcap);
+// workspace (doubles) of one low-rank update item for concatenated ranks up to kws
+size_t tlr_item_elems(int nb, int kcap, int kws);
+// batched-kernel workspace the handle needs for its tile size, rank cap and update bound kws
+size_t tlr_scratch_want(const tlr_ctx* h);
 int tlr_potrf_tile(tlr_ctx* h, double* A, int lda, int nb, int64_t col0, cudaStream_t s);
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s);
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s);

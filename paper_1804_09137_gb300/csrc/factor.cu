@@ -115,8 +115,8 @@ __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
 
 }  // namespace
 
-size_t tlr_item_elems(int nb, int kcap) {
-  const size_t Kmax = 2 * (size_t)kcap;
+size_t tlr_item_elems(int nb, int kcap, int kws) {
+  const size_t Kmax = (size_t)kws;
   return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax;
 }
 
@@ -128,8 +128,8 @@ static int chunk_for(const tlr_ctx* h, size_t per_item, size_t reserve = 0) {
 }
 
 int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s) {
-  const int nb = h->nb, kcap = h->kcap, Kmax = 2 * kcap;
-  const size_t ie = tlr_item_elems(nb, kcap);
+  const int nb = h->nb, kcap = h->kcap, Kmax = h->kws;
+  const size_t ie = tlr_item_elems(nb, kcap, h->kws);
   const int chunk = chunk_for(h, ie);
   if (chunk < 1) TLR_RETURN_OOM();
   const size_t smem = 2 * (size_t)nb * sizeof(double) + (size_t)nb * sizeof(int);

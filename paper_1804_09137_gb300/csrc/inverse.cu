@@ -169,7 +169,7 @@ static int zplan(tlr_ctx* h, cudaStream_t s) {
       zc[t] = c;
       pos += (int64_t)c * h->nb;
     }
-    const int64_t need = h->dense ? 1 : 3 * pos + std::max<int64_t>(T, 1) * h->nb * 8;
+    const int64_t need = h->dense ? 1 : 2 * pos + std::max<int64_t>(T, 1) * h->nb * 16;
     if (need > h->arenaz) {
       TLR_CUDA_TRY(cudaStreamSynchronize(s));
       ZTRY_OOM(tlr_arena_alloc(&h->Uz, &h->Vz, &h->arenaz, need));
@@ -715,8 +715,8 @@ struct InverseScope {  // marks the handle as forming the inverse for the scope'
 };
 }  // namespace
 
-// one attempt; *grow > 0 (the entries Z's arena was asked for) when TRTRI ran out of arena, and then
-// the caller enlarges it and starts again
+// one attempt; *grow > 0 (the entries Z's arena was asked for) when TRTRI ran out of arena, -1 when an
+// update workspace was too narrow, and then the caller enlarges it and starts again
 static int inverse_once(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, int* fused, int64_t* grow) {
   *grow = 0;
   ZTRY(ensure_z(h));
@@ -818,6 +818,7 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3, i
     ZTRY(inverse_once(h, s, alpha, out3, fused, &grow));
     if (grow == 0) return TLR_OK;
     if (attempt >= 4) TLR_RETURN_OOM();
-    ZTRY(tlr_arena_alloc(&h->Uz, &h->Vz, &h->arenaz, std::max(grow, 2 * h->arenaz)));
+    if (grow < 0) ZTRY(tlr_widen(h));
+    else ZTRY(tlr_arena_alloc(&h->Uz, &h->Vz, &h->arenaz, std::max(grow + grow / 2, h->arenaz + h->arenaz / 2)));
   }
 }

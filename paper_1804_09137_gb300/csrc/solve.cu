@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "tile.cuh"
+#include "tileops.h"
 
 namespace {
 
@@ -294,6 +295,46 @@ __global__ void k_colvar(const double* __restrict__ W, int64_t ldw, int64_t rows
   if (threadIdx.x == 0) var[blockIdx.x] = sigma2 - acc;
 }
 
+// Step k of the batched forward solve W = L^{-1} C (C consumed, both npad x mb, column-major, ld):
+// d0: W_k = L_kk^{-1} C_k with the diagonal tile's explicit inverse; for the block rows i > k
+// (thread i - k - 1): low rank  d1: T_i = V_ik^T W_k (rank x mb in Tb, ld kcap), d2: C_i -= U_ik T_i;
+// dense  d1 empty, d2: C_i -= A_ik W_k.  Every product writes a block of its own (no operand is
+// written by a product of the same stage).
+__global__ void k_msolve_desc(TlrView v, int k, const double* __restrict__ linv_k, int mb, double* __restrict__ C,
+                              double* __restrict__ W, int64_t ld, double* __restrict__ Tb, GemmGen* __restrict__ d0,
+                              GemmGen* __restrict__ d1, GemmGen* __restrict__ d2) {
+  const int nb = v.nb;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  GemmGen g;
+  g.A = g.B = nullptr; g.C = nullptr; g.m = g.n = g.k = 0; g.lda = g.ldb = nb; g.ldc = (int)ld;
+  g.tA = g.tB = 0; g.alpha = 1.0; g.beta = 0.0; g.lower = 0;
+  if (q == 0) {
+    GemmGen x = g;
+    x.A = linv_k; x.B = C + (size_t)k * nb; x.ldb = (int)ld; x.C = W + (size_t)k * nb;
+    x.m = nb; x.n = mb; x.k = nb;
+    *d0 = x;
+  }
+  const int i = k + 1 + q;
+  if (i >= v.nt) return;
+  const int64_t t = dtile_index(i, k);
+  const double* Wk = W + (size_t)k * nb;
+  double* Ci = C + (size_t)i * nb;
+  GemmGen a = g, b = g;
+  b.C = Ci; b.m = nb; b.n = mb; b.alpha = -1.0; b.beta = 1.0; b.ldb = (int)ld;
+  if (v.dslot[t] >= 0) {
+    b.A = tileA(v, t); b.B = Wk; b.k = nb;
+  } else {
+    const int r = v.rank[t];
+    double* Ti = Tb + (size_t)(i - k - 1) * v.kcap * mb;
+    if (r > 0) {
+      a.A = tileV(v, t); a.tA = 1; a.B = Wk; a.ldb = (int)ld; a.C = Ti; a.ldc = v.kcap; a.m = r; a.n = mb; a.k = nb;
+      b.A = tileU(v, t); b.B = Ti; b.ldb = v.kcap; b.k = r;
+    }
+  }
+  d1[q] = a;
+  d2[q] = b;
+}
+
 }  // namespace
 
 int tlr_permute_in(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) {
@@ -387,19 +428,51 @@ int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const do
 }
 
 
-// Prediction variance at m new points (sorted-order observations): for each new point
-// w = L^{-1} sigma_i by the tile forward solve of the likelihood (sigma_i generated on the
-// fly), var_i = sigma2 - |w|^2.
+#define TRY_RC(x)                  \
+  do {                             \
+    int rc_ = (x);                 \
+    if (rc_ != TLR_OK) return rc_; \
+  } while (0)
+
+// Prediction variance at m new points (sorted-order observations), mb points at a time: the
+// covariances C = Sigma_{obs,new} (npad x mb, generated), W = L^{-1} C by the batched tile forward solve
+// (three batched GEMM launches per block column), var_j = sigma2 - |W[:, j]|^2.
 int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s) {
+  const int nt = h->nt, nb = h->nb;
   const int64_t npad = h->npad;
-  double* w = h->d_vec + 2 * npad;  // the third work vector (the first two hold a = Sigma^{-1} z and L^{-1} z)
-  const dim3 gcov((unsigned)std::min<int64_t>((npad + 255) / 256, 64), 1);
-  for (int64_t i = 0; i < m; ++i) {
-    k_cov_block<<<gcov, 256, 0, s>>>(h->tab, h->mp, h->x, h->y, h->n, npad, xn + i, yn + i, w, npad);
+  const size_t nn = (size_t)nb * nb;
+  // the last diagonal tile's inverse (the Cholesky forms the others)
+  TRY_RC(tops_trinv(h->D + (size_t)(nt - 1) * nn, nb, h->linv + (size_t)(nt - 1) * nn, s));
+  // workspace: descriptors, then per right-hand side C, W (npad each) and the thin products (nt kcap)
+  const size_t gd = (sizeof(GemmGen) + 7) / 8;
+  const size_t desc = (1 + 2 * (size_t)nt) * gd + 16;
+  const size_t per = 2 * (size_t)npad + (size_t)nt * h->kcap;
+  if (h->scratch_elems <= desc + per) TLR_RETURN_OOM();
+  const int64_t mb = std::min<int64_t>(std::min<int64_t>(m, 1024), (int64_t)((h->scratch_elems - desc) / per));
+  GemmGen* d0 = (GemmGen*)h->scratch;
+  GemmGen* d1 = (GemmGen*)(h->scratch + gd);
+  GemmGen* d2 = (GemmGen*)(h->scratch + (1 + (size_t)nt) * gd);
+  double* C = h->scratch + desc;
+  double* W = C + (size_t)npad * mb;
+  double* Tb = W + (size_t)npad * mb;
+  const TlrView v = view_of(h);
+  for (int64_t j0 = 0; j0 < m; j0 += mb) {
+    const int cnt = (int)std::min<int64_t>(mb, m - j0);
+    k_cov_block<<<dim3((unsigned)std::min<int64_t>((npad + 255) / 256, 64), (unsigned)cnt), 256, 0, s>>>(
+        h->tab, h->mp, h->x, h->y, h->n, npad, xn + j0, yn + j0, C, npad);
     TLR_LAUNCH_CHECK();
-    int rc = tlr_fwd_solve(h, w, s);
-    if (rc) return rc;
-    k_colvar<<<1, 256, 0, s>>>(w, npad, npad, h->mp.sigma2, var + i);
+    for (int k = 0; k < nt; ++k) {
+      const int rows = nt - k - 1;
+      k_msolve_desc<<<(unsigned)(rows / 128 + 1), 128, 0, s>>>(v, k, h->linv + (size_t)k * nn, cnt, C, W, npad, Tb,
+                                                                d0, d1, d2);
+      TLR_LAUNCH_CHECK();
+      TRY_RC(tops_gemm(d0, 1, nb, cnt, s));
+      if (rows > 0) {
+        TRY_RC(tops_gemm(d1, rows, h->kcap, cnt, s));
+        TRY_RC(tops_gemm(d2, rows, nb, cnt, s));
+      }
+    }
+    k_colvar<<<(unsigned)cnt, 256, 0, s>>>(W, npad, npad, h->mp.sigma2, var + j0);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;

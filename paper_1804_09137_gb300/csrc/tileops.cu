@@ -63,6 +63,12 @@ __device__ void upd_lr_item(const TlrView& v, int alg, int k, int2 it, double ta
     return;
   }
   const int k0 = v.rank[tt];
+  // the concatenated rank must fit the workspace (else the host widens it and repeats the step)
+  const int rin = X.dense ? Y.k : (Y.dense ? X.k : min(X.k, Y.k));
+  if (k0 + rin > Kmax) {
+    if (threadIdx.x == 0) set_status(st, TLR_ST_WIDEN, tt);
+    return;
+  }
   double* Ut = tileU(v, tt);
   double* Vt = tileV(v, tt);
   for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) { w.Up[e] = Ut[e]; w.Vp[e] = Vt[e]; }
@@ -319,7 +325,12 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
   DenseEntry de{bufs + (size_t)blockIdx.x * nb * nb, nb};
   int conv = 0;
   const int k = cta_aca(de, nb, nb, nb, tau * 0.125, aca_max, w, dsm, sh, shi, &conv);
-  if (!conv && !trunc_cap && threadIdx.x == 0) set_status(st, TLR_ERR_RANK_CAP, tt);
+  if (!conv && threadIdx.x == 0) {
+    // below the widest workspace the host widens it and repeats; at it, the rank cap was exceeded
+    if (aca_max < 2 * v.kcap) set_status(st, TLR_ST_WIDEN, tt);
+    else if (!trunc_cap) set_status(st, TLR_ERR_RANK_CAP, tt);
+  }
+  if (!conv && aca_max < 2 * v.kcap) return;
   __syncthreads();
   const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, v, tt, st, sh, shi);
   if (threadIdx.x == 0) v.rank[tt] = kr;
@@ -518,7 +529,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
   }
   if (n_lr > 0) {
     PhaseScope ps("update.lowrank_target", s);
-    const size_t ie = tlr_item_elems(h->nb, h->kcap);
+    const size_t ie = tlr_item_elems(h->nb, h->kcap, h->kws);
     const int chunk = chunk_of(h, ie, 0);
     if (chunk < 1) TLR_RETURN_OOM();
     const int slots = std::max(resident_ctas(h->nb) - std::max(reserve, 0), 1);
@@ -532,7 +543,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     TLR_CUDA_TRY(cudaMemsetAsync(h->d_ctr, 0, sizeof(int), s));
     if (g_tlr_prof.enabled) tlr_prof_begin(s);
     k_upd_lr_gen<<<grid, TLR_THREADS, upd_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
-                                                            2 * h->kcap, h->opts.truncate_at_cap, h->scratch, ie,
+                                                            h->kws, h->opts.truncate_at_cap, h->scratch, ie,
                                                             h->d_stat, g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr,
                                                             staged ? h->dop : nullptr,
                                                             staged ? (int)std::min(n_dop, n_lr) : 0);
@@ -545,7 +556,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
 size_t tops_dd_item_elems(const tlr_ctx* h) {
   // the item's product, recompression buffers and descriptors, its tensor-core slices (if any) and alignment
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
-  return (size_t)h->nb * h->nb + tlr_item_elems(h->nb, h->kcap) + 2 * gd + tc_item_doubles(h, h->nb, h->nb, h->nb) +
+  return (size_t)h->nb * h->nb + tlr_item_elems(h->nb, h->kcap, h->kws) + 2 * gd + tc_item_doubles(h, h->nb, h->nb, h->nb) +
          32;
 }
 
@@ -554,7 +565,7 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   if (n_dd <= 0) return TLR_OK;
   if (!ws_base) { ws_base = h->scratch; ws_elems = h->scratch_elems; }
   const size_t nn = (size_t)h->nb * h->nb;
-  const size_t ie = tlr_item_elems(h->nb, h->kcap);
+  const size_t ie = tlr_item_elems(h->nb, h->kcap, h->kws);
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
   const size_t tcd = tc_item_doubles(h, h->nb, h->nb, h->nb);
   const size_t per = tops_dd_item_elems(h);
@@ -577,7 +588,7 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
     if (rc) return rc;
     rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
     if (rc) return rc;
-    k_dd_compress<<<cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, 2 * h->kcap, 2 * h->kcap,
+    k_dd_compress<<<cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, h->kws, h->kws,
                                                  h->opts.truncate_at_cap, ws, ie, h->d_stat);
     TLR_LAUNCH_CHECK();
   }
