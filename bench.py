@@ -825,7 +825,8 @@ def main():
             "data": "synthetic (jittered grid; z = L e drawn from the exact model by the dense path)"
                     if dense is not None else "synthetic (jittered grid; z drawn from the TLR model)",
             "config": main_config(a, n, len(xn_h), "replicas" if world > 1 else "single"),
-            "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": roof, "roofline_tensor": roof_tc, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "gpu_launches_per_step": int(launches) / a.steps, "clocks": clk,
             "dense_fp64_gpu": dense, "accuracy": accuracy, "deterministic_across_steps": deterministic,
             "device_bytes": {"tlr_handle_after_first_step": int(tlr_bytes), "handle": mem},
             "prediction_variance": pred_var,

@@ -271,7 +271,8 @@ int tlr_inverse_stats(tlr_handle h, int* kmin, double* kmean, int* kmax, int64_t
 /* While profiling is enabled (tlr_profile), device time of each phase of the
  * path (generate, compress, chol.*, trtri.*, lauum.*, solves, grad_fused,
  * update.*) is recorded with CUDA events.  Writes a JSON object
- * {"phase": [ms, count], ...} into buf (len bytes, host memory).
+ * {"phase": [ms, count, launches], ...} into buf (len bytes, host memory):
+ * device time, times entered, and kernel launches issued inside it.
  * Synchronises the device. */
 int tlr_profile_phases(char* buf, int64_t len);
 

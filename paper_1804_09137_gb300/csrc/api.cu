@@ -63,6 +63,7 @@ namespace {
 struct PhaseRec {
   const char* name;
   cudaEvent_t a, b;
+  long long l0, l1;  // this library's launch counter at the phase's start and end
 };
 thread_local std::vector<PhaseRec> g_ph;
 thread_local std::vector<int> g_ph_open;
@@ -70,7 +71,7 @@ thread_local std::vector<int> g_ph_open;
 
 void tlr_phase_begin(const char* name, cudaStream_t s) {
   if (!g_tlr_prof.enabled) return;
-  PhaseRec r{name, nullptr, nullptr};
+  PhaseRec r{name, nullptr, nullptr, (long long)g_tlr_launches, (long long)g_tlr_launches};
   cudaEventCreate(&r.a);
   cudaEventCreate(&r.b);
   cudaEventRecord(r.a, s);
@@ -81,6 +82,7 @@ void tlr_phase_begin(const char* name, cudaStream_t s) {
 void tlr_phase_end(cudaStream_t s) {
   if (!g_tlr_prof.enabled || g_ph_open.empty()) return;
   cudaEventRecord(g_ph[g_ph_open.back()].b, s);
+  g_ph[g_ph_open.back()].l1 = (long long)g_tlr_launches;
   g_ph_open.pop_back();
 }
 
@@ -737,20 +739,26 @@ int tlr_memory(tlr_handle h, int64_t* total, int64_t* arenas, int64_t* arena_use
 int tlr_profile_phases(char* buf, int64_t len) {
   if (!buf || len <= 0) return -1;
   TLR_CUDA_TRY(cudaDeviceSynchronize());
-  std::vector<std::pair<std::string, std::pair<double, int>>> acc;
+  struct Acc {
+    std::string name;
+    double ms;
+    int count;
+    long long launches;
+  };
+  std::vector<Acc> acc;
   for (auto& r : g_ph) {
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
     bool found = false;
     for (auto& e : acc)
-      if (e.first == r.name) { e.second.first += t; e.second.second += 1; found = true; }
-    if (!found) acc.push_back({r.name, {t, 1}});
+      if (e.name == r.name) { e.ms += t; e.count += 1; e.launches += r.l1 - r.l0; found = true; }
+    if (!found) acc.push_back({r.name, t, 1, r.l1 - r.l0});
   }
   std::string out = "{";
   for (size_t i = 0; i < acc.size(); ++i) {
     char tmp[256];
-    snprintf(tmp, sizeof(tmp), "%s\"%s\": [%.3f, %d]", i ? ", " : "", acc[i].first.c_str(), acc[i].second.first,
-             acc[i].second.second);
+    snprintf(tmp, sizeof(tmp), "%s\"%s\": [%.3f, %d, %lld]", i ? ", " : "", acc[i].name.c_str(), acc[i].ms,
+             acc[i].count, acc[i].launches);
     out += tmp;
   }
   out += "}";
