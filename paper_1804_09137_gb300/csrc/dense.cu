@@ -15,34 +15,7 @@
 
 namespace {
 
-constexpr int PB = 32;                     // panel width of the tile Cholesky
-constexpr long long BAR_WAIT = 1ll << 32;  // clock cycles before a barrier wait gives up
-
-// grid-wide barrier on a counter zeroed before the launch: the i-th barrier completes when the
-// counter reaches i * gridDim.x; false when the wait gave up
-__device__ bool grid_barrier(unsigned int* bar, unsigned int& target, long long* st) {
-  __shared__ int s_ok;
-  __syncthreads();
-  target += gridDim.x;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    int ok = 1;
-    const long long t0 = clock64();
-    while (*(volatile unsigned int*)bar < target) {
-      if (clock64() - t0 > BAR_WAIT) {
-        set_status(st, TLR_ERR_TIMEOUT, 5);
-        ok = 0;
-        break;
-      }
-      __nanosleep(64);
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
+constexpr int PB = 32;  // panel width of the tile Cholesky
 
 __global__ void __launch_bounds__(256, 2) k_potrf_tile(double* __restrict__ A, int lda, int nb, int64_t col0,
                                                        long long* __restrict__ st, unsigned int* __restrict__ bar) {

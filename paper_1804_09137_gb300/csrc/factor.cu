@@ -227,5 +227,6 @@ int tlr_factor(tlr_ctx* h, cudaStream_t s) {
       if ((rc = launch_updates(h, k, s))) return rc;
     }
   }
-  return TLR_OK;
+  // the last diagonal tile's inverse (the others are formed for the TRSM): the solves apply them all
+  return tops_trinv(h->D + (size_t)(nt - 1) * nb * nb, nb, h->linv + (size_t)(nt - 1) * nb * nb, s);
 }

@@ -750,12 +750,7 @@ static int inverse_once(tlr_ctx* h, cudaStream_t s, const double* alpha, double*
     max_dd = std::max(max_dd, (int)(off[ZP_T2_DD + 1] - off[ZP_T2_DD]));
   }
   if (max_dd > 0) ZTRY(ensure_aux(h, std::min(max_dd, 32)));
-  // ---- TRTRI
-  // L_kk^{-1} of every diagonal tile comes from the Cholesky (the last one is formed here)
-  {
-    PhaseScope ps("trtri.diag", s);
-    ZTRY(tops_trinv(h->D + (size_t)(nt - 1) * nn, nb, h->linv + (size_t)(nt - 1) * nn, s));
-  }
+  // ---- TRTRI (L_kk^{-1} of every diagonal tile comes from the Cholesky)
   const int64_t* gl = h->zoff + (size_t)nt * ZPH;
   auto GL = [&](int g) { return h->d_zlist + gl[g]; };
   auto GN = [&](int g) { return (int)(gl[g + 1] - gl[g]); };

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "tile.cuh"
@@ -79,12 +81,11 @@ __global__ void k_trsv_lower_t(const double* __restrict__ L, int nb, double* __r
   }
 }
 
-// xo = op(M) r for the explicit inverse M = L_kk^{-1} of a diagonal tile (op(M) = M^T when
-// trans): 32 rows per CTA
-__global__ void k_diag_inv_apply(const double* __restrict__ M, int nb, int trans, const double* __restrict__ r,
-                                 double* __restrict__ xo) {
+// rows r0 .. r0 + 31 of xo = op(M) r for the explicit inverse M = L_kk^{-1} of a diagonal tile
+// (op(M) = M^T when trans), one CTA of 256 threads
+__device__ void diag_inv_rows(const double* __restrict__ M, int nb, int trans, const double* __restrict__ r,
+                              double* __restrict__ xo, int r0) {
   __shared__ double part[8][33];
-  const int r0 = blockIdx.x * 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (!trans) {  // (M r)_a = sum_b M[b * nb + a] r[b]: lanes over rows (coalesced), warps split b
     const int a = r0 + lane;
@@ -98,6 +99,7 @@ __global__ void k_diag_inv_apply(const double* __restrict__ M, int nb, int trans
       for (int w = 0; w < 8; ++w) t += part[w][lane];
       xo[a] = t;
     }
+    __syncthreads();  // part is rewritten by the CTA's next call
   } else {  // (M^T r)_a = sum_{b >= a} M[a * nb + b] r[b]: warp per row, lanes over b
     for (int q = warp; q < 32; q += 8) {
       const int a = r0 + q;
@@ -152,18 +154,18 @@ __device__ void tile_gemv_sub(const TlrView& v, int64_t t, int bwd, const double
   }
 }
 
-// Step k of a solve after x_k = op(L_kk^{-1}) r_k is in xk: CTA 0 stores x_k into r_k;
-// the others update the remaining blocks, GEMV_SPLIT row chunks per tile (a dense tile's
+// Work item q of step k of a solve, after x_k = op(L_kk^{-1}) r_k is in xk: item 0 stores x_k into
+// r_k; the others update the remaining blocks, GEMV_SPLIT row chunks per tile (a dense tile's
 // nb^2 multiply-adds are spread over the chunks; a low-rank tile is one chunk's work)
 #define GEMV_SPLIT 16
-__global__ void k_gemv_step(TlrView v, int k, int bwd, const double* __restrict__ xk, double* __restrict__ r) {
-  extern __shared__ double tv[];
+__device__ void gemv_item(const TlrView& v, int k, int bwd, const double* __restrict__ xk, double* __restrict__ r,
+                          int q, double* tv) {
   const int nb = v.nb;
-  if (blockIdx.x == 0) {
+  if (q == 0) {
     for (int a = threadIdx.x; a < nb; a += blockDim.x) r[(size_t)k * nb + a] = xk[a];
     return;
   }
-  const int q = blockIdx.x - 1;
+  --q;
   const int tix = q / GEMV_SPLIT, c = q % GEMV_SPLIT;
   const int other = bwd ? tix : k + 1 + tix;  // block row i (forward) or column j (backward)
   const int64_t t = bwd ? dtile_index(k, other) : dtile_index(other, k);
@@ -180,6 +182,28 @@ __global__ void k_gemv_step(TlrView v, int k, int bwd, const double* __restrict_
   }
   if (c0 >= c1) return;
   tile_gemv_sub(v, t, bwd, xk, r + (size_t)other * nb, c0, c1, tv);
+}
+
+// A whole tile triangular solve in one launch, r <- L^{-1} r (forward) or L^{-T} r (backward): a
+// cooperative grid walks the block columns (rows), each step in two phases separated by grid
+// barriers: x_k = op(L_kk^{-1}) r_k into xk (32-row chunks over the CTAs), then the work items of
+// gemv_item over the CTAs in turn.  tv: kcap doubles of dynamic shared memory.
+__global__ void __launch_bounds__(256) k_solve_tiles(TlrView v, const double* __restrict__ linv, int bwd,
+                                                     double* __restrict__ r, double* __restrict__ xk,
+                                                     long long* __restrict__ st, unsigned int* __restrict__ bar) {
+  extern __shared__ double tv[];
+  const int nb = v.nb, nt = v.nt;
+  const int nchunk = (nb + 31) / 32;
+  unsigned int target = 0;
+  for (int step = 0; step < nt; ++step) {
+    const int k = bwd ? nt - 1 - step : step;
+    for (int c = blockIdx.x; c < nchunk; c += gridDim.x)
+      diag_inv_rows(linv + (size_t)k * nb * nb, nb, bwd, r + (size_t)k * nb, xk, 32 * c);
+    if (!grid_barrier(bar, target, st)) return;
+    const int items = 1 + (bwd ? k : nt - k - 1) * GEMV_SPLIT;
+    for (int q = blockIdx.x; q < items; q += gridDim.x) gemv_item(v, k, bwd, xk, r, q, tv);
+    if (!grid_barrier(bar, target, st)) return;
+  }
 }
 
 // z_i = L_ii e_i + sum_{j<i} L_ij e_j   (one CTA per tile row i)
@@ -349,57 +373,60 @@ int tlr_permute_out(tlr_ctx* h, const double* src, double* dst, cudaStream_t s) 
   return TLR_OK;
 }
 
-// Tile solves.  A diagonal block is applied as a GEMV with the explicit inverse
-// L_kk^{-1} kept by the Cholesky (the last block, whose inverse the Cholesky does not
-// form, by substitution), then the off-diagonal blocks of its column (forward) or row
-// (backward) are subtracted.
-static int solve_diag(tlr_ctx* h, int k, int trans, double* r, cudaStream_t s) {
-  const int nb = h->nb;
-  double* rk = r + (size_t)k * nb;
-  if (k == h->nt - 1 || !h->linv || !h->d_xk) {
-    if (trans) k_trsv_lower_t<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, rk);
-    else k_trsv_lower<<<1, 256, 0, s>>>(h->D + (size_t)k * nb * nb, nb, rk);
-    TLR_LAUNCH_CHECK();
-    TLR_CUDA_TRY(cudaMemcpyAsync(h->d_xk, rk, (size_t)nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return TLR_OK;
-  }
-  k_diag_inv_apply<<<(nb + 31) / 32, 256, 0, s>>>(h->linv + (size_t)k * nb * nb, nb, trans, rk, h->d_xk);
+// Tile solves: one cooperative launch each (k_solve_tiles), the diagonal blocks applied as GEMVs with
+// the explicit inverses L_kk^{-1} (all formed by tlr_factor).  A single tile (also the allocation-free
+// context, which keeps no inverse) is solved by substitution.
+namespace {
+int solve_max_grid(size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> memo;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = memo.find({dev, smem});
+  if (it != memo.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_tiles, 256, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  memo[{dev, smem}] = per_sm * sms;
+  return per_sm * sms;
+}
+
+int solve_tiles(tlr_ctx* h, int bwd, double* r, cudaStream_t s) {
+  const size_t sm = (size_t)h->kcap * sizeof(double);
+  const int maxg = solve_max_grid(sm);
+  if (maxg < 1) return TLR_ERR_CUDA;
+  const int grid = std::min(maxg, 1 + (h->nt - 1) * GEMV_SPLIT);
+  TlrView v = view_of(h);
+  const double* linv = h->linv;
+  double* xk = h->d_xk;
+  long long* st = h->d_stat;
+  unsigned int* bar = reinterpret_cast<unsigned int*>(h->d_stat + ST_BAR);
+  TLR_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned int), s));
+  void* args[] = {&v, &linv, &bwd, &r, &xk, &st, &bar};
+  TLR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_tiles, dim3(grid), dim3(256), args, sm, s));
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }
+}  // namespace
 
 int tlr_fwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
-  const int nb = h->nb, nt = h->nt;
-  if (nt == 1 || !h->d_xk) {  // one tile (also the allocation-free context)
-    k_trsv_lower<<<1, 256, 0, s>>>(h->D, nb, r);
+  if (h->nt == 1 || !h->d_xk) {  // one tile (also the allocation-free context)
+    k_trsv_lower<<<1, 256, 0, s>>>(h->D, h->nb, r);
     TLR_LAUNCH_CHECK();
     return TLR_OK;
   }
-  const size_t sm = (size_t)h->kcap * sizeof(double);
-  for (int k = 0; k < nt; ++k) {
-    int rc = solve_diag(h, k, 0, r, s);
-    if (rc) return rc;
-    k_gemv_step<<<1 + (nt - k - 1) * GEMV_SPLIT, 256, sm, s>>>(view_of(h), k, 0, h->d_xk, r);
-    TLR_LAUNCH_CHECK();
-  }
-  return TLR_OK;
+  return solve_tiles(h, 0, r, s);
 }
 
 int tlr_bwd_solve(tlr_ctx* h, double* r, cudaStream_t s) {
-  const int nb = h->nb, nt = h->nt;
-  if (nt == 1 || !h->d_xk) {
-    k_trsv_lower_t<<<1, 256, 0, s>>>(h->D, nb, r);
+  if (h->nt == 1 || !h->d_xk) {
+    k_trsv_lower_t<<<1, 256, 0, s>>>(h->D, h->nb, r);
     TLR_LAUNCH_CHECK();
     return TLR_OK;
   }
-  const size_t sm = (size_t)h->kcap * sizeof(double);
-  for (int k = nt - 1; k >= 0; --k) {
-    int rc = solve_diag(h, k, 1, r, s);
-    if (rc) return rc;
-    k_gemv_step<<<1 + k * GEMV_SPLIT, 256, sm, s>>>(view_of(h), k, 1, h->d_xk, r);
-    TLR_LAUNCH_CHECK();
-  }
-  return TLR_OK;
+  return solve_tiles(h, 1, r, s);
 }
 
 int tlr_lmul(tlr_ctx* h, const double* e, double* z, cudaStream_t s) {
@@ -440,9 +467,7 @@ int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const do
 int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s) {
   const int nt = h->nt, nb = h->nb;
   const int64_t npad = h->npad;
-  const size_t nn = (size_t)nb * nb;
-  // the last diagonal tile's inverse (the Cholesky forms the others)
-  TRY_RC(tops_trinv(h->D + (size_t)(nt - 1) * nn, nb, h->linv + (size_t)(nt - 1) * nn, s));
+  const size_t nn = (size_t)nb * nb;  // (the Cholesky formed every L_kk^{-1})
   // workspace: descriptors, then per right-hand side C, W (npad each) and the thin products (nt kcap)
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
   const size_t desc = (1 + 2 * (size_t)nt) * gd + 16;

@@ -90,3 +90,35 @@ struct TileItem {
   int i, j, k;  // target (i, j); source index k (meaning depends on the operation)
   int kind;     // operation-specific case code
 };
+
+// ---- grid-wide barrier of the cooperative (one-launch) kernels: every CTA is resident (cooperative
+// launch); each wait is bounded (about two seconds), after which the CTA records TLR_ERR_TIMEOUT and
+// the barrier reports false
+constexpr long long BAR_WAIT = 1ll << 32;  // clock cycles before a barrier wait gives up
+
+// grid-wide barrier on a counter zeroed before the launch: the i-th barrier completes when the
+// counter reaches i * gridDim.x; false when the wait gave up
+__device__ inline bool grid_barrier(unsigned int* bar, unsigned int& target, long long* st) {
+  __shared__ int s_ok;
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    const long long t0 = clock64();
+    while (*(volatile unsigned int*)bar < target) {
+      if (clock64() - t0 > BAR_WAIT) {
+        set_status(st, TLR_ERR_TIMEOUT, 5);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+

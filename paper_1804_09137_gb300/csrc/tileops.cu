@@ -434,12 +434,13 @@ size_t tc_item_doubles(const tlr_ctx* h, int m, int n, int k) {
 
 // batched product of device descriptors (m, n, k bounds): depths >= TC_MIN_DEPTH on the tensor cores with
 // the workspace tc (tc_doubles), the others on the CUDA cores
+// (all_deep: every non-empty descriptor has depth kmax, so no CUDA-core launch is needed after the tensor cores)
 int tops_gemm_mixed(tlr_ctx* h, const GemmGen* d_desc, int count, int m, int n, int kmax, double* tc, size_t tc_doubles,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool all_deep = false) {
   const int S = tlr_tc_slices(h);
   if (!S || kmax < TC_MIN_DEPTH || !tc_doubles) return tops_gemm(d_desc, count, m, n, s);
   int rc = oz_run_device(d_desc, count, m, n, kmax, TC_MIN_DEPTH, S, tc, tc_doubles * 8, h->d_stat, s);
-  if (rc) return rc;
+  if (rc || all_deep) return rc;
   return tops_gemm(d_desc, count, m, n, s, TC_MIN_DEPTH);
 }
 }  // namespace
@@ -470,7 +471,7 @@ static int stage_dense_operand_products(tlr_ctx* h, const TlrView& v, int alg, i
   const size_t slot = (size_t)h->nb * h->kcap;
   const size_t gd = (sizeof(GemmGen) + 7) / 8;
   const size_t tcd = tc_item_doubles(h, h->nb, h->kcap, h->nb);
-  const int64_t tc_items = std::min<int64_t>(n_dop, 16);  // the tensor-core workspace is reused in chunks
+  const int64_t tc_items = std::min<int64_t>(n_dop, 64);  // the tensor-core workspace is reused in chunks
   const size_t want = (size_t)n_dop * (slot + gd) + (size_t)tc_items * tcd + 64;
   if (want > h->dop_elems) {
     TLR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -489,7 +490,7 @@ static int stage_dense_operand_products(tlr_ctx* h, const TlrView& v, int alg, i
   const size_t tc_avail = tcd ? (size_t)(h->dop + h->dop_elems - tc) : 0;
   k_dop_desc<<<(unsigned)((n_dop + 127) / 128), 128, 0, s>>>(v, alg, k, d_lr, (int)n_dop, h->dop, d);
   TLR_LAUNCH_CHECK();
-  int rc = tops_gemm_mixed(h, d, (int)n_dop, h->nb, h->kcap, h->nb, tc, tc_avail, s);
+  int rc = tops_gemm_mixed(h, d, (int)n_dop, h->nb, h->kcap, h->nb, tc, tc_avail, s, true);
   if (rc) return rc;
   *staged = true;
   return TLR_OK;
@@ -519,7 +520,7 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
       k_upd_d_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dn + q0, cnt, d0, d1, d2, ws, per);
       TLR_LAUNCH_CHECK();
       // stage 0 (a dense factor times a thin one, depth nb) and stage 2 (dense x dense, depth nb)
-      int rc = tops_gemm_mixed(h, d0, cnt, h->nb, nc, h->nb, tc, tcd ? tc_avail : 0, s);
+      int rc = tops_gemm_mixed(h, d0, cnt, h->nb, nc, h->nb, tc, tcd ? tc_avail : 0, s, true);
       if (rc) return rc;
       rc = tops_gemm(d1, cnt, h->nb, nc, s);
       if (rc) return rc;
@@ -584,7 +585,7 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
     const size_t tc_avail = tcd ? (size_t)(ws_base + ws_elems - tc) : 0;
     k_dd_prep<<<(cnt + 127) / 128, 128, 0, s>>>(v, alg, k, d_dd + q0, cnt, d1, d2, bufs);
     TLR_LAUNCH_CHECK();
-    int rc = tops_gemm_mixed(h, d1, cnt, h->nb, h->nb, h->nb, tc, tc_avail, s);
+    int rc = tops_gemm_mixed(h, d1, cnt, h->nb, h->nb, h->nb, tc, tc_avail, s, true);
     if (rc) return rc;
     rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
     if (rc) return rc;
@@ -622,7 +623,7 @@ int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const 
                                                       pass == 0 ? which : 2, dense_right, alpha, tmp, tmp_elems,
                                                       desc, dst);
       TLR_LAUNCH_CHECK();
-      int rc = tops_gemm_mixed(h, desc, cnt, h->nb, ncols_max, h->nb, tc, tc_avail, s);
+      int rc = tops_gemm_mixed(h, desc, cnt, h->nb, ncols_max, h->nb, tc, tc_avail, s, true);
       if (rc) return rc;
       k_copy_back<<<dim3(32, cnt), 256, 0, s>>>(desc, dst);
       TLR_LAUNCH_CHECK();
