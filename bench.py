@@ -256,7 +256,7 @@ def run_regions(a):
     sizes, thetas, pts = regions.region_problems(a.regions)
     t64 = lambda v: torch.tensor(np.asarray(v), dtype=torch.float64, device=dev)
     choice = regions.autotune_nb(sizes, eps, dev=dev)
-    log("autotune", choice)
+    log("autotune", {k: v[:3] for k, v in choice.items()})
     xs = [t64(p[0]) for p in pts]
     ys = [t64(p[1]) for p in pts]
     zs = [t64(inputs.standard_normal(int(n), seed=7 + r)) for r, n in enumerate(sizes)]
@@ -288,6 +288,7 @@ def run_regions(a):
             "config": {"workload": f"regions{a.regions}_n500-8000_eps1e-8", "regions": a.regions,
                        "sum_n": int(sizes.sum()), "workers": a.workers,
                        "nb_by_size_class": {str(k): v[0] for k, v in choice.items()},
+                       "rank_cap_by_size_class": {str(k): v[1] for k, v in choice.items()},
                        "l2": "inputs larger than L2"},
             "gpu_launches": int(T.launch_count() - l0), "clocks": clk,
             "result": {"failures": int(sum(v != 0 for v in st)), "ll_sum": float(ll.sum().item())}}

@@ -67,5 +67,8 @@ def test_autotuner_picks_a_measured_candidate(T):
 
     choice = regions.autotune_nb([900, 1100, 2600], eps=1e-8, candidates=(0, 256, 512), edges=(2000,))
     assert set(choice) == {0, 1}
-    for c, (nb, secs, timings) in choice.items():
-        assert nb in timings and secs == min(timings.values())
+    for c, (nb, cap, secs, timings) in choice.items():
+        assert (nb, cap) in timings and secs == min(timings.values())
+        # every tile size was tried with both rank caps
+        for b in {b for b, _ in timings if b > 0}:
+            assert (b, max(b // 4, 16)) in timings and (b, b // 2) in timings

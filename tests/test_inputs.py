@@ -56,12 +56,14 @@ def test_region_size_classes_and_options():
     from paper_1804_09137_gb300 import regions
 
     assert [regions.size_class(n) for n in (500, 1999, 2000, 3999, 4000, 8000)] == [0, 0, 1, 1, 2, 2]
-    choice = {0: (0, 0.0, {}), 1: (768, 0.0, {}), 2: (384, 0.0, {})}
+    choice = {0: (0, 0, 0.0, {}), 1: (768, 192, 0.0, {}), 2: (384, 0, 0.0, {})}
     o = regions.make_opts(1500, choice, 1e-8)  # one tile covering the region
     assert o.nb == 1500 and o.eps == 1e-8 and o.metric == 0
-    o = regions.make_opts(3000, choice, 1e-8)
-    assert o.nb == 768 and o.rank_cap == 384
-    o = regions.make_opts(700, {0: (1024, 0.0, {})}, 1e-8)  # a tile larger than the region: single tile
+    o = regions.make_opts(3000, choice, 1e-8)  # the autotuned rank cap
+    assert o.nb == 768 and o.rank_cap == 192
+    o = regions.make_opts(5000, choice, 1e-8)  # no cap chosen: half the tile
+    assert o.nb == 384 and o.rank_cap == 192
+    o = regions.make_opts(700, {0: (1024, 0, 0.0, {})}, 1e-8)  # a tile larger than the region: single tile
     assert o.nb == 700
     sizes, thetas, pts = regions.region_problems(R=6)
     assert len(pts) == 6 and all(len(p[0]) == int(n) for p, n in zip(pts, sizes))
