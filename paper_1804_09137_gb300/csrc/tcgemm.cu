@@ -164,8 +164,7 @@ __host__ __device__ inline int round_up(int a, int b) { return (a + b - 1) / b *
 
 // ------------------------------------------------------------------ split
 // E[r] = largest biased exponent over row r (0 for padded rows and zero rows)
-__global__ void k_oz_rowexp(const OzSrc* __restrict__ srcs) {
-  const OzSrc d = srcs[blockIdx.y];
+__device__ __forceinline__ void rowexp_body(const OzSrc& d) {
   const int rows_pad = round_up(d.rows, d.block_rows);
   if (d.col) {  // element (r, k) at X[k * ld + r]: a thread per row, coalesced across rows
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,6 +187,8 @@ __global__ void k_oz_rowexp(const OzSrc* __restrict__ srcs) {
     }
   }
 }
+
+__global__ void k_oz_rowexp(const OzSrc* __restrict__ srcs) { rowexp_body(srcs[blockIdx.y]); }
 
 // digits of 8 consecutive k of one row: thread (row r, k octet q)
 template <int S>
@@ -602,33 +603,60 @@ int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, l
 }
 
 namespace {
-// descriptor q -> split descriptors 2q, 2q + 1 and GEMM descriptor q with fixed-size buffers
-__global__ void k_oz_from_gen(const GemmGen* __restrict__ g, int count, int k_min, int S, char* __restrict__ base,
-                              size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per, OzSrc* __restrict__ src,
-                              OzGemm* __restrict__ gem) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= count) return;
-  const GemmGen x = g[q];
+// descriptor q -> split descriptors 2q (op(A)), 2q + 1 (op(B)^T) and GEMM descriptor q with fixed-size
+// buffers at base + q per
+__device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_min, char* __restrict__ base,
+                                               size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per,
+                                               OzSrc* a, OzSrc* b, OzGemm* og) {
   char* p = base + (size_t)q * per;
   uint16_t* sa = reinterpret_cast<uint16_t*>(p);
   uint16_t* sb = reinterpret_cast<uint16_t*>(p + sa_bytes);
   int* xa = reinterpret_cast<int*>(p + sa_bytes + sb_bytes);
   int* xb = reinterpret_cast<int*>(p + sa_bytes + sb_bytes + xa_bytes);
   const bool run = x.m > 0 && x.n > 0 && x.k >= k_min && x.k > 0;
-  OzSrc a, b;
-  a.X = x.A; a.ld = x.lda; a.col = x.tA ? 0 : 1; a.rows = run ? x.m : 0; a.depth = x.k; a.out = sa; a.ex = xa;
-  a.block_rows = OZ_BM;
-  b.X = x.B; b.ld = x.ldb; b.col = x.tB ? 1 : 0; b.rows = run ? x.n : 0; b.depth = x.k; b.out = sb; b.ex = xb;
-  b.block_rows = OZ_BN;
-  src[2 * q] = a;
-  src[2 * q + 1] = b;
-  OzGemm og;
+  a->X = x.A; a->ld = x.lda; a->col = x.tA ? 0 : 1; a->rows = run ? x.m : 0; a->depth = x.k; a->out = sa; a->ex = xa;
+  a->block_rows = OZ_BM; a->kb0 = 0; a->nkb = 0; a->multi = 0;
+  b->X = x.B; b->ld = x.ldb; b->col = x.tB ? 1 : 0; b->rows = run ? x.n : 0; b->depth = x.k; b->out = sb; b->ex = xb;
+  b->block_rows = OZ_BN; b->kb0 = 0; b->nkb = 0; b->multi = 0;
   const int nkb = (x.k + OZ_BK - 1) / OZ_BK;
-  og.a.sl = sa; og.a.ex = xa; og.a.rows = x.m; og.a.nkb = nkb;
-  og.b.sl = sb; og.b.ex = xb; og.b.rows = x.n; og.b.nkb = nkb;
-  og.C = x.C; og.ldc = x.ldc; og.m = run ? x.m : 0; og.n = run ? x.n : 0;
-  og.alpha = x.alpha; og.beta = x.beta; og.lower = x.lower;
-  gem[q] = og;
+  memset(og, 0, sizeof(*og));
+  og->a.sl = sa; og->a.ex = xa; og->a.rows = x.m; og->a.nkb = nkb;
+  og->b.sl = sb; og->b.ex = xb; og->b.rows = x.n; og->b.nkb = nkb;
+  og->C = x.C; og->ldc = x.ldc; og->m = run ? x.m : 0; og->n = run ? x.n : 0;
+  og->alpha = x.alpha; og->beta = x.beta; og->lower = x.lower;
+}
+
+// the exponent pass of operand blockIdx.y (descriptor y / 2, side y % 2) straight from the GEMM
+// descriptors; the first CTA of each operand also stores its split descriptor (and side 0 the GEMM
+// descriptor) for the slice and product kernels
+__global__ void k_oz_rowexp_gen(const GemmGen* __restrict__ g, int k_min, char* __restrict__ base, size_t sa_bytes,
+                                size_t sb_bytes, size_t xa_bytes, size_t per, OzSrc* __restrict__ src,
+                                OzGemm* __restrict__ gem) {
+  const int y = blockIdx.y, q = y >> 1;
+  OzSrc a, b;
+  OzGemm og;
+  descs_from_gen(g[q], q, k_min, base, sa_bytes, sb_bytes, xa_bytes, per, &a, &b, &og);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    src[y] = (y & 1) ? b : a;
+    if (!(y & 1)) gem[q] = og;
+  }
+  rowexp_body((y & 1) ? b : a);
+}
+
+template <int S>
+int launch_split_gen(const GemmGen* d_g, int cnt, int k_min, char* base, size_t sa, size_t sb, size_t xa, size_t per,
+                     OzSrc* src, OzGemm* gem, int max_rows, int max_depth, cudaStream_t s) {
+  const int rows_pad = round_up(std::max(max_rows, 1), OZ_BM);
+  const int depth_pad = round_up(std::max(max_depth, 1), OZ_BK);
+  // 2 cnt operands; callers keep cnt <= 32767
+  k_oz_rowexp_gen<<<dim3((rows_pad * 32 + 255) / 256, 2 * cnt), 256, 0, s>>>(d_g, k_min, base, sa, sb, xa, per, src,
+                                                                            gem);
+  TLR_LAUNCH_CHECK();
+  const dim3 blk(32, 8);
+  const dim3 grid((rows_pad + 31) / 32, (depth_pad / 8 + 7) / 8, 2 * cnt);
+  k_oz_split<S><<<grid, blk, 0, s>>>(src);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
 }
 }  // namespace
 
@@ -647,7 +675,7 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
   const size_t xb = align128((size_t)round_up(max_n, OZ_BN) * 4);
   const size_t per = sa + sb + xa + xb;
   const size_t per_all = per + 2 * sizeof(OzSrc) + sizeof(OzGemm);
-  const int chunk = (int)std::min<size_t>(65535, ws_bytes > 512 ? (ws_bytes - 512) / per_all : 0);
+  const int chunk = (int)std::min<size_t>(32767, ws_bytes > 512 ? (ws_bytes - 512) / per_all : 0);
   if (chunk < 1) TLR_RETURN_OOM();
   char* base = static_cast<char*>(ws);
   for (int q0 = 0; q0 < count; q0 += chunk) {
@@ -655,9 +683,13 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
     char* descs = reinterpret_cast<char*>(align128(reinterpret_cast<size_t>(base + (size_t)cnt * per)));
     OzSrc* src = reinterpret_cast<OzSrc*>(descs);
     OzGemm* gem = reinterpret_cast<OzGemm*>(descs + align128((size_t)2 * cnt * sizeof(OzSrc)));
-    k_oz_from_gen<<<(cnt + 127) / 128, 128, 0, s>>>(d_g + q0, cnt, k_min, S, base, sa, sb, xa, per, src, gem);
-    TLR_LAUNCH_CHECK();
-    int rc = oz_split(src, 2 * cnt, std::max(max_m, max_n), max_k, S, s);
+    int rc;
+    switch (S) {
+      case 4: rc = launch_split_gen<4>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
+      case 5: rc = launch_split_gen<5>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
+      case 6: rc = launch_split_gen<6>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
+      default: rc = -1;
+    }
     if (rc) return rc;
     rc = oz_gemm(gem, cnt, max_m, max_n, S, d_stat, s);
     if (rc) return rc;

@@ -337,25 +337,30 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
 }
 
 // descriptors of X_tmp = alpha op(M) X (or alpha A op(M)) for tile items
+// items q < nl: low-rank tiles lr[q] (X = U or V by `which`, op(M) transM); the others dense tiles
+// dn[q - nl] (op(M) transM_dense, M on the right when dense_right); products into tmp (low-rank ones
+// first, lr_elems each, then dn_elems each)
 __global__ void k_trmul_desc(TlrView v, const double* __restrict__ M0, size_t m_stride, int m_by, int transM,
-                             const int2* __restrict__ items, int cnt, int which, int dense_right, double alpha,
-                             double* __restrict__ tmp, size_t tmp_elems, GemmGen* __restrict__ desc,
-                             double** __restrict__ dst) {
+                             int transM_dense, const int2* __restrict__ lr, int nl, const int2* __restrict__ dn,
+                             int cnt, int which, int dense_right, double alpha, double* __restrict__ tmp,
+                             size_t lr_elems, size_t dn_elems, GemmGen* __restrict__ desc, double** __restrict__ dst) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= cnt) return;
-  const int2 it = items[q];
+  const bool dense = q >= nl;
+  const int2 it = dense ? dn[q - nl] : lr[q];
   const double* M = M0 + (m_by == 1 ? (size_t)it.x * m_stride : m_by == 2 ? (size_t)it.y * m_stride : 0);
   const int64_t t = dtile_index(it.x, it.y);
   const int nb = v.nb;
   GemmGen g;
-  g.C = tmp + (size_t)q * tmp_elems; g.ldc = nb; g.lda = nb; g.ldb = nb; g.alpha = alpha; g.beta = 0.0;
+  g.C = dense ? tmp + (size_t)nl * lr_elems + (size_t)(q - nl) * dn_elems : tmp + (size_t)q * lr_elems;
+  g.ldc = nb; g.lda = nb; g.ldb = nb; g.alpha = alpha; g.beta = 0.0;
   g.lower = 0; g.m = nb; g.k = nb;
   double* X;
-  if (which == 2) {
+  if (dense) {
     X = tileA(v, t);
     g.n = nb;
-    if (dense_right) { g.A = X; g.tA = 0; g.B = M; g.tB = transM; }
-    else { g.A = M; g.tA = transM; g.B = X; g.tB = 0; }
+    if (dense_right) { g.A = X; g.tA = 0; g.B = M; g.tB = transM_dense; }
+    else { g.A = M; g.tA = transM_dense; g.B = X; g.tB = 0; }
   } else {
     X = which == 0 ? tileU(v, t) : tileV(v, t);
     g.n = v.rank[t];
@@ -599,35 +604,34 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
 int tops_trmul(tlr_ctx* h, const TlrView& v, const double* M, int transM, const int2* d_lr, int n_lr, int which,
                int transM_dense, const int2* d_dn, int n_dn, int dense_right, double alpha, cudaStream_t s,
                size_t m_stride, int m_by) {
+  // low-rank and dense items in one index space (low-rank first), three launches a chunk
   const size_t nb = h->nb;
   const size_t gd = (sizeof(GemmGen) + 7) / 8 + 1;
-  for (int pass = 0; pass < 2; ++pass) {
-    const int total = pass == 0 ? n_lr : n_dn;
-    const int2* items = pass == 0 ? d_lr : d_dn;
-    if (total <= 0) continue;
-    const size_t tmp_elems = pass == 0 ? nb * (size_t)h->kcap : nb * nb;
-    const int ncols_max = pass == 0 ? h->kcap : h->nb;
-    const size_t tcd = tc_item_doubles(h, h->nb, ncols_max, h->nb);
-    const int chunk = chunk_of(h, tmp_elems + gd + tcd, 128);
-    if (chunk < 1) TLR_RETURN_OOM();
-    for (int q0 = 0; q0 < total; q0 += chunk) {
-      const int cnt = total - q0 < chunk ? total - q0 : chunk;
-      GemmGen* desc = (GemmGen*)h->scratch;
-      double** dst = (double**)(h->scratch + (size_t)cnt * (gd - 1) + 8);
-      double* tmp = h->scratch + (size_t)cnt * gd + 16;
-      double* tc = tmp + (size_t)cnt * tmp_elems + 16;
-      tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
-      const size_t tc_avail = tcd ? (size_t)(h->scratch + h->scratch_elems - tc) : 0;
-      k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, m_stride, m_by, pass == 0 ? transM : transM_dense,
-                                                      items + q0, cnt,
-                                                      pass == 0 ? which : 2, dense_right, alpha, tmp, tmp_elems,
-                                                      desc, dst);
-      TLR_LAUNCH_CHECK();
-      int rc = tops_gemm_mixed(h, desc, cnt, h->nb, ncols_max, h->nb, tc, tc_avail, s, true);
-      if (rc) return rc;
-      k_copy_back<<<dim3(32, cnt), 256, 0, s>>>(desc, dst);
-      TLR_LAUNCH_CHECK();
-    }
+  const int total = std::max(n_lr, 0) + std::max(n_dn, 0);
+  if (total <= 0) return TLR_OK;
+  const size_t lr_elems = nb * (size_t)h->kcap, dn_elems = nb * nb;
+  const size_t tcd = tc_item_doubles(h, h->nb, h->nb, h->nb);
+  const int chunk = chunk_of(h, dn_elems + gd + tcd, 128);
+  if (chunk < 1) TLR_RETURN_OOM();
+  for (int q0 = 0; q0 < total; q0 += chunk) {
+    const int cnt = total - q0 < chunk ? total - q0 : chunk;
+    const int nl = std::max(0, std::min(n_lr - q0, cnt));  // low-rank items of this chunk
+    const int2* lr = d_lr + std::min(q0, std::max(n_lr, 0));
+    const int2* dn = d_dn + std::max(0, q0 - std::max(n_lr, 0));
+    GemmGen* desc = (GemmGen*)h->scratch;
+    double** dst = (double**)(h->scratch + (size_t)cnt * (gd - 1) + 8);
+    double* tmp = h->scratch + (size_t)cnt * gd + 16;
+    double* tc = tmp + (size_t)nl * lr_elems + (size_t)(cnt - nl) * dn_elems + 16;
+    tc = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(tc) + 127) & ~(uintptr_t)127);
+    const size_t tc_avail = tcd ? (size_t)(h->scratch + h->scratch_elems - tc) : 0;
+    k_trmul_desc<<<(cnt + 127) / 128, 128, 0, s>>>(v, M, m_stride, m_by, transM, transM_dense, lr, nl, dn, cnt, which,
+                                                    dense_right, alpha, tmp, lr_elems, dn_elems, desc, dst);
+    TLR_LAUNCH_CHECK();
+    const int ncols = cnt > nl ? h->nb : h->kcap;
+    int rc = tops_gemm_mixed(h, desc, cnt, h->nb, ncols, h->nb, tc, tc_avail, s, true);
+    if (rc) return rc;
+    k_copy_back<<<dim3(32, cnt), 256, 0, s>>>(desc, dst);
+    TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
 }
