@@ -277,6 +277,83 @@ __device__ void cta_apply_q2_df(const dfloat* __restrict__ A1, const double* __r
   __syncthreads();
 }
 
+// One matrix of cta_geqr2_pair_df (the same arithmetic): Householder QR in place of an m x K
+// double-float matrix, the scaled reflector staged in shared memory vs (m double-floats) for the
+// trailing columns.  Used when the two factors of a recompression run on the two CTAs of a cluster.
+__device__ void cta_geqr2_one_df(dfloat* __restrict__ A, double* __restrict__ tau, int lda, int m, int K,
+                                 dfloat* __restrict__ vs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nref = K < m ? K : m;
+  __shared__ dfloat sc_tau, sc_scal, red[TLR_MAX_WARPS];
+  __shared__ int sc_on;
+  for (int c = 0; c < nref; ++c) {
+    dfloat* a = A + (size_t)c * lda;
+    float ps = 0.f, pc = 0.f;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) df_dot_add(ps, pc, a[r], a[r]);
+    const dfloat s1 = df_warp_sum(df_norm(ps, pc));
+    if (lane == 0) red[warp] = s1;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // the reflector's scalars, in float64
+      dfloat t = red[0];
+      for (int q = 1; q < nw; ++q) t = df_add(t, red[q]);
+      const double sig = df_to(t);
+      const double alpha = df_to(a[c]);
+      double beta = alpha, tc = 0.0, scal = 1.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
+        tc = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      sc_on = sig > 0.0;
+      sc_tau = df_from(tc);
+      sc_scal = df_from(scal);
+      tau[c] = tc;
+      a[c] = df_from(beta);
+    }
+    __syncthreads();
+    const int on = sc_on;
+    const dfloat sc = sc_scal;
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) {
+      const dfloat v1 = on ? df_mul(a[r], sc) : a[r];
+      a[r] = v1;
+      vs[r] = v1;
+    }
+    __syncthreads();
+    const int n1 = on ? K - c - 1 : 0;
+    for (int jj = warp; jj < n1; jj += nw) {
+      dfloat* b = A + (size_t)(c + 1 + jj) * lda;
+      const dfloat bc = b[c];
+      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(vs, b, c + 1, m, lane)), bc), sc_tau);
+      if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
+      df_col_axpy(b, d, vs, c + 1, m, lane);
+    }
+    __syncthreads();
+  }
+}
+
+// One matrix of cta_apply_q2_df: B <- Q B (double-float, ncol columns), Q = H_0 ... H_{K-1} from
+// cta_geqr2_one_df (reflectors A, taus t), reflector by reflector staged in shared memory vs.
+__device__ void cta_apply_q_one_df(const dfloat* __restrict__ A, const double* __restrict__ t, dfloat* __restrict__ B,
+                                   int lda, int m, int K, int ldb, int ncol, dfloat* __restrict__ vs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = K - 1; c >= 0; --c) {
+    const double tc = t[c];
+    if (tc == 0.0) continue;
+    __syncthreads();  // the previous reflector's readers are done
+    for (int r = c + 1 + threadIdx.x; r < m; r += blockDim.x) vs[r] = A[(size_t)c * lda + r];
+    __syncthreads();
+    const dfloat td = df_from_scaled(tc, 0);
+    for (int jj = warp; jj < ncol; jj += nw) {
+      dfloat* b = B + (size_t)jj * ldb;
+      const dfloat bc = b[c];
+      const dfloat d = df_mul(df_add(df_warp_sum(df_col_dot(vs, b, c + 1, m, lane)), bc), td);
+      if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
+      df_col_axpy(b, d, vs, c + 1, m, lane);
+    }
+  }
+  __syncthreads();
+}
+
 // C[0:m, 0:n] = beta C + alpha op(A) op(B) (op(X) = X^T when tX), column-major, in 64 x 64
 // blocks blk0, blk0 + nblk_step, ... (lower_only: blocks on or below the diagonal), with the
 // products accumulated in double-float (Dot2) on the float32 pipe; inputs are
@@ -437,43 +514,53 @@ __device__ void cta_gemm_nn_thin(int nb, int kb, int ka, double alpha, const dou
 
 // Recompress Up Vp^T (nb x K each, destroyed) into Uo Vo^T (nb x k, ld nb) with
 // singular values > eps.  Returns k (same in all threads).
-__device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, const TlrView& v,
-                              int64_t info, long long* st, double* sh, int* shi, double* flops = nullptr) {
-  if (K == 0) return 0;
-  dfloat* Ud = (dfloat*)w.Up;
-  dfloat* Vd = (dfloat*)w.Vp;
-  // scale every column by a power of two so that its largest entry is in [1, 2):
-  // Q is unchanged, R's columns are scaled back below, and the squares formed in
-  // double-float stay far inside the float32 exponent range
-  const int warp0 = threadIdx.x >> 5, lane0 = threadIdx.x & 31, nw0 = blockDim.x >> 5;
-  for (int j = warp0; j < 2 * K; j += nw0) {
-    const double* col = (j < K ? w.Up : w.Vp) + (size_t)(j % K) * nb;
+// ---- stages of the recompression (shared by the one-CTA and the two-CTA cluster versions)
+// side 0: the U factor (w.Up, exponents w.eu), side 1: the V factor (w.Vp, w.ev).
+
+// scale every column by a power of two so that its largest entry is in [1, 2) and convert it to
+// double-float in place: Q is unchanged, R's columns are scaled back below, and the squares formed in
+// double-float stay far inside the float32 exponent range
+__device__ void rc_scale_side(const ItemWs& w, int nb, int K, int side) {
+  double* P = side ? w.Vp : w.Up;
+  int* ex = side ? w.ev : w.eu;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < K; j += nw) {
+    const double* col = P + (size_t)j * nb;
     double mx = 0.0;
-    for (int r = lane0; r < nb; r += 32) mx = fmax(mx, fabs(col[r]));
+    for (int r = lane; r < nb; r += 32) mx = fmax(mx, fabs(col[r]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane0 == 0) {
-      const int ex = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
-      if (j < K) w.eu[j] = ex; else w.ev[j - K] = ex;
-    }
+    if (lane == 0) ex[j] = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
   }
   __syncthreads();
-  for (size_t e = threadIdx.x; e < (size_t)nb * K; e += blockDim.x) {
-    const int j = (int)(e / nb);
-    Ud[e] = df_from_scaled(w.Up[e], -w.eu[j]);
-    Vd[e] = df_from_scaled(w.Vp[e], -w.ev[j]);
-  }
+  dfloat* D = (dfloat*)P;
+  for (size_t e = threadIdx.x; e < (size_t)nb * K; e += blockDim.x) D[e] = df_from_scaled(P[e], -ex[e / nb]);
   __syncthreads();
-  cta_geqr2_pair_df(Ud, w.tu, Vd, w.tv, nb, nb, K, w.vs);
-  const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
-  // R_u, R_v unscaled to float64 (Ke x K each, upper trapezoid) in the output buffers, then M = R_u R_v^T
-  double* Ru = (double*)w.Uq;
-  double* Rv = (double*)w.Vq;
+}
+
+// after the QR of a side: its R factor unscaled to float64 (Ke x K, upper trapezoid) into w.Uq (side 0)
+// or w.Vq (side 1)
+__device__ void rc_extract_r(const ItemWs& w, int nb, int K, int side) {
+  const int Ke = K < nb ? K : nb;
+  const dfloat* D = (const dfloat*)(side ? w.Vp : w.Up);
+  const int* ex = side ? w.ev : w.eu;
+  double* R = (double*)(side ? w.Vq : w.Uq);
   for (int e = threadIdx.x; e < Ke * K; e += blockDim.x) {
     const int a = e % Ke, c = e / Ke;
-    Ru[e] = (a <= c) ? df_to_scaled(Ud[(size_t)c * nb + a], w.eu[c]) : 0.0;
-    Rv[e] = (a <= c) ? df_to_scaled(Vd[(size_t)c * nb + a], w.ev[c]) : 0.0;
+    R[e] = (a <= c) ? df_to_scaled(D[(size_t)c * nb + a], ex[c]) : 0.0;
   }
   __syncthreads();
+}
+
+// one CTA, after both R factors are in w.Uq / w.Vq: the core M = R_u R_v^T, its column-pivoted
+// Householder QR stopped at the first step whose trailing block has Frobenius norm <= eps (then
+// ||M - Q_k R_k P^T||_2 <= eps), the tile's block in the arena, the U block Q_M[:, :k] (into the
+// arena, then as double-float into w.Uq) and the V block P R_k^T (double-float, w.Vq).  Returns k
+// (0: nothing is written).
+__device__ int rc_core(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, const TlrView& v,
+                       int64_t info, long long* st, double* sh, int* shi, double* flops) {
+  const int Ke = K < nb ? K : nb;  // rows of the trapezoidal R factors
+  double* Ru = (double*)w.Uq;
+  double* Rv = (double*)w.Vq;
   for (int e = threadIdx.x; e < Ke * Ke; e += blockDim.x) {
     const int a = e % Ke, b = e / Ke;
     const int c0 = a > b ? a : b;
@@ -579,7 +666,6 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   // the tile's columns in the arena (a new block when k exceeds its reservation)
   if (!cta_lr_reserve(v, info, k, st)) return 0;
   double* Uo = tileU(v, info);
-  double* Vo = tileV(v, info);
   // U block = Q_M[:, :k] (Ke x k): apply the k reflectors of M to [I_k; 0]
   for (int j = 0; j < k; ++j)
     for (int r = threadIdx.x; r < nb; r += blockDim.x) {
@@ -597,22 +683,43 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
   for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) w.Uq[e] = df_from_scaled(Uo[e], 0);
   __syncthreads();
   if (flops && threadIdx.x == 0) atomicAdd(flops, fl + 4.0 * Ke * k * k);
+  return k;
+}
+
+// flops of the QR of one nb x K factor and of applying its Q to k columns
+__device__ __forceinline__ double rc_side_flops(int nb, int K, int k) {
+  const double m = nb, KK = K, Kq = K < nb ? K : nb;
+  return 2.0 * m * KK * Kq - (KK + m) * Kq * Kq + 2.0 * Kq * Kq * Kq / 3.0 + k * (4.0 * m * Kq - 2.0 * Kq * Kq);
+}
+
+// the output of a side: Uo (side 0) or Vo (side 1) from the double-float w.Uq / w.Vq
+__device__ void rc_store_side(const ItemWs& w, int nb, int k, const TlrView& v, int64_t t, int side) {
+  double* O = side ? tileV(v, t) : tileU(v, t);
+  const dfloat* Q = side ? w.Vq : w.Uq;
+  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) O[e] = df_to_scaled(Q[e], 0);
+  __syncthreads();
+}
+
+// Recompression of the rank-K product Up Vp^T by one CTA (see the file's header); both factors in
+// lockstep.  Returns the new rank written to tile `info`.
+__device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kcap, int trunc_cap, const TlrView& v,
+                              int64_t info, long long* st, double* sh, int* shi, double* flops = nullptr) {
+  if (K == 0) return 0;
+  rc_scale_side(w, nb, K, 0);
+  rc_scale_side(w, nb, K, 1);
+  dfloat* Ud = (dfloat*)w.Up;
+  dfloat* Vd = (dfloat*)w.Vp;
+  cta_geqr2_pair_df(Ud, w.tu, Vd, w.tv, nb, nb, K, w.vs);
+  rc_extract_r(w, nb, K, 0);
+  rc_extract_r(w, nb, K, 1);
+  const int k = rc_core(w, nb, K, eps, kcap, trunc_cap, v, info, st, sh, shi, flops);
+  if (k == 0) return 0;
+  const int Ke = K < nb ? K : nb;
   cta_apply_q2_df(Ud, w.tu, w.Uq, Vd, w.tv, w.Vq, nb, nb, Ke, nb, k, w.vs);
   __syncthreads();
-  for (size_t e = threadIdx.x; e < (size_t)nb * k; e += blockDim.x) {
-    Uo[e] = df_to_scaled(w.Uq[e], 0);
-    Vo[e] = df_to_scaled(w.Vq[e], 0);
-  }
-  __syncthreads();
-  if (flops && threadIdx.x == 0) {
-    // Householder QR of two nb x K factors and applying both Q to k columns (the core
-    // product and its pivoted QR were counted above)
-    const double m = nb, KK = K, Kq = Ke;
-    (void)KK;
-    const double qr = 2.0 * (2.0 * m * KK * Kq - (KK + m) * Kq * Kq + 2.0 * Kq * Kq * Kq / 3.0);
-    const double apply = 2.0 * k * (4.0 * m * Kq - 2.0 * Kq * Kq);
-    atomicAdd(flops, qr + apply);
-  }
+  rc_store_side(w, nb, k, v, info, 0);
+  rc_store_side(w, nb, k, v, info, 1);
+  if (flops && threadIdx.x == 0) atomicAdd(flops, 2.0 * rc_side_flops(nb, K, k));
   return k;
 }
 
