@@ -812,7 +812,7 @@ def main():
             traffic = tr.get("dram_bytes_per_launch")
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
-            "kernel": "k_upd_lr_gen", "launches": prof["launches"], "kernel_ms_per_step": prof["ms"] / a.steps,
+            "kernel": "k_upd_lr_pair", "launches": prof["launches"], "kernel_ms_per_step": prof["ms"] / a.steps,
             "peak_source": "float64 derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (a DFMA loop measured "
                            "1.19 TFLOP/s)",
             "frac_of_ff32_ceiling": (achieved / FF32_CEIL_TFLOPS) if achieved else None,
