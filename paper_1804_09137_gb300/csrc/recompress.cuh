@@ -730,7 +730,9 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
 // residual column there, and the next pivot row where that column is largest
 // among unused rows.  Stops (conv = 1) after two successive rank-one terms with
 // ||u|| ||v|| <= tol, when the residual rows are zero, or when every row is used;
-// conv = 0 when aca_max terms did not suffice.  Factors go to w.Up / w.Vp.
+// conv = 0 when aca_max terms did not suffice.  Factors go to w.Up / w.Vp (float64, for the
+// recompression) and to w.Uq / w.Vq as double-float copies: the residual rows and columns subtract the
+// terms so far with double-float dot products (the float64 pipe runs at 1/64 of the float32 rate).
 // Shared memory: dsm >= 2 nb doubles + nb ints.
 template <class E>
 __device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int aca_max, const ItemWs& w,
@@ -745,9 +747,10 @@ __device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int a
     if (k >= aca_max) break;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       double val = 0.0;
-      if (b < mj) {
-        val = entry(istar, b);
-        for (int l = 0; l < k; ++l) val = fma(-w.Up[(size_t)l * nb + istar], w.Vp[(size_t)l * nb + b], val);
+      if (b < mj) {  // residual row: the sum over the terms so far in double-float (Dot2)
+        float s = 0.f, c = 0.f;
+        for (int l = 0; l < k; ++l) df_dot_add(s, c, w.Uq[(size_t)l * nb + istar], w.Vq[(size_t)l * nb + b]);
+        val = entry(istar, b) - ((double)s + (double)c);
       }
       row[b] = val;
     }
@@ -781,14 +784,18 @@ __device__ int cta_aca(const E& entry, int nb, int mi, int mj, double tol, int a
     double pu = 0.0, pv = 0.0;
     for (int a = threadIdx.x; a < nb; a += blockDim.x) {
       double val = 0.0;
-      if (a < mi) {
-        val = entry(a, jstar);
-        for (int l = 0; l < k; ++l) val = fma(-w.Vp[(size_t)l * nb + jstar], w.Up[(size_t)l * nb + a], val);
+      if (a < mi) {  // residual column, likewise
+        float s = 0.f, c = 0.f;
+        for (int l = 0; l < k; ++l) df_dot_add(s, c, w.Vq[(size_t)l * nb + jstar], w.Uq[(size_t)l * nb + a]);
+        val = entry(a, jstar) - ((double)s + (double)c);
       }
       col[a] = val;
-      w.Up[(size_t)k * nb + a] = val;
       const double rv = row[a] / delta;
+      // the new term in float64 (for the recompression) and in double-float (for the residuals)
+      w.Up[(size_t)k * nb + a] = val;
       w.Vp[(size_t)k * nb + a] = rv;
+      w.Uq[(size_t)k * nb + a] = df_from_scaled(val, 0);
+      w.Vq[(size_t)k * nb + a] = df_from_scaled(rv, 0);
       pu = fma(val, val, pu);
       pv = fma(rv, rv, pv);
     }
