@@ -724,6 +724,57 @@ __device__ int cta_recompress(const ItemWs& w, int nb, int K, double eps, int kc
 }
 
 
+// ---- two CTAs of a cluster on one recompression
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+
+// an int in the shared memory of cluster CTA `rank` (distributed shared memory)
+__device__ __forceinline__ int dsmem_load_int(const int* p, int rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// Both CTAs of a cluster call it with the cluster's workspace: the recompression of cta_recompress with the
+// U side (scaling, Householder QR, applying Q, storing U) on cluster rank 0 and the V side on rank 1;
+// rank 0 also runs the core (rc_core) between two cluster barriers.  The arithmetic is that of
+// cta_recompress.  Returns the new rank on both CTAs (s_k: an int of the caller's shared memory).
+__device__ int cluster_recompress(const ItemWs& w, int nb, int K, double tau, int kcap, int trunc_cap,
+                                  const TlrView& v, int64_t t, long long* st, double* sh, int* shi, double* flops,
+                                  int rank, int* s_k) {
+  if (K == 0) return 0;
+  const int side = rank;  // 0: U, 1: V
+  const int Ke = K < nb ? K : nb;
+  rc_scale_side(w, nb, K, side);
+  cta_geqr2_one_df((dfloat*)(side ? w.Vp : w.Up), side ? w.tv : w.tu, nb, nb, K, w.vs);
+  rc_extract_r(w, nb, K, side);
+  cluster_sync_all();  // both R factors are in the workspace
+  if (rank == 0) {
+    const int kr = rc_core(w, nb, K, tau, kcap, trunc_cap, v, t, st, sh, shi, flops);
+    if (threadIdx.x == 0) *s_k = kr;
+    __syncthreads();
+  }
+  cluster_sync_all();  // the core's U and V blocks, the arena block and the rank are out
+  const int kr = dsmem_load_int(s_k, 0);
+  cluster_sync_all();  // rank 1 has read the rank from rank 0's shared memory
+  if (kr > 0) {
+    cta_apply_q_one_df((const dfloat*)(side ? w.Vp : w.Up), side ? w.tv : w.tu, side ? w.Vq : w.Uq, nb, nb, Ke, nb,
+                       kr, w.vs);
+    rc_store_side(w, nb, kr, v, t, side);
+    if (flops && threadIdx.x == 0) atomicAdd(flops, rc_side_flops(nb, K, kr));
+  }
+  return kr;
+}
+
 // Adaptive cross approximation with partial pivoting of an mi x mj block (rows
 // and columns beyond are zero) whose entries come from E(a, b): each step takes
 // the residual row at the pivot row, its largest entry as pivot column, the

@@ -171,25 +171,6 @@ __global__ void k_dop_desc(TlrView v, int alg, int k, const int2* __restrict__ i
 // V side; rank 0 also runs the small core (M = R_u R_v^T, its pivoted QR, the arena block) between
 // two cluster barriers.  Halves the latency of an item, which bounds every launch (each launch lasts
 // as long as its longest item).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ int cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return (int)r;
-}
-
-// an int in the shared memory of cluster CTA `rank` (distributed shared memory)
-__device__ __forceinline__ int dsmem_load_int(const int* p, int rank) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(p), ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-  int v;
-  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
-  return v;
-}
-
 __device__ void upd_lr_item_pair(const TlrView& v, int alg, int k, int2 it, double tau, int Kmax, int trunc_cap,
                                  ItemWs& w, long long* __restrict__ st, double* __restrict__ flops, double* sh,
                                  int* shi, const double* __restrict__ pre, int rank, int* s_k) {
@@ -254,25 +235,7 @@ __device__ void upd_lr_item_pair(const TlrView& v, int alg, int k, int2 it, doub
   }
   __syncthreads();
   if (flops && threadIdx.x == 0 && pf > 0.0) atomicAdd(flops, pf);
-  const int K = k0 + r;
-  const int Ke = K < nb ? K : nb;
-  // this side: scale, Householder QR, R
-  rc_scale_side(w, nb, K, side);
-  cta_geqr2_one_df((dfloat*)P, side ? w.tv : w.tu, nb, nb, K, w.vs);
-  rc_extract_r(w, nb, K, side);
-  cluster_sync_all();  // both R factors are in the workspace
-  if (rank == 0) {
-    const int kr = rc_core(w, nb, K, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, flops);
-    if (threadIdx.x == 0) *s_k = kr;
-    __syncthreads();
-  }
-  cluster_sync_all();  // the core's U and V blocks, the arena block and the rank are out
-  const int kr = dsmem_load_int(s_k, 0);
-  if (kr > 0) {
-    cta_apply_q_one_df((const dfloat*)P, side ? w.tv : w.tu, side ? w.Vq : w.Uq, nb, nb, Ke, nb, kr, w.vs);
-    rc_store_side(w, nb, kr, v, tt, side);
-    if (flops && threadIdx.x == 0) atomicAdd(flops, rc_side_flops(nb, K, kr));
-  }
+  const int kr = cluster_recompress(w, nb, k0 + r, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, flops, rank, s_k);
   if (rank == 0 && threadIdx.x == 0) v.rank[tt] = kr;
 }
 
@@ -472,6 +435,44 @@ __global__ void k_dd_compress(TlrView v, const int2* __restrict__ items, const d
   __syncthreads();
   const int kr = cta_recompress(w, nb, k, tau, v.kcap, trunc_cap, v, tt, st, sh, shi);
   if (threadIdx.x == 0) v.rank[tt] = kr;
+}
+
+// The same on a cluster of two CTAs per item: rank 0 runs the cross approximation, then both run the
+// recompression (cluster_recompress: U side on rank 0, V side on rank 1).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 3)
+    k_dd_compress_pair(TlrView v, const int2* __restrict__ items, const double* __restrict__ bufs, double eps,
+                       const double* __restrict__ d_zeta, double zpow, int aca_max, int Kmax, int trunc_cap,
+                       double* __restrict__ ws, size_t item_elems, long long* __restrict__ st) {
+  extern __shared__ double dsm[];
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  __shared__ int s_aca[2], s_k;
+  const int rank = cluster_rank();
+  const int q = blockIdx.x >> 1;
+  const int2 it = items[q];
+  const int nb = v.nb;
+  const int64_t tt = dtile_index(it.x, it.y);
+  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
+  ItemWs w = item_ws(ws, item_elems, q, nb, Kmax, v.kcap);
+  w.vs = reinterpret_cast<dfloat*>(dsm);  // free after the cross approximation
+  if (rank == 0) {
+    DenseEntry de{bufs + (size_t)q * nb * nb, nb};
+    int conv = 0;
+    const int k = cta_aca(de, nb, nb, nb, tau * 0.125, aca_max, w, dsm, sh, shi, &conv);
+    if (!conv && threadIdx.x == 0) {
+      // below the widest workspace the host widens it and repeats; at it, the rank cap was exceeded
+      if (aca_max < 2 * v.kcap) set_status(st, TLR_ST_WIDEN, tt);
+      else if (!trunc_cap) set_status(st, TLR_ERR_RANK_CAP, tt);
+    }
+    if (threadIdx.x == 0) { s_aca[0] = k; s_aca[1] = conv; }
+    __syncthreads();
+  }
+  cluster_sync_all();  // the cross factors are in the workspace
+  const int k = dsmem_load_int(&s_aca[0], 0), conv = dsmem_load_int(&s_aca[1], 0);
+  cluster_sync_all();  // rank 1 has read them
+  if (!conv && aca_max < 2 * v.kcap) return;
+  const int kr = cluster_recompress(w, nb, k, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, nullptr, rank, &s_k);
+  if (rank == 0 && threadIdx.x == 0) v.rank[tt] = kr;
 }
 
 // descriptors of X_tmp = alpha op(M) X (or alpha A op(M)) for tile items
@@ -774,7 +775,9 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
   const int chunk = ws_elems > 64 ? (int)std::min<size_t>((ws_elems - 64) / per, 65535) : 0;
   if (chunk < 1) TLR_RETURN_OOM();
   const size_t smem = 2 * (size_t)h->nb * sizeof(double) + (size_t)h->nb * sizeof(int);
-  if (tlr_smem_optin((const void*)k_dd_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
+  if (tlr_smem_optin((const void*)k_dd_compress, smem) != TLR_OK ||
+      tlr_smem_optin((const void*)k_dd_compress_pair, smem) != TLR_OK)
+    return TLR_ERR_CUDA;
   for (int64_t q0 = 0; q0 < n_dd; q0 += chunk) {
     const int cnt = (int)(n_dd - q0 < chunk ? n_dd - q0 : chunk);
     GemmGen* d1 = (GemmGen*)ws_base;
@@ -790,8 +793,12 @@ int tops_update_dd(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_d
     if (rc) return rc;
     rc = tops_gemm(d2, cnt, h->nb, h->nb, s);
     if (rc) return rc;
-    k_dd_compress<<<cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, h->kws, h->kws,
-                                                 h->opts.truncate_at_cap, ws, ie, h->d_stat);
+    if (upd_pair_mode())
+      k_dd_compress_pair<<<2 * cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, h->kws, h->kws,
+                                                            h->opts.truncate_at_cap, ws, ie, h->d_stat);
+    else
+      k_dd_compress<<<cnt, TLR_THREADS, smem, s>>>(v, d_dd + q0, bufs, eps, d_zeta, zpow, h->kws, h->kws,
+                                                   h->opts.truncate_at_cap, ws, ie, h->d_stat);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
