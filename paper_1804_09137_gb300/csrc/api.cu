@@ -164,7 +164,7 @@ int dmalloc(T** p, size_t count) {
 void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
-                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop, h->off, h->cap, h->top, h->offz, h->capz, h->topz, h->dtab,
+                  h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop, h->off, h->cap, h->top, h->offz, h->capz, h->topz,
                   h->gpart};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -302,7 +302,6 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->rank, ct);
   rc |= dmalloc(&h->dslot, ct);
   rc |= dmalloc(&h->tab, TAB_ELEMS);
-  rc |= dmalloc(&h->dtab, TAB_ELEMS);
   rc |= dmalloc(&h->linv, (size_t)h->cap_nt * nb * nb);
   rc |= dmalloc(&h->d_stat, 4);
   rc |= dmalloc(&h->d_ctr, 4);
@@ -725,7 +724,7 @@ int tlr_memory(tlr_handle h, int64_t* total, int64_t* arenas, int64_t* arena_use
   const double ar = 2.0 * d * ((double)h->arena + (double)h->arenaz);
   const double ws = d * ((double)h->scratch_elems + (double)h->scratch_dd_elems + (double)h->dop_elems +
                          (double)h->gpart_elems + (double)h->msave_elems);
-  double fixed = d * (2 * cnp + 4 * cnp + (double)h->nb + 2.0 * TAB_ELEMS + h->red_len + 4) + 4.0 * h->cap_n + 16.0;
+  double fixed = d * (2 * cnp + 4 * cnp + (double)h->nb + TAB_ELEMS + h->red_len + 4) + 4.0 * h->cap_n + 16.0;
   fixed += d * 2 * h->cap_nt * nn + ct * (4 + 4 + 8 + 4) + 8;               // D, linv, rank, dslot, off, cap
   fixed += d * (double)h->dcap * nn + 8.0 * (double)h->list_cap;            // dense pool, plan lists
   if (h->Dz) fixed += d * h->cap_nt * nn + ct * (4 + 4 + 8 + 4) + 8 + d * (double)h->dcapz * nn +

@@ -658,7 +658,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       if (!src.empty()) ZTRY(oz_split(dsrc, (int)src.size(), nb, max_depth, S, s));
       OzGradCtx gx;
       memset(&gx, 0, sizeof(gx));
-      gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.dtab = h->dtab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;
+      gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;
       ZTRY(oz_gemm(dgem, (int)gem.size(), nb, nb, S, h->d_stat, s, &gx));
     } else {
       PhaseScope ps("lauum.gemm", s);

@@ -68,7 +68,7 @@ __global__ void k_tab_nodes(const MaternParams mp, double* __restrict__ vals) {
 }
 
 // one thread per (function, interval): Chebyshev coefficients -> monomial in t
-__global__ void k_tab_coefs(const double* __restrict__ vals, double* __restrict__ tab, float2* __restrict__ dtab) {
+__global__ void k_tab_coefs(const double* __restrict__ vals, double* __restrict__ tab) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= TAB_NFUN * TAB_NINT) return;
   const double* v = vals + (size_t)id * TAB_NC;
@@ -90,11 +90,6 @@ __global__ void k_tab_coefs(const double* __restrict__ vals, double* __restrict_
   }
   double* out = tab + (size_t)id * TAB_NC;
   for (int d = 0; d < TAB_NC; ++d) out[d] = a[d];
-  if (dtab)  // the same coefficients as double-float pairs (hi = nearest float, lo = the rest)
-    for (int d = 0; d < TAB_NC; ++d) {
-      const float hi = __double2float_rn(a[d]);
-      dtab[(size_t)id * TAB_NC + d] = make_float2(hi, __double2float_rn(a[d] - (double)hi));
-    }
 }
 
 __global__ void k_gen_diag(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
@@ -116,7 +111,7 @@ int tlr_build_table(tlr_ctx* h, cudaStream_t s) {
   const int warps = TAB_NINT * TAB_NC;
   k_tab_nodes<<<(warps * 32 + 255) / 256, 256, 0, s>>>(h->mp, vals);
   TLR_LAUNCH_CHECK();
-  k_tab_coefs<<<(TAB_NFUN * TAB_NINT + 127) / 128, 128, 0, s>>>(vals, h->tab, h->dtab);
+  k_tab_coefs<<<(TAB_NFUN * TAB_NINT + 127) / 128, 128, 0, s>>>(vals, h->tab);
   TLR_LAUNCH_CHECK();
   h->tab_valid = 1;
   return TLR_OK;

@@ -419,19 +419,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restr
               const int jt = tab_locate(rr, gx.mp.e_lo, &t);
               if (jt >= 0 && jt < TAB_NINT) {  // below the table the derivatives vanish
                 const double w = wa * gx.alpha[pb] - zab;
-                // the two derivative polynomials by Horner in double-float (the float64 pipe runs at
-                // 1/64 of the float32 rate): t in [-1, 1], relative error about 13 * 2^-48
-                const dfloat td = df_from_scaled(t, 0);
-                const dfloat* c1 = gx.dtab + (size_t)(TAB_NINT + jt) * TAB_NC;
-                const dfloat* c2 = gx.dtab + (size_t)(2 * TAB_NINT + jt) * TAB_NC;
-                dfloat s1 = c1[TAB_DEG], s2 = c2[TAB_DEG];
-#pragma unroll
-                for (int d = TAB_DEG - 1; d >= 0; --d) {
-                  s1 = df_add(df_mul(s1, td), c1[d]);
-                  s2 = df_add(df_mul(s2, td), c2[d]);
-                }
-                g1 = fma(w, df_to_scaled(s1, 0), g1);
-                g2 = fma(w, df_to_scaled(s2, 0), g2);
+                g1 = fma(w, tab_poly(gx.tab + (size_t)(TAB_NINT + jt) * TAB_NC, t), g1);
+                g2 = fma(w, tab_poly(gx.tab + (size_t)(2 * TAB_NINT + jt) * TAB_NC, t), g2);
               }
             }
           }

@@ -76,7 +76,6 @@ struct OzGradCtx {
   const double* y;
   const double* alpha;  // Sigma^{-1} z in sorted order
   const double* tab;    // Matern table
-  const float2* dtab;   // its coefficients as double-float pairs
   MaternParams mp;
   int64_t n;            // points
   double* part;         // partial sums, 2 per CTA tile
