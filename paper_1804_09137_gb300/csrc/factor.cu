@@ -117,8 +117,7 @@ __global__ void k_gemm_desc(const GemmDesc* __restrict__ desc, int nb) {
 
 size_t tlr_item_elems(int nb, int kcap, int kws) {
   const size_t Kmax = (size_t)kws;
-  // factors, products, cores, scalars and exponents, and the taus of the four-CTA recompression
-  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 8 * Kmax;
+  return 4 * (size_t)nb * Kmax + (size_t)kcap * kcap + 2 * Kmax * Kmax + 4 * Kmax;
 }
 
 static int chunk_for(const tlr_ctx* h, size_t per_item, size_t reserve = 0) {

@@ -25,10 +25,6 @@ struct ItemWs {  // per-item workspace layout (doubles)
   double* s;     // Kmax
   int* eu;       // Kmax column scale exponents of Up
   int* ev;       // Kmax column scale exponents of Vp
-  double* tub;   // Kmax each: taus of the bottom halves' QRs and of the combinations (four-CTA version)
-  double* tvb;
-  double* tuc;
-  double* tvc;
   dfloat* vs;    // shared memory: two staged reflectors, 2 nb (the kernel's dynamic shared memory)
 };
 
@@ -47,11 +43,6 @@ __device__ __forceinline__ ItemWs item_ws(double* base, size_t item_elems, int s
   w.s = p; p += Kmax;
   w.eu = (int*)p;
   w.ev = w.eu + Kmax;
-  p += Kmax;  // 2 Kmax ints
-  w.tub = p; p += Kmax;
-  w.tvb = p; p += Kmax;
-  w.tuc = p; p += Kmax;
-  w.tvc = p;
   w.vs = nullptr;
   return w;
 }
@@ -759,17 +750,13 @@ __device__ __forceinline__ int dsmem_load_int(const int* p, int rank) {
 // cta_recompress.  Returns the new rank on both CTAs (s_k: an int of the caller's shared memory).
 __device__ int cluster_recompress(const ItemWs& w, int nb, int K, double tau, int kcap, int trunc_cap,
                                   const TlrView& v, int64_t t, long long* st, double* sh, int* shi, double* flops,
-                                  int rank, int* s_k, int side = -1, bool worker = true) {
-  // side: 0 U, 1 V (default: the cluster rank); a CTA that is not a worker only takes part in the barriers;
-  // the core runs on cluster rank 0
+                                  int rank, int* s_k) {
   if (K == 0) return 0;
-  if (side < 0) side = rank;
+  const int side = rank;  // 0: U, 1: V
   const int Ke = K < nb ? K : nb;
-  if (worker) {
-    rc_scale_side(w, nb, K, side);
-    cta_geqr2_one_df((dfloat*)(side ? w.Vp : w.Up), side ? w.tv : w.tu, nb, nb, K, w.vs);
-    rc_extract_r(w, nb, K, side);
-  }
+  rc_scale_side(w, nb, K, side);
+  cta_geqr2_one_df((dfloat*)(side ? w.Vp : w.Up), side ? w.tv : w.tu, nb, nb, K, w.vs);
+  rc_extract_r(w, nb, K, side);
   cluster_sync_all();  // both R factors are in the workspace
   if (rank == 0) {
     const int kr = rc_core(w, nb, K, tau, kcap, trunc_cap, v, t, st, sh, shi, flops);
@@ -778,161 +765,12 @@ __device__ int cluster_recompress(const ItemWs& w, int nb, int K, double tau, in
   }
   cluster_sync_all();  // the core's U and V blocks, the arena block and the rank are out
   const int kr = dsmem_load_int(s_k, 0);
-  cluster_sync_all();  // every CTA has read the rank from rank 0's shared memory
-  if (kr > 0 && worker) {
+  cluster_sync_all();  // rank 1 has read the rank from rank 0's shared memory
+  if (kr > 0) {
     cta_apply_q_one_df((const dfloat*)(side ? w.Vp : w.Up), side ? w.tv : w.tu, side ? w.Vq : w.Uq, nb, nb, Ke, nb,
                        kr, w.vs);
     rc_store_side(w, nb, kr, v, t, side);
     if (flops && threadIdx.x == 0) atomicAdd(flops, rc_side_flops(nb, K, kr));
-  }
-  return kr;
-}
-
-// ---- four CTAs of a cluster on one recompression (TSQR: each factor's rows in two halves)
-// Householder QR of the 2K x K stack of two upper triangular K x K factors, T in rows 0..K-1 of A and B in
-// rows h..h+K-1 (column-major, ld lda, double-float), in place: the combined R in T's upper triangle, the
-// reflector of column c in B's rows 0..c of column c (its unit entry on T's row c implied), taus tc.  The
-// entries of A below either triangle (the two halves' own reflectors) are not touched.
-__device__ void cta_tsqr_combine_df(dfloat* __restrict__ A, int lda, int h, int K, double* __restrict__ tc) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __shared__ dfloat sc_tau, sc_scal, red[TLR_MAX_WARPS];
-  __shared__ int sc_on;
-  for (int c = 0; c < K; ++c) {
-    dfloat* col = A + (size_t)c * lda;
-    float ps = 0.f, pc = 0.f;
-    for (int i = threadIdx.x; i <= c; i += blockDim.x) df_dot_add(ps, pc, col[h + i], col[h + i]);
-    const dfloat s1 = df_warp_sum(df_norm(ps, pc));
-    if (lane == 0) red[warp] = s1;
-    __syncthreads();
-    if (threadIdx.x == 0) {  // the reflector's scalars, in float64
-      dfloat tt = red[0];
-      for (int q = 1; q < nw; ++q) tt = df_add(tt, red[q]);
-      const double sig = df_to(tt);
-      const double alpha = df_to(col[c]);
-      double beta = alpha, tcv = 0.0, scal = 1.0;
-      if (sig > 0.0) {
-        beta = -copysign(sqrt(fma(alpha, alpha, sig)), alpha);
-        tcv = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      sc_on = sig > 0.0;
-      sc_tau = df_from(tcv);
-      sc_scal = df_from(scal);
-      tc[c] = tcv;
-      col[c] = df_from(beta);
-    }
-    __syncthreads();
-    const int on = sc_on;
-    const dfloat sc = sc_scal, td = sc_tau;
-    if (on)
-      for (int i = threadIdx.x; i <= c; i += blockDim.x) col[h + i] = df_mul(col[h + i], sc);
-    __syncthreads();
-    if (on)
-      for (int jj = warp; jj < K - c - 1; jj += nw) {
-        dfloat* b = A + (size_t)(c + 1 + jj) * lda;
-        const dfloat bc = b[c];
-        float s = 0.f, e = 0.f;
-        for (int i = lane; i <= c; i += 32) df_dot_add(s, e, col[h + i], b[h + i]);
-        const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), td);
-        if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
-        for (int i = lane; i <= c; i += 32) b[h + i] = df_sub_prod(b[h + i], d, col[h + i]);
-      }
-    __syncthreads();
-  }
-}
-
-// B <- Q_c B for the combination's reflectors (cta_tsqr_combine_df on A, taus tc): B's rows 0..K-1 and
-// h..h+K-1 (ncol columns, ld ldb, double-float), a warp per column
-__device__ void cta_apply_tsqr_combine_df(const dfloat* __restrict__ A, int lda, int h, int K,
-                                          const double* __restrict__ tc, dfloat* __restrict__ B, int ldb,
-                                          int ncol) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int jj = warp; jj < ncol; jj += nw) {
-    dfloat* b = B + (size_t)jj * ldb;
-    for (int c = K - 1; c >= 0; --c) {
-      const double tcv = tc[c];
-      if (tcv == 0.0) continue;
-      const dfloat* v = A + (size_t)c * lda + h;
-      const dfloat bc = b[c];
-      float s = 0.f, e = 0.f;
-      for (int i = lane; i <= c; i += 32) df_dot_add(s, e, v[i], b[h + i]);
-      const dfloat d = df_mul(df_add(df_warp_sum(df_norm(s, e)), bc), df_from_scaled(tcv, 0));
-      if (lane == 0) b[c] = df_add(bc, make_float2(-d.x, -d.y));
-      for (int i = lane; i <= c; i += 32) b[h + i] = df_sub_prod(b[h + i], d, v[i]);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-
-// the rows [r0, r1) of a side's factor from the double-float w.Uq / w.Vq into the tile
-__device__ void rc_store_rows(const ItemWs& w, int nb, int k, const TlrView& v, int64_t t, int side, int r0,
-                              int r1) {
-  double* O = side ? tileV(v, t) : tileU(v, t);
-  const dfloat* Q = side ? w.Vq : w.Uq;
-  const int m = r1 - r0;
-  for (size_t e = threadIdx.x; e < (size_t)m * k; e += blockDim.x) {
-    const size_t c = e / m, r = r0 + e % m;
-    O[c * nb + r] = df_to_scaled(Q[c * nb + r], 0);
-  }
-  __syncthreads();
-}
-
-// Four CTAs of a cluster (ranks 0, 1: U side, rows [0, h) and [h, nb); ranks 2, 3: V side) on the
-// recompression of the rank-K product in the cluster's workspace, K <= min(h, nb - h): the columns'
-// exponents (by the top half) and the conversion of each half's rows, each half's Householder QR, the two
-// R factors combined by the top half (cta_tsqr_combine_df), the core on rank 0, the combination's
-// reflectors applied by the top half, each half's reflectors applied to its rows and the rows stored.
-// Q of a side = diag(Q_top, Q_bottom) Q_combination.  Returns the new rank on every CTA.
-__device__ int cluster4_recompress(const ItemWs& w, int nb, int K, double tau, int kcap, int trunc_cap,
-                                   const TlrView& v, int64_t t, long long* st, double* sh, int* shi,
-                                   double* flops, int rank, int h, int* s_k) {
-  const int side = rank >> 1, half = rank & 1;
-  const int r0 = half ? h : 0, r1 = half ? nb : h, m = r1 - r0;
-  double* P = side ? w.Vp : w.Up;
-  int* ex = side ? w.ev : w.eu;
-  double* tq = half ? (side ? w.tvb : w.tub) : (side ? w.tv : w.tu);
-  double* tc = side ? w.tvc : w.tuc;
-  // column exponents over all rows (the top half), then each half converts its rows
-  if (half == 0) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int j = warp; j < K; j += nw) {
-      const double* col = P + (size_t)j * nb;
-      double mx = 0.0;
-      for (int r = lane; r < nb; r += 32) mx = fmax(mx, fabs(col[r]));
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) ex[j] = (mx > 0.0 && isfinite(mx)) ? ilogb(mx) : 0;
-    }
-  }
-  cluster_sync_all();  // the exponents are out
-  dfloat* D = (dfloat*)P;
-  for (size_t e = threadIdx.x; e < (size_t)m * K; e += blockDim.x) {
-    const size_t c = e / m, r = r0 + e % m;
-    D[c * nb + r] = df_from_scaled(P[c * nb + r], -ex[c]);
-  }
-  __syncthreads();
-  cta_geqr2_one_df(D + r0, tq, nb, m, K, w.vs);
-  cluster_sync_all();  // both halves' R factors are in place
-  if (half == 0) {
-    cta_tsqr_combine_df(D, nb, h, K, tc);
-    rc_extract_r(w, nb, K, side);
-  }
-  cluster_sync_all();  // both combined R factors are in the workspace
-  if (rank == 0) {
-    const int kr = rc_core(w, nb, K, tau, kcap, trunc_cap, v, t, st, sh, shi, flops);
-    if (threadIdx.x == 0) *s_k = kr;
-    __syncthreads();
-  }
-  cluster_sync_all();  // the core's U and V blocks, the arena block and the rank are out
-  const int kr = dsmem_load_int(s_k, 0);
-  cluster_sync_all();  // every CTA has read the rank
-  dfloat* Bq = side ? w.Vq : w.Uq;
-  if (kr > 0 && half == 0) cta_apply_tsqr_combine_df(D, nb, h, K, tc, Bq, nb, kr);
-  cluster_sync_all();  // the combination is applied to both halves' rows
-  if (kr > 0) {
-    cta_apply_q_one_df(D + r0, tq, Bq + r0, nb, m, K, nb, kr, w.vs);
-    rc_store_rows(w, nb, kr, v, t, side, r0, r1);
-    if (flops && threadIdx.x == 0 && half == 0) atomicAdd(flops, rc_side_flops(nb, K, kr));
   }
   return kr;
 }

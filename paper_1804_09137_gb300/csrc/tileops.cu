@@ -239,112 +239,6 @@ __device__ void upd_lr_item_pair(const TlrView& v, int alg, int k, int2 it, doub
   if (rank == 0 && threadIdx.x == 0) v.rank[tt] = kr;
 }
 
-// The update on a cluster of four CTAs: ranks 0 and 1 the U side (top and bottom rows), 2 and 3 the V
-// side; the top half of each side forms the side's product and factor, then cluster4_recompress (or, when
-// the concatenated rank exceeds half a tile, the two-CTA recompression on the top halves).
-__device__ void upd_lr_item_quad(const TlrView& v, int alg, int k, int2 it, double tau, int Kmax, int trunc_cap,
-                                 ItemWs& w, long long* __restrict__ st, double* __restrict__ flops, double* sh,
-                                 int* shi, const double* __restrict__ pre, int rank, int* s_k) {
-  const int nb = v.nb;
-  const int64_t tt = dtile_index(it.x, it.y);
-  Opnd X, Y;
-  double alpha;
-  operands(v, alg, it.x, it.y, k, &X, &Y, &alpha);
-  // every CTA takes the same branches (the same data decide them)
-  if (X.k == 0 || Y.k == 0) return;
-  if (X.dense && Y.dense) {
-    if (rank == 0 && threadIdx.x == 0) set_status(st, TLR_ERR_STATE, tt);
-    return;
-  }
-  const int k0 = v.rank[tt];
-  const int r = X.dense ? Y.k : (Y.dense ? X.k : min(X.k, Y.k));
-  if (k0 + r > Kmax) {
-    if (rank == 0 && threadIdx.x == 0) set_status(st, TLR_ST_WIDEN, tt);
-    return;
-  }
-  const int side = rank >> 1, half = rank & 1;
-  if (half == 0) {
-    double* Pold = side ? tileV(v, tt) : tileU(v, tt);
-    double* P = side ? w.Vp : w.Up;
-    for (size_t e = threadIdx.x; e < (size_t)nb * k0; e += blockDim.x) P[e] = Pold[e];
-    double* Pn = P + (size_t)k0 * nb;
-    double pf = 0.0;
-    if (!X.dense && !Y.dense) {
-      const bool uside = Y.k <= X.k;  // the product goes to U (else to V)
-      if (uside == (side == 0)) {
-        pf = 2.0 * nb * X.k * Y.k * 2.0;
-        const bool thin = X.k <= 48 && Y.k <= 48;
-        if (thin) cta_gemm_tn_thin(X.k, Y.k, nb, 1.0, X.V, Y.U, w.W, X.k);  // W = V_x^T U_y
-        else cta_gemm_df(X.k, Y.k, nb, 1.0, X.V, nb, 1, Y.U, nb, 0, 0.0, w.W, X.k);
-        if (uside) {
-          if (thin) cta_gemm_nn_thin(nb, Y.k, X.k, alpha, X.U, w.W, X.k, 0, Pn);  // U_x W
-          else cta_gemm_df(nb, Y.k, X.k, alpha, X.U, nb, 0, w.W, X.k, 0, 0.0, Pn, nb);
-        } else {
-          if (thin) cta_gemm_nn_thin(nb, X.k, Y.k, 1.0, Y.V, w.W, X.k, 1, Pn);  // V_y W^T
-          else cta_gemm_df(nb, X.k, Y.k, 1.0, Y.V, nb, 0, w.W, X.k, 1, 0.0, Pn, nb);
-        }
-      } else if (side == 1) {
-        for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = Y.V[e];
-      } else {
-        for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = alpha * X.U[e];
-      }
-    } else if (X.dense) {
-      if (side == 0) {
-        pf = pre ? 0.0 : 2.0 * nb * nb * Y.k;
-        if (pre) for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = pre[e];
-        else cta_gemm_df(nb, Y.k, nb, alpha, X.A, nb, X.tA, Y.U, nb, 0, 0.0, Pn, nb);
-      } else {
-        for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = Y.V[e];
-      }
-    } else {
-      if (side == 1) {
-        pf = pre ? 0.0 : 2.0 * nb * nb * X.k;
-        if (pre) for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = pre[e];
-        else cta_gemm_df(nb, X.k, nb, 1.0, Y.A, nb, !Y.tA, X.V, nb, 0, 0.0, Pn, nb);
-      } else {
-        for (size_t e = threadIdx.x; e < (size_t)nb * r; e += blockDim.x) Pn[e] = alpha * X.U[e];
-      }
-    }
-    __syncthreads();
-    if (flops && threadIdx.x == 0 && pf > 0.0) atomicAdd(flops, pf);
-  }
-  const int K = k0 + r;
-  const int h = (nb + 1) / 2;
-  int kr;
-  if (K <= nb - h)
-    kr = cluster4_recompress(w, nb, K, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, flops, rank, h, s_k);
-  else
-    kr = cluster_recompress(w, nb, K, tau, v.kcap, trunc_cap, v, tt, st, sh, shi, flops, rank, s_k, side,
-                            half == 0);
-  if (rank == 0 && threadIdx.x == 0) v.rank[tt] = kr;
-}
-
-// Persistent, in clusters of four CTAs (upd_lr_item_quad); otherwise as k_upd_lr_pair.
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(256, 3)
-    k_upd_lr_quad(TlrView v, int alg, int k, const int2* __restrict__ items, int n_items, int* __restrict__ ctr,
-                  double eps, const double* __restrict__ d_zeta, double zpow, int Kmax, int trunc_cap,
-                  double* __restrict__ ws, size_t item_elems, long long* __restrict__ st, double* __restrict__ flops,
-                  const double* __restrict__ pre, int n_pre) {
-  extern __shared__ dfloat vs_dyn[];  // nb: staged reflectors of this CTA's rows
-  __shared__ double sh[TLR_THREADS / 32 + 2];
-  __shared__ int shi[TLR_THREADS / 32 + 2];
-  __shared__ int s_item, s_k;
-  const int rank = cluster_rank();
-  const double tau = d_zeta ? eps * pow(*d_zeta, zpow) : eps;
-  ItemWs w = item_ws(ws, item_elems, blockIdx.x >> 2, v.nb, Kmax, v.kcap);
-  w.vs = vs_dyn;
-  for (;;) {
-    if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
-    cluster_sync_all();
-    const int q = dsmem_load_int(&s_item, 0);
-    cluster_sync_all();  // every CTA holds q before rank 0 takes the next one
-    if (q >= n_items) break;
-    upd_lr_item_quad(v, alg, k, items[q], tau, Kmax, trunc_cap, w, st, flops, sh, shi,
-                     q < n_pre ? pre + (size_t)q * v.nb * v.kcap : nullptr, rank, &s_k);
-    __syncthreads();
-  }
-}
-
 // Persistent, in clusters of two CTAs: rank 0 takes items in list order from the atomic counter and
 // shares the index through distributed shared memory; both CTAs work on the item (upd_lr_item_pair)
 // with the cluster's workspace.  Every cluster runs the same arithmetic, so results are reproducible.
@@ -664,53 +558,47 @@ namespace {
 // dynamic shared memory of the cluster version (one side's staged reflector)
 size_t pair_smem(int nb) { return (size_t)nb * sizeof(dfloat); }
 
-// CTAs per low-rank update item: 4 (k_upd_lr_quad) by default, 2 (k_upd_lr_pair) or 1 (k_upd_lr_gen)
-// with the environment variable TLR_UPD_CTAS
-int upd_ctas() {
+// items on two-CTA clusters (k_upd_lr_pair) unless the environment variable TLR_UPD_PAIR is 0
+bool upd_pair_mode() {
   static int mode = -1;
   if (mode < 0) {
-    const char* e = getenv("TLR_UPD_CTAS");
-    const int m = e ? atoi(e) : 4;
-    mode = (m == 1 || m == 2) ? m : 4;
+    const char* e = getenv("TLR_UPD_PAIR");
+    mode = (e && atoi(e) == 0) ? 0 : 1;
   }
-  return mode;
+  return mode == 1;
 }
-bool upd_pair_mode() { return upd_ctas() >= 2; }
 
-// resident clusters of k_upd_lr_pair (csize 2) or k_upd_lr_quad (csize 4) on the current device for tile
-// size nb (0 if unavailable)
-int resident_clusters(int nb, int csize) {
+// resident clusters of k_upd_lr_pair on the current device for tile size nb (0 if unavailable)
+int resident_pairs(int nb) {
   static std::mutex mu;
   static std::map<std::pair<int, int>, int> memo;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  const int key = nb * 8 + csize;
   {
     std::lock_guard<std::mutex> lock(mu);
-    auto it = memo.find({dev, key});
+    auto it = memo.find({dev, nb});
     if (it != memo.end()) return it->second;
   }
   int clusters = 0;
-  const void* fn = csize == 4 ? (const void*)k_upd_lr_quad : (const void*)k_upd_lr_pair;
-  if (tlr_smem_optin(fn, pair_smem(nb)) == TLR_OK) {
+  if (tlr_smem_optin((const void*)k_upd_lr_pair, pair_smem(nb)) == TLR_OK) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize * 512);
+    cfg.gridDim = dim3(2 * 1024);
     cfg.blockDim = dim3(TLR_THREADS);
     cfg.dynamicSmemBytes = pair_smem(nb);
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = csize;
+    attr.val.clusterDim.x = 2;
     attr.val.clusterDim.y = 1;
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, (const void*)k_upd_lr_pair, &cfg) != cudaSuccess) {
       cudaGetLastError();
       clusters = 0;
     }
   }
   std::lock_guard<std::mutex> lock(mu);
-  memo[{dev, key}] = clusters;
+  memo[{dev, nb}] = clusters;
   return clusters;
 }
 }  // namespace
@@ -850,20 +738,13 @@ int tops_update(tlr_ctx* h, const TlrView& v, int alg, int k, const int2* d_lr, 
     double* fl = g_tlr_prof.enabled ? g_tlr_prof.d_flops : nullptr;
     const double* pre = staged ? h->dop : nullptr;
     const int n_pre = staged ? (int)std::min(n_dop, n_lr) : 0;
-    const int csize = upd_ctas();
-    const int clusters = csize > 1 ? resident_clusters(h->nb, csize) : 0;
+    const int pairs = upd_pair_mode() ? resident_pairs(h->nb) : 0;
     if (g_tlr_prof.enabled) tlr_prof_begin(s);
-    if (clusters > 0) {  // each item on a cluster of csize CTAs (one workspace a cluster)
-      const int cl = (int)std::min<int64_t>(
-          n_lr, std::min(std::max(clusters - std::max(reserve, 0) / csize, 1), chunk));
-      if (csize == 4)
-        k_upd_lr_quad<<<4 * cl, TLR_THREADS, pair_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps,
-                                                                    d_zeta, zpow, h->kws, h->opts.truncate_at_cap,
-                                                                    h->scratch, ie, h->d_stat, fl, pre, n_pre);
-      else
-        k_upd_lr_pair<<<2 * cl, TLR_THREADS, pair_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps,
-                                                                    d_zeta, zpow, h->kws, h->opts.truncate_at_cap,
-                                                                    h->scratch, ie, h->d_stat, fl, pre, n_pre);
+    if (pairs > 0) {  // each item on a cluster of two CTAs (one workspace a cluster)
+      const int cl = (int)std::min<int64_t>(n_lr, std::min(std::max(pairs - std::max(reserve, 0) / 2, 1), chunk));
+      k_upd_lr_pair<<<2 * cl, TLR_THREADS, pair_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta,
+                                                                  zpow, h->kws, h->opts.truncate_at_cap, h->scratch,
+                                                                  ie, h->d_stat, fl, pre, n_pre);
     } else {
       k_upd_lr_gen<<<grid, TLR_THREADS, upd_smem(h->nb), s>>>(v, alg, k, d_lr, (int)n_lr, h->d_ctr, eps, d_zeta, zpow,
                                                               h->kws, h->opts.truncate_at_cap, h->scratch, ie,
