@@ -340,3 +340,39 @@ def test_great_circle_distance_matches_oracle(T):
         kg = h.predict(dev(z[obs]), dev(lon[held]), dev(lat[held])).cpu().numpy()
         np.testing.assert_allclose(kg, kw, rtol=1e-7, atol=1e-8)
         h.close()
+
+
+_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1804_09137_gb300 import inputs, tlr as T
+from oracle import dense as DN
+theta = (1.0, 0.1, 0.5)
+x, y = inputs.jittered_grid(50)
+z = DN.sample(x, y, theta, inputs.standard_normal(len(x)))
+d = lambda a: torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+h = T.Handle(d(x), d(y), nb=256, eps=1e-9, rank_cap=128, dense_rank=48)
+h.factor(theta)
+ll, g = h.loglik_grad(d(z))
+h.check()
+print(" ".join(float(v).hex() for v in [ll.item(), *g.cpu().numpy()]))
+"""
+
+
+def test_cluster_split_equals_one_cta_bit_for_bit(T):
+    """The low-rank update items split over two-CTA clusters (default) and on one CTA each (the environment
+    variable TLR_UPD_PAIR=0, read once per process) run the same arithmetic: l and the gradient agree bit for
+    bit (n = 2,500, 10 tiles, eps = 1e-9)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for mode in ("1", "0"):
+        env = dict(os.environ, TLR_UPD_PAIR=mode)
+        r = subprocess.run([sys.executable, "-c", _CHILD, root], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out.append(r.stdout.strip().splitlines()[-1])
+    assert out[0] == out[1], out
