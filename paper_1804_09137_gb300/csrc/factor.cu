@@ -60,6 +60,45 @@ __global__ void k_aca_compress(const double* __restrict__ tab, const MaternParam
   if (threadIdx.x == 0) v.rank[t] = kr;
 }
 
+// The same on a cluster of two CTAs per tile: rank 0 runs the cross approximation, then both run the
+// recompression (cluster_recompress: U side on rank 0, V side on rank 1).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 3)
+    k_aca_compress_pair(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
+                        const double* __restrict__ y, int64_t n, TlrView v, int64_t t0, double eps, int aca_max,
+                        int Kmax, int trunc_cap, double* __restrict__ ws, size_t item_elems,
+                        long long* __restrict__ st) {
+  extern __shared__ double dsm[];
+  __shared__ double sh[TLR_THREADS / 32 + 2];
+  __shared__ int shi[TLR_THREADS / 32 + 2];
+  __shared__ int s_aca[2], s_k;
+  const int rank = cluster_rank();
+  const int nb = v.nb;
+  const int q = blockIdx.x >> 1;
+  const int64_t t = t0 + q;
+  int ti, tj;
+  decode_lower(t, &ti, &tj);
+  ItemWs w = item_ws(ws, item_elems, q, nb, Kmax, v.kcap);
+  w.vs = reinterpret_cast<dfloat*>(dsm);  // free after the cross approximation
+  if (rank == 0) {
+    const int64_t pi0 = (int64_t)ti * nb, pj0 = (int64_t)tj * nb;
+    const int mi = (int)min((int64_t)nb, n - pi0), mj = (int)min((int64_t)nb, n - pj0);
+    GenEntry ge{tab, mp, x, y, n, pi0, pj0};
+    int conv = 0;
+    const int k = cta_aca(ge, nb, mi, mj, eps * 0.125, aca_max, w, dsm, sh, shi, &conv);
+    if (threadIdx.x == 0) { s_aca[0] = k; s_aca[1] = conv; }
+    __syncthreads();
+  }
+  cluster_sync_all();  // the cross factors are in the workspace
+  const int k = dsmem_load_int(&s_aca[0], 0), conv = dsmem_load_int(&s_aca[1], 0);
+  cluster_sync_all();  // rank 1 has read them
+  if (!conv) {  // not compressible within aca_max terms: stored dense
+    if (rank == 0 && threadIdx.x == 0) v.rank[t] = -1;
+    return;
+  }
+  const int kr = cluster_recompress(w, nb, k, eps, v.kcap, trunc_cap, v, t, st, sh, shi, nullptr, rank, &s_k);
+  if (rank == 0 && threadIdx.x == 0) v.rank[t] = kr;
+}
+
 // dense generation of listed tiles (Sigma_ij into the dense pool)
 __global__ void k_gen_dense_list(const double* __restrict__ tab, const MaternParams mp, const double* __restrict__ x,
                                  const double* __restrict__ y, int64_t n, TlrView v, const int2* __restrict__ items) {
@@ -133,14 +172,21 @@ int tlr_compress_tiles(tlr_ctx* h, double eps, cudaStream_t s) {
   const int chunk = chunk_for(h, ie);
   if (chunk < 1) TLR_RETURN_OOM();
   const size_t smem = 2 * (size_t)nb * sizeof(double) + (size_t)nb * sizeof(int);
-  if (tlr_smem_optin((const void*)k_aca_compress, smem) != TLR_OK) return TLR_ERR_CUDA;
+  if (tlr_smem_optin((const void*)k_aca_compress, smem) != TLR_OK ||
+      tlr_smem_optin((const void*)k_aca_compress_pair, smem) != TLR_OK)
+    return TLR_ERR_CUDA;
   int aca_max = h->dense_rank + 8;
   if (aca_max > Kmax) aca_max = Kmax;
   const TlrView v = view_of(h);
   for (int64_t t0 = 0; t0 < h->ntiles; t0 += chunk) {
     const int cnt = (int)((h->ntiles - t0) < chunk ? (h->ntiles - t0) : chunk);
-    k_aca_compress<<<cnt, TLR_THREADS, smem, s>>>(h->tab, h->mp, h->x, h->y, h->n, v, t0, eps, aca_max, Kmax,
-                                                   h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
+    if (tops_cluster_mode())
+      k_aca_compress_pair<<<2 * cnt, TLR_THREADS, smem, s>>>(h->tab, h->mp, h->x, h->y, h->n, v, t0, eps, aca_max,
+                                                             Kmax, h->opts.truncate_at_cap, h->scratch, ie,
+                                                             h->d_stat);
+    else
+      k_aca_compress<<<cnt, TLR_THREADS, smem, s>>>(h->tab, h->mp, h->x, h->y, h->n, v, t0, eps, aca_max, Kmax,
+                                                     h->opts.truncate_at_cap, h->scratch, ie, h->d_stat);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;

@@ -603,6 +603,8 @@ int resident_pairs(int nb) {
 }
 }  // namespace
 
+bool tops_cluster_mode() { return upd_pair_mode(); }
+
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip) {
   if (count <= 0) return TLR_OK;
   const int blocks = ((m + 63) / 64) * ((n + 63) / 64);

@@ -42,6 +42,9 @@ int tops_trinv(const double* T, int nb, double* X, cudaStream_t s);
 // Allows kernel f to start with dyn bytes of dynamic shared memory: above the default 48 KB per block
 // (static plus dynamic) the kernel must opt in.  TLR_OK or TLR_ERR_CUDA.
 int tlr_smem_optin(const void* f, size_t dyn);
+// true when recompressions run on two-CTA clusters (the default; the environment variable TLR_UPD_PAIR=0
+// selects one CTA each)
+bool tops_cluster_mode();
 // batched general GEMM from a device descriptor array
 // (descriptors with k >= k_skip are left out: another path computes them)
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30);
