@@ -20,6 +20,7 @@ constexpr int PB = 32;  // panel width of the tile Cholesky
 __global__ void __launch_bounds__(256, 2) k_potrf_tile(double* __restrict__ A, int lda, int nb, int64_t col0,
                                                        long long* __restrict__ st, unsigned int* __restrict__ bar) {
   __shared__ double Ls[PB][PB + 1];
+  __shared__ double Linv[PB];  // reciprocals of the diagonal block's pivots
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned int target = 0;
   for (int c0 = 0; c0 < nb; c0 += PB) {
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_tile(double* __restrict__ A, i
           __syncwarp();
         }
         for (int q = lane + 1; q < PB; ++q) Ls[lane][q] = 0.0;
+        Linv[lane] = 1.0 / Ls[lane][lane];
       }
       __syncthreads();
       if (blockIdx.x == 0)
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256, 2) k_potrf_tile(double* __restrict__ A, i
         const int r = c1 + rr;
         double x = lane < w ? A[(size_t)(c0 + lane) * lda + r] : 0.0;
         for (int c = 0; c < w; ++c) {
-          const double xc = __shfl_sync(0xffffffffu, x, c) / Ls[c][c];
+          const double xc = __shfl_sync(0xffffffffu, x, c) * Linv[c];
           if (lane == c) x = xc;
           else if (lane > c) x = fma(-xc, Ls[lane][c], x);
         }

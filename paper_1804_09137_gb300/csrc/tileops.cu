@@ -331,7 +331,7 @@ __global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
 // X = T^{-1} for a lower triangular nb x nb tile T (both column-major, ld nb) by forward
 // substitution on the identity, TRINV_COLS columns per CTA.  Column block c0 is zero above
 // row c0 and stays so: the sweep starts at the 32-row block holding c0.
-#define TRINV_COLS 8
+#define TRINV_COLS 2
 __global__ void k_trinv(const double* __restrict__ T, int nb, double* __restrict__ X) {
   __shared__ double Ls[32][33];
   __shared__ double Xs[32][TRINV_COLS + 1];
