@@ -655,7 +655,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       if (!src.empty())
         TLR_CUDA_TRY(cudaMemcpyAsync(dsrc, src.data(), src.size() * sizeof(OzSrc), cudaMemcpyHostToDevice, s));
       TLR_CUDA_TRY(cudaMemcpyAsync(dgem, gem.data(), gem.size() * sizeof(OzGemm), cudaMemcpyHostToDevice, s));
-      if (!src.empty()) ZTRY(oz_split(dsrc, (int)src.size(), nb, max_depth, S, s));
+      if (!src.empty()) ZTRY(oz_split(dsrc, (int)src.size(), nb, max_depth, S, s, true));
       OzGradCtx gx;
       memset(&gx, 0, sizeof(gx));
       gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;

@@ -1,9 +1,13 @@
 // Float64-accurate GEMM on the bf16 tensor cores (see tcgemm.h for the method).
 //
-// k_oz_rowexp / k_oz_split: per-row power-of-two scale and 8-bit digit slices of
-// each operand, written in the K-major core-matrix layout of the tensor core
-// (8 rows x 16 bytes per core matrix, the four core matrices of a row group along
-// K adjacent), one contiguous block per (row block, k block) holding all slices.
+// k_oz_slice / k_oz_slice_gen: per-row power-of-two scale and 8-bit digit slices of
+// each operand in one pass (a CTA finds the exponents of its 32 rows over the whole
+// depth, then slices its share of the depth), written in the K-major core-matrix
+// layout of the tensor core (8 rows x 16 bytes per core matrix, the four core
+// matrices of a row group along K adjacent), one contiguous block per (row block,
+// k block) holding all slices.  An operand made of several segments along k takes
+// two passes instead (k_oz_rowexp, exponents by atomic maximum over the segments,
+// then k_oz_split).
 //
 // k_oz_gemm: one CTA per 128 x 64 output tile, three warp roles:
 //   warp 0      producer: one bulk (TMA) copy per operand and stage into a
@@ -240,6 +244,105 @@ __global__ void k_oz_split(const OzSrc* __restrict__ srcs) {
   }
 }
 
+// One pass for an operand that is a single segment: a CTA of 32 x 8 threads takes the 32 rows
+// r0 .. r0 + 31, finds their exponents over the whole depth, then writes the slices of the k octets
+// [q0, q1) (thread (row, y) the octets y, y + 8, ...).  The exponents are stored by the CTAs with
+// q0 = 0.  A CTA beyond the operand's padded rows returns at once (uniformly).
+template <int S>
+__device__ __forceinline__ void slice_rows(const OzSrc& d, int r0, int q0, int q1) {
+  __shared__ int part[8][33];
+  __shared__ int rowE[32];
+  const int BR = d.block_rows;
+  const int rows_pad = round_up(d.rows, BR);
+  if (r0 >= rows_pad) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (d.col) {  // element (r, k) at X[k ld + r]: a warp reads 32 rows of one k
+    const int r = r0 + tx;
+    int E = 0;
+    if (r < d.rows)
+      for (int k = ty; k < d.depth; k += 8) E = max(E, dexp(d.X[(size_t)k * d.ld + r]));
+    part[ty][tx] = E;
+    __syncthreads();
+    if (ty == 0) {
+#pragma unroll
+      for (int i = 1; i < 8; ++i) E = max(E, part[i][tx]);
+      rowE[tx] = E;
+    }
+  } else {  // element (r, k) at X[r ld + k]: warp y reads the rows y, y + 8, y + 16, y + 24 along k
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rr = ty + 8 * i, r = r0 + rr;
+      int E = 0;
+      if (r < d.rows)
+        for (int k = tx; k < d.depth; k += 32) E = max(E, dexp(d.X[(size_t)r * d.ld + k]));
+      for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+      if (tx == 0) rowE[rr] = E;
+    }
+  }
+  __syncthreads();
+  const int r = r0 + tx;
+  const int E = rowE[tx];
+  if (q0 == 0 && ty == 0) d.ex[r] = E;
+  const int depth_pad = round_up(d.depth, OZ_BK);
+  const int qend = min(q1, depth_pad / 8);
+  const int nkb = d.nkb > 0 ? d.nkb : depth_pad / OZ_BK;
+  const int rb = r / BR, rr = r % BR;
+  const size_t tile = (size_t)BR * OZ_BK;  // bf16 per slice tile
+  for (int q = q0 + ty; q < qend; q += 8) {
+    uint32_t w[S][4];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[s][i] = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = q * 8 + j;
+      double x = 0.0;
+      if (r < d.rows && k < d.depth) x = d.col ? d.X[(size_t)k * d.ld + r] : d.X[(size_t)r * d.ld + k];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+      const int e = (int)((b >> 52) & 0x7ff);
+      unsigned long long F = 0ull;  // |x| 2^-(E - 1022) as a fraction with 64 bits
+      if (e != 0 && e != 0x7ff) {
+        const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = E - e;
+        F = sh <= 11 ? (mant << (11 - sh)) : (sh - 11 < 64 ? (mant >> (sh - 11)) : 0ull);
+      }
+      const uint32_t sgn = (uint32_t)(b >> 63) << 31;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const uint32_t dg = (uint32_t)(F >> (56 - 8 * s)) & 0xffu;
+        const float v = (float)dg * __int_as_float((127 - 8 * (s + 1)) << 23);
+        const uint32_t h = dg ? ((sgn | (uint32_t)__float_as_int(v)) >> 16) : 0u;
+        w[s][j >> 1] |= h << (16 * (j & 1));
+      }
+    }
+    const int kb = d.kb0 + (q * 8) / OZ_BK, kq = ((q * 8) % OZ_BK) / 8;
+    const size_t in_tile = (size_t)((rr >> 3) * (OZ_BK / 8) + kq) * 64 + (size_t)(rr & 7) * 8;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      uint16_t* dst = d.out + (((size_t)rb * nkb + kb) * S + s) * tile + in_tile;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    }
+  }
+}
+
+// single-segment operands described on the device: blockIdx.z the operand, blockIdx.y the depth chunk
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_slice(const OzSrc* __restrict__ srcs, int qpc) {
+  const OzSrc d = srcs[blockIdx.z];
+  slice_rows<S>(d, blockIdx.x * 32, blockIdx.y * qpc, (blockIdx.y + 1) * qpc);
+}
+
+// k octets per depth chunk so that rows32 x count x chunks CTAs fill the GPU about twice
+inline int slice_chunk_octets(int rows_pad, int depth_pad, int count) {
+  const int Q = depth_pad / 8;
+  const long long ctas = (long long)(rows_pad / 32) * count;
+  const long long target = 2432;  // 152 SMs x 8 resident CTAs of 256 threads x 2
+  int nz = ctas >= target ? 1 : (int)((target + ctas - 1) / ctas);
+  nz = std::max(1, std::min(nz, (Q + 7) / 8));
+  return round_up((Q + nz - 1) / nz, 8);
+}
+
 // ------------------------------------------------------------------ GEMM
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restrict__ descs, int tiles_m,
@@ -462,15 +565,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_gemm(const OzGemm* __restr
 }
 
 template <int S>
-int launch_split(const OzSrc* d_src, int count, int max_rows, int max_depth, cudaStream_t s) {
+int launch_split(const OzSrc* d_src, int count, int max_rows, int max_depth, bool segments, cudaStream_t s) {
   const int rows_pad = round_up(std::max(max_rows, 1), OZ_BM);
   const int depth_pad = round_up(std::max(max_depth, 1), OZ_BK);
   for (int c0 = 0; c0 < count; c0 += 65535) {
     const int cnt = std::min(65535, count - c0);
+    const dim3 blk(32, 8);
+    if (!segments) {  // exponents and slices in one pass
+      const int qpc = slice_chunk_octets(rows_pad, depth_pad, cnt);
+      k_oz_slice<S><<<dim3(rows_pad / 32, (depth_pad / 8 + qpc - 1) / qpc, cnt), blk, 0, s>>>(d_src + c0, qpc);
+      TLR_LAUNCH_CHECK();
+      continue;
+    }
     // a warp per row covers both source orientations of the exponent pass
     k_oz_rowexp<<<dim3((rows_pad * 32 + 255) / 256, cnt), 256, 0, s>>>(d_src + c0);
     TLR_LAUNCH_CHECK();
-    const dim3 blk(32, 8);
     const dim3 grid((rows_pad + 31) / 32, (depth_pad / 8 + 7) / 8, cnt);
     k_oz_split<S><<<grid, blk, 0, s>>>(d_src + c0);
     TLR_LAUNCH_CHECK();
@@ -509,12 +618,12 @@ size_t oz_slices_elems(int rows, int depth, int block_rows, int S) {
   return (size_t)round_up(std::max(rows, 1), block_rows) * round_up(std::max(depth, 1), OZ_BK) * S;
 }
 
-int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s) {
+int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s, bool segments) {
   if (count <= 0) return TLR_OK;
   switch (S) {
-    case 4: return launch_split<4>(d_src, count, max_rows, max_depth, s);
-    case 5: return launch_split<5>(d_src, count, max_rows, max_depth, s);
-    case 6: return launch_split<6>(d_src, count, max_rows, max_depth, s);
+    case 4: return launch_split<4>(d_src, count, max_rows, max_depth, segments, s);
+    case 5: return launch_split<5>(d_src, count, max_rows, max_depth, segments, s);
+    case 6: return launch_split<6>(d_src, count, max_rows, max_depth, segments, s);
     default: return -1;
   }
 }
@@ -626,35 +735,30 @@ __device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_mi
   og->alpha = x.alpha; og->beta = x.beta; og->lower = x.lower;
 }
 
-// the exponent pass of operand blockIdx.y (descriptor y / 2, side y % 2) straight from the GEMM
-// descriptors; the first CTA of each operand also stores its split descriptor (and side 0 the GEMM
-// descriptor) for the slice and product kernels
-__global__ void k_oz_rowexp_gen(const GemmGen* __restrict__ g, int k_min, char* __restrict__ base, size_t sa_bytes,
-                                size_t sb_bytes, size_t xa_bytes, size_t per, OzSrc* __restrict__ src,
-                                OzGemm* __restrict__ gem) {
-  const int y = blockIdx.y, q = y >> 1;
+// exponents and slices of operand blockIdx.z (descriptor z / 2, side z % 2) straight from the GEMM
+// descriptors, depth chunk blockIdx.y; the first CTA of each side-0 operand also stores the GEMM
+// descriptor for the product kernel
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_slice_gen(const GemmGen* __restrict__ g, int k_min, char* __restrict__ base,
+                                                      size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per,
+                                                      OzGemm* __restrict__ gem, int qpc) {
+  const int z = blockIdx.z, q = z >> 1;
   OzSrc a, b;
   OzGemm og;
   descs_from_gen(g[q], q, k_min, base, sa_bytes, sb_bytes, xa_bytes, per, &a, &b, &og);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    src[y] = (y & 1) ? b : a;
-    if (!(y & 1)) gem[q] = og;
-  }
-  rowexp_body((y & 1) ? b : a);
+  if (!(z & 1) && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) gem[q] = og;
+  slice_rows<S>((z & 1) ? b : a, blockIdx.x * 32, blockIdx.y * qpc, (blockIdx.y + 1) * qpc);
 }
 
 template <int S>
 int launch_split_gen(const GemmGen* d_g, int cnt, int k_min, char* base, size_t sa, size_t sb, size_t xa, size_t per,
-                     OzSrc* src, OzGemm* gem, int max_rows, int max_depth, cudaStream_t s) {
+                     OzGemm* gem, int max_rows, int max_depth, cudaStream_t s) {
   const int rows_pad = round_up(std::max(max_rows, 1), OZ_BM);
   const int depth_pad = round_up(std::max(max_depth, 1), OZ_BK);
   // 2 cnt operands; callers keep cnt <= 32767
-  k_oz_rowexp_gen<<<dim3((rows_pad * 32 + 255) / 256, 2 * cnt), 256, 0, s>>>(d_g, k_min, base, sa, sb, xa, per, src,
-                                                                            gem);
-  TLR_LAUNCH_CHECK();
-  const dim3 blk(32, 8);
-  const dim3 grid((rows_pad + 31) / 32, (depth_pad / 8 + 7) / 8, 2 * cnt);
-  k_oz_split<S><<<grid, blk, 0, s>>>(src);
+  const int qpc = slice_chunk_octets(rows_pad, depth_pad, 2 * cnt);
+  k_oz_slice_gen<S><<<dim3(rows_pad / 32, (depth_pad / 8 + qpc - 1) / qpc, 2 * cnt), dim3(32, 8), 0, s>>>(
+      d_g, k_min, base, sa, sb, xa, per, gem, qpc);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }
@@ -681,13 +785,12 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
   for (int q0 = 0; q0 < count; q0 += chunk) {
     const int cnt = std::min(chunk, count - q0);
     char* descs = reinterpret_cast<char*>(align128(reinterpret_cast<size_t>(base + (size_t)cnt * per)));
-    OzSrc* src = reinterpret_cast<OzSrc*>(descs);
     OzGemm* gem = reinterpret_cast<OzGemm*>(descs + align128((size_t)2 * cnt * sizeof(OzSrc)));
     int rc;
     switch (S) {
-      case 4: rc = launch_split_gen<4>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
-      case 5: rc = launch_split_gen<5>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
-      case 6: rc = launch_split_gen<6>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, src, gem, std::max(max_m, max_n), max_k, s); break;
+      case 4: rc = launch_split_gen<4>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
+      case 5: rc = launch_split_gen<5>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
+      case 6: rc = launch_split_gen<6>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
       default: rc = -1;
     }
     if (rc) return rc;

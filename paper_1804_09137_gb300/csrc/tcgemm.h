@@ -15,7 +15,7 @@
 // Pairs with j + l >= S are dropped.  The error is at most about
 // (S + 1) 2^-8S k max|a_row| max|b_col| (S = 6: ~2^-45 relative to that scale).
 //
-// The split is a separate pass (k_oz_split) that writes the slices in the
+// The split is a separate pass before the GEMM that writes the slices in the
 // tensor core's K-major core-matrix layout, tile by tile, so that the GEMM moves
 // each tile into shared memory with one bulk (TMA) copy per operand and stage.
 #pragma once
@@ -94,8 +94,11 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
                   size_t ws_bytes, long long* d_stat, cudaStream_t s);
 // bytes of workspace oz_run_device needs per descriptor for these bounds
 size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S);
-// split `count` operands (descriptors on the device); max_rows / max_depth bound the grid
-int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s);
+// split `count` operands (descriptors on the device); max_rows / max_depth bound the grid.
+// segments: some operand is made of several segments (multi = 1), so the exponents are found in a
+// pass of their own before the slices; otherwise one pass does both.
+int oz_split(const OzSrc* d_src, int count, int max_rows, int max_depth, int S, cudaStream_t s,
+             bool segments = false);
 // batched GEMMs (descriptors on the device); tiles of the largest m x n; status words for time-outs
 int oz_gemm(const OzGemm* d_desc, int count, int max_m, int max_n, int S, long long* d_stat, cudaStream_t s,
             const OzGradCtx* gctx = nullptr);
