@@ -172,6 +172,10 @@ void free_ctx(tlr_ctx* h) {
 
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_lz[i]) cudaEventDestroy(h->ev_lz[i]);
+    if (h->ev_lg[i]) cudaEventDestroy(h->ev_lg[i]);
+  }
   free(h->kind);
   free(h->h_list);
   free(h->plan_off);

@@ -134,6 +134,7 @@ struct tlr_ctx {
   // second stream of the inverse (dense x dense products overlap the other updates of a step)
   cudaStream_t aux;
   cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_lz[2], ev_lg[2];  // LAUUM: a batch's tiles of Sigma^{-1} written / reduced
   double* scratch_dd;
   size_t scratch_dd_elems;
   // copy of the inverse's dense sources (diagonal and dense tiles) read by LAUUM
@@ -374,6 +375,10 @@ int tlr_inverse(tlr_ctx* h, cudaStream_t s, const double* alpha = nullptr, doubl
 // out2[0] = sum part[2 i], out2[1] = sum part[2 i + 1] over i < count, in a fixed order (ws: 512 doubles)
 int tlr_sum_pairs(const double* part, int64_t count, double* out2, double* ws, cudaStream_t s);
 int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s);
+// dl/dbeta, dl/dnu partial pairs of `cnt` dense tiles of Sigma^{-1} (Z + t nb^2, targets tg[t] on the
+// device), block b of tile t into part[2 (slot0 + t mb^2 + b)], mb = ceil(nb / 64)
+int tlr_grad_tiles(const tlr_ctx* h, const int2* tg, int cnt, const double* Z, int64_t slot0, const double* alpha,
+                   double* part, cudaStream_t s);
 int tlr_predict_var_sorted(tlr_ctx* h, int64_t m, const double* xn, const double* yn, double* var, cudaStream_t s);
 int tlr_krige(tlr_ctx* h, const double* a, int64_t m, const double* xn, const double* yn, double* zn,
               cudaStream_t s);

@@ -109,6 +109,57 @@ __global__ void k_grad_fused(TlrView z, const double* __restrict__ tab, const Ma
   }
 }
 
+// The same sums over a batch of dense tiles of Z = Sigma^{-1} (the LAUUM's products, nb x nb each,
+// column-major, tile t of the batch at Z + t nb^2, target (m, n) = tg[t]): CTA (blk, t) takes the
+// 64 x 64 block blk of tile t, thread (row a, column parity) its 32 entries (a, c0 + parity + 2 j), so
+// each warp reads 32 consecutive rows of one column.  The partial pair goes to part[2 (slot0 + t mb^2 +
+// blk)], written even for a block with nothing to add.
+__global__ void __launch_bounds__(128) k_grad_tiles(const int2* __restrict__ tg, const double* __restrict__ Z, int nb,
+                                                    int64_t slot0, const double* __restrict__ tab,
+                                                    const MaternParams mp, const double* __restrict__ x,
+                                                    const double* __restrict__ y, int64_t n,
+                                                    const double* __restrict__ al, double* __restrict__ part) {
+  __shared__ double sh[4][2];
+  const int mb = (nb + 63) / 64;
+  const int t = blockIdx.y;
+  const int2 mn = tg[t];
+  const int bi = blockIdx.x % mb, bj = blockIdx.x / mb;
+  const int r0 = bi * 64, c0 = bj * 64;
+  const bool diag = mn.x == mn.y;
+  double g1 = 0.0, g2 = 0.0;
+  const int a = r0 + (threadIdx.x & 63);
+  const int64_t pa = (int64_t)mn.x * nb + a;
+  if (!(diag && r0 + 63 < c0) && a < nb && pa < n) {
+    const double* Zt = Z + (size_t)t * nb * nb;
+    const double xa = x[pa], ya = y[pa], wa = al[pa];
+    for (int j = 0; j < 32; ++j) {
+      const int b = c0 + (threadIdx.x >> 6) + 2 * j;
+      const int64_t pb = (int64_t)mn.y * nb + b;
+      if (b >= nb || pb >= n || (diag && b >= a)) continue;  // dC_beta(0) = dC_nu(0) = 0
+      const double r = pt_dist(mp, xa, ya, x[pb], y[pb]);
+      if (!(r > 0.0)) continue;
+      double tt;
+      const int jt = tab_locate(r, mp.e_lo, &tt);
+      if (jt < 0 || jt >= TAB_NINT) continue;  // below the table the derivatives vanish
+      const double w = wa * al[pb] - Zt[(size_t)b * nb + a];
+      g1 = fma(w, tab_poly(tab + (size_t)(TAB_NINT + jt) * TAB_NC, tt), g1);
+      g2 = fma(w, tab_poly(tab + (size_t)(2 * TAB_NINT + jt) * TAB_NC, tt), g2);
+    }
+  }
+  g1 = warp_sum(g1);
+  g2 = warp_sum(g2);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[warp][0] = g1; sh[warp][1] = g2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < 4; ++i) { s1 += sh[i][0]; s2 += sh[i][1]; }
+    double* p = part + 2 * (slot0 + (int64_t)t * mb * mb + blockIdx.x);
+    p[0] = s1;
+    p[1] = s2;
+  }
+}
+
 __global__ void k_sum3_stage(const double* __restrict__ part, int64_t cnt, double* __restrict__ out) {
   __shared__ double sh[TLR_THREADS / 32 + 2];
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -168,6 +219,16 @@ int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s
   k_sum3_stage<<<nstage, TLR_THREADS, 0, s>>>(part, cnt, stage);
   TLR_LAUNCH_CHECK();
   k_sum3_stage<<<1, TLR_THREADS, 0, s>>>(stage, nstage, out3);
+  TLR_LAUNCH_CHECK();
+  return TLR_OK;
+}
+
+int tlr_grad_tiles(const tlr_ctx* h, const int2* tg, int cnt, const double* Z, int64_t slot0, const double* alpha,
+                   double* part, cudaStream_t s) {
+  if (cnt <= 0) return TLR_OK;
+  if (cnt > 65535) return TLR_ERR_STATE;
+  const int mb = (h->nb + 63) / 64;
+  k_grad_tiles<<<dim3(mb * mb, cnt), 128, 0, s>>>(tg, Z, h->nb, slot0, h->tab, h->mp, h->x, h->y, h->n, alpha, part);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }

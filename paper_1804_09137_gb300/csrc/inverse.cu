@@ -312,7 +312,23 @@ static int seg_copy(const CopySeg* d_segs, int64_t n, cudaStream_t s) {
 // of depth sum(rank) written once; dense x dense products are added afterwards, one
 // GEMM per tile and launch.  Z overwrites the dense sources' slots, so those (and the
 // diagonal) are read from a copy.  Workspace: h->scratch (descriptors, G, panels).
-static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* out3) {
+static int ensure_aux(tlr_ctx* h, int items);
+
+// LAUUM with the gradient: the tensor-core products of a batch write its tiles of Sigma^{-1} into one of
+// two buffers and a CUDA-core kernel on another stream reduces them into the gradient while the next
+// batch's products run (the float64 derivative work beside the tensor cores), unless the environment
+// variable TLR_LAUUM_OVERLAP is 0 (then the product kernel's epilogue does the reduction itself)
+static bool lauum_overlap_mode() {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = getenv("TLR_LAUUM_OVERLAP");
+    mode = (e && atoi(e) == 0) ? 0 : 1;
+  }
+  return mode == 1;
+}
+
+static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, double* out3) {
+  cudaStream_t s = s_user;  // the LAUUM's own stream (the second, higher-priority one when overlapping)
   const int nt = h->nt, nb = h->nb;
   const int64_t T = h->ntiles;
   const size_t nn = (size_t)nb * nb;
@@ -330,6 +346,8 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
   // tensor-core epilogue, and the dense sources are read where TRTRI left them (Dz, compact dense pool)
   const int S = tlr_tc_slices(h);
   const bool fused = S > 0 && alpha && out3;
+  const bool overlap = fused && lauum_overlap_mode();
+  const int mb64 = (nb + 63) / 64;  // 64 x 64 blocks a side of a tile (the batch reduction's partials)
   const size_t msave_want = fused ? 0 : (size_t)(nt + nd) * nn;
   if (msave_want > h->msave_elems) {
     if (h->msave) cudaFree(h->msave);
@@ -408,10 +426,12 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
   auto tgt_slices = [&](size_t q) -> size_t {
     return fused ? slice_dbl(fdepth(q)) + (size_t)ndd[q] * (2 * sizeof(OzSrc) + 7) / 8 : slice_dbl(depth[q]);
   };
-  // partial sums of the fused gradient: eight per CTA tile of every target
+  // partial sums of the fused gradient: eight per CTA tile of every target (two per 64 x 64 block when
+  // overlapping, then the targets' list after them)
   const int tiles_per = ((nb + OZ_BM - 1) / OZ_BM) * ((nb + OZ_BN - 1) / OZ_BN);
+  const int64_t part_pairs = overlap ? (int64_t)tg.size() * mb64 * mb64 : (int64_t)tg.size() * tiles_per * 4;
   if (fused) {
-    const size_t want = (size_t)tg.size() * tiles_per * 8;
+    const size_t want = 2 * (size_t)part_pairs + (overlap ? tg.size() : 0);
     if (want > h->gpart_elems) {
       if (h->gpart) cudaFree(h->gpart);
       h->gpart = nullptr;
@@ -422,7 +442,12 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       }
       h->gpart_elems = want;
     }
-    TLR_CUDA_TRY(cudaMemsetAsync(h->gpart, 0, want * sizeof(double), s));
+    TLR_CUDA_TRY(cudaMemsetAsync(h->gpart, 0, 2 * (size_t)part_pairs * sizeof(double), s));
+  }
+  const int2* d_tg = overlap ? reinterpret_cast<const int2*>(h->gpart + 2 * part_pairs) : nullptr;
+  if (overlap) {
+    static_assert(sizeof(int2) == sizeof(double), "one target a double");
+    TLR_CUDA_TRY(cudaMemcpyAsync((void*)d_tg, tg.data(), tg.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
   }
   // one target alone must fit (with the reserve for a full-depth product): grow the workspace if not
   {
@@ -432,7 +457,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
                          2 * (size_t)nb * depth[q] + 8 + tgt_slices(q);
       worst = std::max(worst, per);
     }
-    worst += 64 + slice_dbl(nb);
+    worst += 64 + slice_dbl(nb) + (overlap ? 2 * nn + 32 : 0);
     if (worst > h->scratch_elems) {
       TLR_CUDA_TRY(cudaStreamSynchronize(s));
       cudaFree(h->scratch);
@@ -446,7 +471,41 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       h->scratch_elems = want;
     }
   }
-  const size_t budget = h->scratch_elems;
+  size_t budget = h->scratch_elems;
+  // overlapping: two buffers of zcap tiles of Sigma^{-1} at the top of the workspace, zcap chosen so that
+  // the targets' average preparation needs and their tiles share it
+  size_t zcap = 0;
+  double* zb2[2] = {nullptr, nullptr};
+  if (overlap && !tg.empty()) {
+    size_t tot = 0;
+    for (size_t q = 0; q < tg.size(); ++q)
+      tot += (size_t)(nt - tg[q].x) * (3 * gd + cd + 2) + gd + (size_t)gel[q] + 2 * (size_t)nb * depth[q] + 8 +
+             tgt_slices(q);
+    const size_t avg = tot / tg.size() + 1;
+    const size_t fixed = 64 + slice_dbl(nb) + 32;
+    zcap = budget > fixed ? (budget - fixed) / (avg + 2 * nn) : 0;
+    zcap = std::max<size_t>(1, std::min<size_t>(zcap, std::min<size_t>(tg.size(), 65535)));
+    size_t worst1 = 0;
+    for (size_t q = 0; q < tg.size(); ++q)
+      worst1 = std::max(worst1, (size_t)(nt - tg[q].x) * (3 * gd + cd + 2) + gd + (size_t)gel[q] +
+                                    2 * (size_t)nb * depth[q] + 8 + tgt_slices(q));
+    while (zcap > 1 && worst1 + fixed + 2 * zcap * nn > budget) --zcap;
+    budget -= 2 * zcap * nn + 32;
+    double* zr = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(h->scratch + budget) + 127) & ~(uintptr_t)127);
+    zb2[0] = zr;
+    zb2[1] = zr + zcap * nn;
+    // the batch loop runs on the second stream (after everything so far on the caller's), the reductions
+    // on the caller's
+    ZTRY(ensure_aux(h, 0));
+    for (int i = 0; i < 2; ++i) {
+      if (!h->ev_lz[i]) TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_lz[i], cudaEventDisableTiming));
+      if (!h->ev_lg[i]) TLR_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_lg[i], cudaEventDisableTiming));
+    }
+    TLR_CUDA_TRY(cudaEventRecord(h->ev_fork, s_user));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    s = h->aux;
+  }
+  int nbatch = 0;
   size_t b0 = 0;
   std::vector<char> host;
   while (b0 < tg.size()) {
@@ -457,7 +516,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
       const int m = tg[b1].x;
       const size_t per = (size_t)(nt - m) * (3 * gd + cd + 2) + gd + (size_t)gel[b1] + 2 * (size_t)nb * depth[b1] + 8 +
                          tgt_slices(b1);
-      if (b1 > b0 && need + per > budget) break;
+      if (b1 > b0 && (need + per > budget || (overlap && b1 - b0 >= zcap))) break;
       need += per;
       ++b1;
     }
@@ -611,9 +670,14 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
         OzGemm og;
         memset(&og, 0, sizeof(og));
         og.m = nb; og.n = nb; og.ldc = nb; og.alpha = 1.0; og.beta = 0.0;
-        og.mode = 1; og.diag = m == n; og.lower = m == n;
-        og.p0a = (int64_t)m * nb; og.p0b = (int64_t)n * nb;
-        og.part_off = (int64_t)q * tiles_per;
+        og.lower = m == n;
+        if (overlap) {  // the tile of Sigma^{-1} into this batch's buffer
+          og.C = zb2[nbatch & 1] + (q - b0) * nn;
+        } else {
+          og.mode = 1; og.diag = m == n;
+          og.p0a = (int64_t)m * nb; og.p0b = (int64_t)n * nb;
+          og.part_off = (int64_t)q * tiles_per;
+        }
         if (nkb > 0) {
           sp = align(sp);
           uint16_t* sa = reinterpret_cast<uint16_t*>(sp);
@@ -656,10 +720,24 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
         TLR_CUDA_TRY(cudaMemcpyAsync(dsrc, src.data(), src.size() * sizeof(OzSrc), cudaMemcpyHostToDevice, s));
       TLR_CUDA_TRY(cudaMemcpyAsync(dgem, gem.data(), gem.size() * sizeof(OzGemm), cudaMemcpyHostToDevice, s));
       if (!src.empty()) ZTRY(oz_split(dsrc, (int)src.size(), nb, max_depth, S, s, true));
-      OzGradCtx gx;
-      memset(&gx, 0, sizeof(gx));
-      gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;
-      ZTRY(oz_gemm(dgem, (int)gem.size(), nb, nb, S, h->d_stat, s, &gx));
+      if (overlap) {
+        // the buffer's previous batch has been reduced; this batch's tiles are reduced on the caller's
+        // stream while the next batch is prepared and multiplied here
+        const int par = nbatch & 1;
+        if (nbatch >= 2) TLR_CUDA_TRY(cudaStreamWaitEvent(s, h->ev_lg[par], 0));
+        ZTRY(oz_gemm(dgem, (int)gem.size(), nb, nb, S, h->d_stat, s));
+        TLR_CUDA_TRY(cudaEventRecord(h->ev_lz[par], s));
+        TLR_CUDA_TRY(cudaStreamWaitEvent(s_user, h->ev_lz[par], 0));
+        ZTRY(tlr_grad_tiles(h, d_tg + b0, (int)(b1 - b0), zb2[par], (int64_t)b0 * mb64 * mb64, alpha, h->gpart,
+                            s_user));
+        TLR_CUDA_TRY(cudaEventRecord(h->ev_lg[par], s_user));
+        ++nbatch;
+      } else {
+        OzGradCtx gx;
+        memset(&gx, 0, sizeof(gx));
+        gx.x = h->x; gx.y = h->y; gx.alpha = alpha; gx.tab = h->tab; gx.mp = h->mp; gx.n = h->n; gx.part = h->gpart;
+        ZTRY(oz_gemm(dgem, (int)gem.size(), nb, nb, S, h->d_stat, s, &gx));
+      }
     } else {
       PhaseScope ps("lauum.gemm", s);
       if (S) ZTRY(oz_run_host(gbig.data(), (int)gbig.size(), S, tcw, tcw_bytes, h->d_stat, s));
@@ -674,8 +752,13 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s, const double* alpha, double* o
     }
     b0 = b1;
   }
+  if (overlap) {  // the caller's stream continues after the last batch (its reductions are already on it)
+    TLR_CUDA_TRY(cudaEventRecord(h->ev_join, s));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(s_user, h->ev_join, 0));
+    s = s_user;
+  }
   if (fused) {  // dl/dbeta, dl/dnu from the partial sums, in a fixed order
-    ZTRY(tlr_sum_pairs(h->gpart, (int64_t)tg.size() * tiles_per * 4, out3 + 1, h->scratch, s));
+    ZTRY(tlr_sum_pairs(h->gpart, part_pairs, out3 + 1, h->scratch, s));
   } else if (T > 0) {
     k_mark_all_dense<<<256, 256, 0, s>>>(h->dslotz, T);
     TLR_LAUNCH_CHECK();
