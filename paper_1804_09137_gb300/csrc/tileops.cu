@@ -324,6 +324,12 @@ __global__ void k_upd_d_desc(TlrView v, int alg, int k, const int2* __restrict__
 __global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
   const GemmGen g = desc[blockIdx.y];
   if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0 || g.k >= k_skip) return;
+  if (g.tA && !g.tB && g.beta == 0.0 && g.m <= 64 && g.n <= 64 && g.lda == g.k && g.ldb == g.k) {
+    // A^T B of two thin column blocks (ranks x depth): warps on 4 x 4 blocks of the small result, lanes
+    // along the depth, instead of a 64 x 64 block mostly outside it
+    if (blockIdx.x == 0) cta_gemm_tn_thin(g.m, g.n, g.k, g.alpha, g.A, g.B, g.C, g.ldc);
+    return;
+  }
   cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
                      gridDim.x, g.lower);
 }
