@@ -646,11 +646,14 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, doub
                                  ? (size_t)(reinterpret_cast<char*>(base + budget) - tcw) : 0;
     {
       PhaseScope ps("lauum.prep", s);
-      ZTRY(seg_copy(dcs, (int64_t)n_cs, s));
-      ZTRY(tops_gemm(dg1, (int)n_g1, mx_g, mx_g, s));
-      if (S) ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));
-      else ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
-      ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s));
+      { PhaseScope p1("lauum.prep.copy", s); ZTRY(seg_copy(dcs, (int64_t)n_cs, s)); }
+      { PhaseScope p1("lauum.prep.UtU", s); ZTRY(tops_gemm(dg1, (int)n_g1, mx_g, mx_g, s)); }
+      {
+        PhaseScope p1("lauum.prep.dense", s);
+        if (S) ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));
+        else ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
+      }
+      { PhaseScope p1("lauum.prep.VG", s); ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s)); }
     }
     if (fused) {
       // each target: operand A = [panel A | M_km^T ...], B = [panel B | M_kn^T ...] as k segments,

@@ -421,6 +421,72 @@ __device__ __forceinline__ void cta_gemm_df_blocks(int m, int n, int k, double a
   __syncthreads();
 }
 
+// The same in 128 x 32 blocks, for results of at most a few dozen columns (a dense tile or a tall
+// factor times a thin one): thread (row ty, column tx) of a 32 x 8 grid takes rows ty + 32 i and
+// columns tx + 8 j, so a 64-wide block is not mostly padding.
+__device__ __forceinline__ void cta_gemm_df_blocks_n32(int m, int n, int k, double alpha, const double* __restrict__ A,
+                                                       int lda, int tA, const double* __restrict__ B, int ldb, int tB,
+                                                       double beta, double* __restrict__ C, int ldc, int blk0,
+                                                       int nblk_step) {
+  __shared__ dfloat As[16][128 + 1];
+  __shared__ dfloat Bs[16][32 + 1];
+  const bool act = threadIdx.x < 256;
+  const int ty = threadIdx.x & 31, tx = (threadIdx.x >> 5) & 7;
+  const int mb = (m + 127) / 128, nbk = (n + 31) / 32;
+  for (int blk = blk0; blk < mb * nbk; blk += nblk_step) {
+    const int r0 = (blk % mb) * 128, c0 = (blk / mb) * 32;
+    float as[4][4], ae[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { as[i][j] = 0.f; ae[i][j] = 0.f; }
+    for (int k0 = 0; k0 < k; k0 += 16) {
+      __syncthreads();
+      for (int id = threadIdx.x; act && id < 128 * 16; id += 256) {
+        int a, kk;
+        if (!tA) { a = id & 127; kk = id >> 7; } else { kk = id & 15; a = id >> 4; }
+        const int ra = r0 + a, kc = k0 + kk;
+        double v = 0.0;
+        if (ra < m && kc < k) v = tA ? A[(size_t)ra * lda + kc] : A[(size_t)kc * lda + ra];
+        As[kk][a] = df_from_scaled(v, 0);
+      }
+      for (int id = threadIdx.x; act && id < 32 * 16; id += 256) {
+        int b, kk;
+        if (!tB) { kk = id & 15; b = id >> 4; } else { b = id & 31; kk = id >> 5; }
+        const int cb = c0 + b, kc = k0 + kk;
+        double v = 0.0;
+        if (cb < n && kc < k) v = tB ? B[(size_t)kc * ldb + cb] : B[(size_t)cb * ldb + kc];
+        Bs[kk][b] = df_from_scaled(v, 0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 16 && act; ++kk) {
+        dfloat av[4], bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 32 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 8 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_dot_add(as[i][j], ae[i][j], av[i], bv[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + ty + 32 * i, c = c0 + tx + 8 * j;
+        if (act && r < m && c < n) {
+          double* cp = C + (size_t)c * ldc + r;
+          const double v = df_to_scaled(df_norm(as[i][j], ae[i][j]), 0);
+          *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * v;
+        }
+      }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void cta_gemm_df(int m, int n, int k, double alpha, const double* A, int lda, int tA,
                                             const double* B, int ldb, int tB, double beta, double* C, int ldc) {
   cta_gemm_df_blocks(m, n, k, alpha, A, lda, tA, B, ldb, tB, beta, C, ldc, 0, 1, 0);

@@ -330,6 +330,11 @@ __global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
     if (blockIdx.x == 0) cta_gemm_tn_thin(g.m, g.n, g.k, g.alpha, g.A, g.B, g.C, g.ldc);
     return;
   }
+  if (g.n <= 32 && !g.lower) {  // a thin result: 128 x 32 blocks
+    cta_gemm_df_blocks_n32(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
+                           gridDim.x);
+    return;
+  }
   cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, blockIdx.x,
                      gridDim.x, g.lower);
 }
