@@ -216,7 +216,9 @@ PRECISION = {"storage": "f64", "potrf_trsv_logdet_quadform_gradient_sums": "f64"
                                          "range)",
              "inverse_depth_ge_256_contractions": "bf16 tensor cores (tcgen05) on 6 digit slices per float64 "
                                                   "operand, exact float32 accumulation of the leading slice "
-                                                  "groups: ~1e-12 of the operands' scale"}
+                                                  "groups: ~1e-12 of the operands' scale",
+             "gradient_derivative_polynomials": "float32 pairs (Horner on a double-float copy of the Matern "
+                                                "table's coefficients; distances, weights and sums in f64)"}
 
 
 def run_reference(a):

@@ -165,7 +165,7 @@ void free_ctx(tlr_ctx* h) {
   void* bufs[] = {h->x,     h->y,     h->perm,   h->D,     h->U,     h->V,      h->rank,   h->tab,
                   h->scratch, h->d_stat, h->d_vec, h->d_red, h->dslot, h->dpool, h->d_list, h->Dz,
                   h->Uz,    h->Vz,    h->rankz,  h->dslotz, h->dpoolz, h->d_zlist, h->linv, h->d_ctr, h->scratch_dd, h->msave, h->d_xk, h->dop, h->off, h->cap, h->top, h->offz, h->capz, h->topz,
-                  h->gpart};
+                  h->gpart, h->tabf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (h->aux) cudaStreamDestroy(h->aux);
@@ -306,6 +306,7 @@ int tlr_alloc(int64_t n, const tlr_opts* opts, tlr_ctx** out) {
   rc |= dmalloc(&h->rank, ct);
   rc |= dmalloc(&h->dslot, ct);
   rc |= dmalloc(&h->tab, TAB_ELEMS);
+  rc |= dmalloc(&h->tabf, TAB_ELEMS);
   rc |= dmalloc(&h->linv, (size_t)h->cap_nt * nb * nb);
   rc |= dmalloc(&h->d_stat, 4);
   rc |= dmalloc(&h->d_ctr, 4);

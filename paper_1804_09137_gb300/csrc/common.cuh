@@ -115,6 +115,7 @@ struct tlr_ctx {
   int64_t* zoff;      // [nt * ZPH + ZG + 1]
   int zplan_valid;
   double* tab;     // Matérn table (TAB_ELEMS)
+  float2* tabf;    // its coefficients as double-float pairs (TAB_ELEMS; absent in the allocation-free entry point)
   MaternParams mp;
   double* linv;    // nt tiles nb x nb: L_kk^{-1} of every diagonal tile (Cholesky, reused by the inverse)
   double* scratch; // batched-kernel workspace

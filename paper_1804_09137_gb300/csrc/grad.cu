@@ -9,6 +9,7 @@
 // dense tiles directly, low-rank tiles as U V^T formed 64 x 64 at a time in
 // registers.  Per-CTA partial sums are reduced in a fixed order.
 #include "tile.cuh"
+#include "df.cuh"
 
 namespace {
 
@@ -109,13 +110,23 @@ __global__ void k_grad_fused(TlrView z, const double* __restrict__ tab, const Ma
   }
 }
 
+// p(t) of one table interval with the coefficients as double-float pairs (Horner in double-float, about
+// 2^-44 relative; the float32 pipe issues 64 times the float64 rate on this GPU)
+__device__ __forceinline__ double tab_poly_df(const float2* __restrict__ c, dfloat t) {
+  dfloat s = c[TAB_DEG];
+#pragma unroll
+  for (int d = TAB_DEG - 1; d >= 0; --d) s = df_add(df_mul(s, t), c[d]);
+  return df_to_scaled(s, 0);
+}
+
 // The same sums over a batch of dense tiles of Z = Sigma^{-1} (the LAUUM's products, nb x nb each,
 // column-major, tile t of the batch at Z + t nb^2, target (m, n) = tg[t]): CTA (blk, t) takes the
 // 64 x 64 block blk of tile t, thread (row a, column parity) its 32 entries (a, c0 + parity + 2 j), so
 // each warp reads 32 consecutive rows of one column.  The partial pair goes to part[2 (slot0 + t mb^2 +
-// blk)], written even for a block with nothing to add.
+// blk)], written even for a block with nothing to add.  The derivative polynomials run in double-float
+// (coefficient pairs tabf), the distance, the weights and the sums in float64.
 __global__ void __launch_bounds__(128) k_grad_tiles(const int2* __restrict__ tg, const double* __restrict__ Z, int nb,
-                                                    int64_t slot0, const double* __restrict__ tab,
+                                                    int64_t slot0, const float2* __restrict__ tabf,
                                                     const MaternParams mp, const double* __restrict__ x,
                                                     const double* __restrict__ y, int64_t n,
                                                     const double* __restrict__ al, double* __restrict__ part) {
@@ -142,8 +153,9 @@ __global__ void __launch_bounds__(128) k_grad_tiles(const int2* __restrict__ tg,
       const int jt = tab_locate(r, mp.e_lo, &tt);
       if (jt < 0 || jt >= TAB_NINT) continue;  // below the table the derivatives vanish
       const double w = wa * al[pb] - Zt[(size_t)b * nb + a];
-      g1 = fma(w, tab_poly(tab + (size_t)(TAB_NINT + jt) * TAB_NC, tt), g1);
-      g2 = fma(w, tab_poly(tab + (size_t)(2 * TAB_NINT + jt) * TAB_NC, tt), g2);
+      const dfloat td = df_from_scaled(tt, 0);
+      g1 = fma(w, tab_poly_df(tabf + (size_t)(TAB_NINT + jt) * TAB_NC, td), g1);
+      g2 = fma(w, tab_poly_df(tabf + (size_t)(2 * TAB_NINT + jt) * TAB_NC, td), g2);
     }
   }
   g1 = warp_sum(g1);
@@ -226,9 +238,9 @@ int tlr_grad_fused(tlr_ctx* h, const double* alpha, double* out3, cudaStream_t s
 int tlr_grad_tiles(const tlr_ctx* h, const int2* tg, int cnt, const double* Z, int64_t slot0, const double* alpha,
                    double* part, cudaStream_t s) {
   if (cnt <= 0) return TLR_OK;
-  if (cnt > 65535) return TLR_ERR_STATE;
+  if (cnt > 65535 || !h->tabf) return TLR_ERR_STATE;
   const int mb = (h->nb + 63) / 64;
-  k_grad_tiles<<<dim3(mb * mb, cnt), 128, 0, s>>>(tg, Z, h->nb, slot0, h->tab, h->mp, h->x, h->y, h->n, alpha, part);
+  k_grad_tiles<<<dim3(mb * mb, cnt), 128, 0, s>>>(tg, Z, h->nb, slot0, h->tabf, h->mp, h->x, h->y, h->n, alpha, part);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }

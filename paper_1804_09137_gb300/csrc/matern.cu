@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace {
 
@@ -104,6 +105,12 @@ __global__ void k_gen_diag(const double* __restrict__ tab, const MaternParams mp
   }
 }
 
+// the coefficients as double-float pairs (bit conversion; magnitudes below 2^-126 become zero)
+__global__ void k_tab_df(const double* __restrict__ tab, float2* __restrict__ tabf) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id < TAB_ELEMS) tabf[id] = df_from_scaled(tab[id], 0);
+}
+
 }  // namespace
 
 int tlr_build_table(tlr_ctx* h, cudaStream_t s) {
@@ -113,6 +120,10 @@ int tlr_build_table(tlr_ctx* h, cudaStream_t s) {
   TLR_LAUNCH_CHECK();
   k_tab_coefs<<<(TAB_NFUN * TAB_NINT + 127) / 128, 128, 0, s>>>(vals, h->tab);
   TLR_LAUNCH_CHECK();
+  if (h->tabf) {
+    k_tab_df<<<(TAB_ELEMS + 255) / 256, 256, 0, s>>>(h->tab, h->tabf);
+    TLR_LAUNCH_CHECK();
+  }
   h->tab_valid = 1;
   return TLR_OK;
 }
