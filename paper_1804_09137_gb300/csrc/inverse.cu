@@ -647,7 +647,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, doub
     {
       PhaseScope ps("lauum.prep", s);
       { PhaseScope p1("lauum.prep.copy", s); ZTRY(seg_copy(dcs, (int64_t)n_cs, s)); }
-      { PhaseScope p1("lauum.prep.UtU", s); ZTRY(tops_gemm(dg1, (int)n_g1, mx_g, mx_g, s)); }
+      { PhaseScope p1("lauum.prep.UtU", s); ZTRY(tops_gemm_thin(dg1, (int)n_g1, s)); }
       {
         PhaseScope p1("lauum.prep.dense", s);
         if (S) ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));

@@ -530,6 +530,53 @@ __device__ void cta_gemm_tn_thin(int ka, int kb, int nb, double alpha, const dou
   __syncthreads();
 }
 
+// The same with four rows per lane in flight (every load of a group issued before its products):
+// for a kernel that has nothing else to hide the load latency behind.
+__device__ void cta_gemm_tn_thin4(int ka, int kb, int nb, double alpha, const double* __restrict__ P,
+                                  const double* __restrict__ Q, double* __restrict__ W, int ldw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int ba = (ka + 3) >> 2, bb = (kb + 3) >> 2;
+  for (int blk = warp; blk < ba * bb; blk += nw) {
+    const int a0 = (blk % ba) * 4, b0 = (blk / ba) * 4;
+    float s[4][4], c[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
+    for (int r0 = lane; r0 < nb; r0 += 128) {
+      double pv[4][4], qv[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 32 * u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pv[u][i] = (r < nb && a0 + i < ka) ? P[(size_t)(a0 + i) * nb + r] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qv[u][j] = (r < nb && b0 + j < kb) ? Q[(size_t)(b0 + j) * nb + r] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        dfloat pa[4], qb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pa[i] = df_from_scaled(pv[u][i], 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qb[j] = df_from_scaled(qv[u][j], 0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_dot_add(s[i][j], c[i][j], pa[i], qb[j]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const dfloat v = df_warp_sum(df_norm(s[i][j], c[i][j]));
+        if (lane == 0 && a0 + i < ka && b0 + j < kb) W[(size_t)(b0 + j) * ldw + a0 + i] = alpha * df_to_scaled(v, 0);
+      }
+  }
+  __syncthreads();
+}
+
 // C[r + b nb] = alpha sum_l A[r + l nb] op(W)[l, b] for r < nb, b < kb, depth ka, with op(W)[l, b] =
 // W[l + b ldw] (tw = 0) or W[b + l ldw]: a thread per row (two at a time), 8 output columns at a time, op(W) staged as
 // double-float in shared memory 64 x 8 at a time.

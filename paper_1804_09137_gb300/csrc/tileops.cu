@@ -321,6 +321,17 @@ __global__ void k_upd_d_desc(TlrView v, int alg, int k, const int2* __restrict__
   d2[q] = g2;
 }
 
+// products A^T B of two thin column blocks (results up to 64 x 64, lda = ldb = depth, beta = 0), a CTA
+// per descriptor; any other descriptor takes the 64 x 64 block path
+__global__ void __launch_bounds__(256) k_gemm_tn_thin(const GemmGen* __restrict__ desc) {
+  const GemmGen g = desc[blockIdx.x];
+  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0) return;
+  if (g.tA && !g.tB && g.beta == 0.0 && g.m <= 64 && g.n <= 64 && g.lda == g.k && g.ldb == g.k)
+    cta_gemm_tn_thin4(g.m, g.n, g.k, g.alpha, g.A, g.B, g.C, g.ldc);
+  else
+    cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, 0, 1, g.lower);
+}
+
 __global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
   const GemmGen g = desc[blockIdx.y];
   if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0 || g.k >= k_skip) return;
@@ -615,6 +626,15 @@ int resident_pairs(int nb) {
 }  // namespace
 
 bool tops_cluster_mode() { return upd_pair_mode(); }
+
+int tops_gemm_thin(const GemmGen* d_desc, int count, cudaStream_t s) {
+  for (int c0 = 0; c0 < count; c0 += 1 << 30) {
+    const int cnt = count - c0 < (1 << 30) ? count - c0 : (1 << 30);
+    k_gemm_tn_thin<<<cnt, 256, 0, s>>>(d_desc + c0);
+    TLR_LAUNCH_CHECK();
+  }
+  return TLR_OK;
+}
 
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip) {
   if (count <= 0) return TLR_OK;

@@ -48,4 +48,6 @@ bool tops_cluster_mode();
 // batched general GEMM from a device descriptor array
 // (descriptors with k >= k_skip are left out: another path computes them)
 int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30);
+// the same for products mostly A^T B of thin column blocks (one CTA a descriptor, four rows a lane in flight)
+int tops_gemm_thin(const GemmGen* d_desc, int count, cudaStream_t s);
 
