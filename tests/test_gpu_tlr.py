@@ -376,3 +376,25 @@ def test_cluster_split_equals_one_cta_bit_for_bit(T):
         assert r.returncode == 0, r.stderr[-2000:]
         out.append(r.stdout.strip().splitlines()[-1])
     assert out[0] == out[1], out
+
+
+def test_lauum_overlapped_reduction_matches_epilogue_reduction(T):
+    """The gradient's reduction of each LAUUM batch by its own kernel beside the next batch's products
+    (default) and inside the tensor-core epilogue (TLR_LAUUM_OVERLAP=0) sum the same entries in another
+    order, the first with double-float derivative polynomials: l and dl/dsigma2 agree bit for bit, dl/dbeta
+    and dl/dnu to 1e-9 relative (n = 2,500, 10 tiles, eps = 1e-9)."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    vals = []
+    for mode in ("1", "0"):
+        env = dict(os.environ, TLR_LAUUM_OVERLAP=mode)
+        r = subprocess.run([sys.executable, "-c", _CHILD, root], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        vals.append([float.fromhex(v) for v in r.stdout.strip().splitlines()[-1].split()])
+    (l1, s1, b1, n1), (l0, s0, b0, n0) = vals
+    assert l1 == l0 and s1 == s0
+    assert abs(b1 - b0) <= 1e-9 * abs(b0) and abs(n1 - n0) <= 1e-9 * abs(n0), vals
