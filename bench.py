@@ -55,8 +55,15 @@ def bf16_peak():
     except (OSError, ValueError):
         pass
     return BF16_FALLBACK_TFLOPS, "fallback (1.7 PFLOP/s sustained, earlier GB300 measurement)"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_upd_lr_gen_n22400.json")
-KERNEL_SOURCES = ["tileops.cu", "recompress.cuh", "tile.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_n22500.json")
+# the source each kernel's DRAM figure was measured on: (file, first marker, end marker or None)
+KERNEL_SOURCES = {
+    "k_upd_lr_pair": [("tileops.cu", None, "__global__ void k_upd_d_desc"), ("recompress.cuh", None, None),
+                      ("tile.cuh", None, None), ("df.cuh", None, None)],
+    "k_oz_gemm": [("tcgemm.cu", "// ------------------------------------------------------------------ GEMM",
+                   "int launch_split("), ("tcgemm.h", "#define OZ_BM", "size_t oz_slices_elems("),
+                  ("df.cuh", None, None)],
+}
 
 
 def _code_only(src: str) -> str:
@@ -66,14 +73,30 @@ def _code_only(src: str) -> str:
     return re.sub(r"\s+", "", src)
 
 
-def kernel_hash():
-    """Hash of the dominant kernel's source code (comments and layout excluded): a DRAM traffic
-    figure measured on another code state is not reported."""
+def kernel_hash(kernel="k_upd_lr_pair"):
+    """Hash of a kernel's source code (the parts of the files it is built from; comments and layout
+    excluded): a DRAM traffic figure measured on another code state is not reported."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f, start, end in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1804_09137_gb300", "csrc", f), encoding="utf-8") as fh:
-            h.update(_code_only(fh.read()).encode())
+            src = fh.read()
+        if start is not None:
+            src = src[src.index(start):]
+        if end is not None:
+            src = src[:src.index(end)]
+        h.update(_code_only(src).encode())
     return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` at the benchmark's size, from the committed ncu summary, when it
+    was taken on the present source of that kernel (else None)."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh).get(kernel, {})
+    except (OSError, ValueError):
+        return None
+    return tr.get("dram_bytes_per_launch_n90000") if tr.get("source_sha") == kernel_hash(kernel) else None
 
 
 def args_():
@@ -806,12 +829,7 @@ def main():
 
     # ---- roofline of the dominant kernel (low-rank update with recompression)
     achieved = prof["flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] > 0 else None
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as fh:
-            tr = json.load(fh)
-        if tr.get("source_sha") == kernel_hash():
-            traffic = tr.get("dram_bytes_per_launch")
+    traffic = measured_traffic("k_upd_lr_pair")
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
             "kernel": "k_upd_lr_pair", "launches": prof["launches"], "kernel_ms_per_step": prof["ms"] / a.steps,
@@ -825,7 +843,7 @@ def main():
     roof_tc = {"bound": "tensor", "kernel": "k_oz_gemm", "achieved": tc_ach, "peak": bpk, "unit": "TFLOP/s",
                "frac": (tc_ach / bpk) if tc_ach else None, "peak_source": bsrc, "launches": prof_tc["launches"],
                "kernel_ms_per_step": prof_tc["ms"] / a.steps, "mma_flops_per_step": prof_tc["flops"] / a.steps,
-               "traffic": None}
+               "traffic": measured_traffic("k_oz_gemm")}
 
     accuracy = None
     if dense is not None:
