@@ -650,18 +650,8 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, doub
       { PhaseScope p1("lauum.prep.UtU", s); ZTRY(tops_gemm_thin(dg1, (int)n_g1, s)); }
       {
         PhaseScope p1("lauum.prep.dense", s);
-        const int n_keep = tops_thin_n();
-        if (S && n_keep > 0) {  // thin results on the CUDA cores, the others on the tensor cores
-          std::vector<GemmGen> wide;
-          for (const GemmGen& g : g1b)
-            if (g.n > n_keep) wide.push_back(g);
-          if (!wide.empty()) ZTRY(oz_run_host(wide.data(), (int)wide.size(), S, tcw, tcw_bytes, h->d_stat, s));
-          ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s, 1, n_keep));
-        } else if (S) {
-          ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));
-        } else {
-          ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
-        }
+        if (S) ZTRY(oz_run_host(g1b.data(), (int)g1b.size(), S, tcw, tcw_bytes, h->d_stat, s));
+        else ZTRY(tops_gemm(dg1b, (int)n_g1b, nb, mx_r, s));
       }
       { PhaseScope p1("lauum.prep.VG", s); ZTRY(tops_gemm(dg2, (int)n_g2, nb, mx_r, s)); }
     }

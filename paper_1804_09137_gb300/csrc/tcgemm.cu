@@ -714,7 +714,7 @@ int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, l
 namespace {
 // descriptor q -> split descriptors 2q (op(A)), 2q + 1 (op(B)^T) and GEMM descriptor q with fixed-size
 // buffers at base + q per
-__device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_min, int n_min, char* __restrict__ base,
+__device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_min, char* __restrict__ base,
                                                size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per,
                                                OzSrc* a, OzSrc* b, OzGemm* og) {
   char* p = base + (size_t)q * per;
@@ -722,7 +722,7 @@ __device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_mi
   uint16_t* sb = reinterpret_cast<uint16_t*>(p + sa_bytes);
   int* xa = reinterpret_cast<int*>(p + sa_bytes + sb_bytes);
   int* xb = reinterpret_cast<int*>(p + sa_bytes + sb_bytes + xa_bytes);
-  const bool run = x.m > 0 && x.n > n_min && x.k >= k_min && x.k > 0;
+  const bool run = x.m > 0 && x.n > 0 && x.k >= k_min && x.k > 0;
   a->X = x.A; a->ld = x.lda; a->col = x.tA ? 0 : 1; a->rows = run ? x.m : 0; a->depth = x.k; a->out = sa; a->ex = xa;
   a->block_rows = OZ_BM; a->kb0 = 0; a->nkb = 0; a->multi = 0;
   b->X = x.B; b->ld = x.ldb; b->col = x.tB ? 1 : 0; b->rows = run ? x.n : 0; b->depth = x.k; b->out = sb; b->ex = xb;
@@ -739,27 +739,26 @@ __device__ __forceinline__ void descs_from_gen(const GemmGen& x, int q, int k_mi
 // descriptors, depth chunk blockIdx.y; the first CTA of each side-0 operand also stores the GEMM
 // descriptor for the product kernel
 template <int S>
-__global__ void __launch_bounds__(256) k_oz_slice_gen(const GemmGen* __restrict__ g, int k_min, int n_min,
-                                                      char* __restrict__ base,
+__global__ void __launch_bounds__(256) k_oz_slice_gen(const GemmGen* __restrict__ g, int k_min, char* __restrict__ base,
                                                       size_t sa_bytes, size_t sb_bytes, size_t xa_bytes, size_t per,
                                                       OzGemm* __restrict__ gem, int qpc) {
   const int z = blockIdx.z, q = z >> 1;
   OzSrc a, b;
   OzGemm og;
-  descs_from_gen(g[q], q, k_min, n_min, base, sa_bytes, sb_bytes, xa_bytes, per, &a, &b, &og);
+  descs_from_gen(g[q], q, k_min, base, sa_bytes, sb_bytes, xa_bytes, per, &a, &b, &og);
   if (!(z & 1) && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) gem[q] = og;
   slice_rows<S>((z & 1) ? b : a, blockIdx.x * 32, blockIdx.y * qpc, (blockIdx.y + 1) * qpc);
 }
 
 template <int S>
-int launch_split_gen(const GemmGen* d_g, int cnt, int k_min, int n_min, char* base, size_t sa, size_t sb, size_t xa,
-                     size_t per, OzGemm* gem, int max_rows, int max_depth, cudaStream_t s) {
+int launch_split_gen(const GemmGen* d_g, int cnt, int k_min, char* base, size_t sa, size_t sb, size_t xa, size_t per,
+                     OzGemm* gem, int max_rows, int max_depth, cudaStream_t s) {
   const int rows_pad = round_up(std::max(max_rows, 1), OZ_BM);
   const int depth_pad = round_up(std::max(max_depth, 1), OZ_BK);
   // 2 cnt operands; callers keep cnt <= 32767
   const int qpc = slice_chunk_octets(rows_pad, depth_pad, 2 * cnt);
   k_oz_slice_gen<S><<<dim3(rows_pad / 32, (depth_pad / 8 + qpc - 1) / qpc, 2 * cnt), dim3(32, 8), 0, s>>>(
-      d_g, k_min, n_min, base, sa, sb, xa, per, gem, qpc);
+      d_g, k_min, base, sa, sb, xa, per, gem, qpc);
   TLR_LAUNCH_CHECK();
   return TLR_OK;
 }
@@ -772,7 +771,7 @@ size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S) {
 }
 
 int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k, int k_min, int S, void* ws,
-                  size_t ws_bytes, long long* d_stat, cudaStream_t s, int n_min) {
+                  size_t ws_bytes, long long* d_stat, cudaStream_t s) {
   if (count <= 0) return TLR_OK;
   const size_t sa = align128(oz_slices_elems(max_m, max_k, OZ_BM, S) * 2);
   const size_t sb = align128(oz_slices_elems(max_n, max_k, OZ_BN, S) * 2);
@@ -789,9 +788,9 @@ int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k
     OzGemm* gem = reinterpret_cast<OzGemm*>(descs + align128((size_t)2 * cnt * sizeof(OzSrc)));
     int rc;
     switch (S) {
-      case 4: rc = launch_split_gen<4>(d_g + q0, cnt, k_min, n_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
-      case 5: rc = launch_split_gen<5>(d_g + q0, cnt, k_min, n_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
-      case 6: rc = launch_split_gen<6>(d_g + q0, cnt, k_min, n_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
+      case 4: rc = launch_split_gen<4>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
+      case 5: rc = launch_split_gen<5>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
+      case 6: rc = launch_split_gen<6>(d_g + q0, cnt, k_min, base, sa, sb, xa, per, gem, std::max(max_m, max_n), max_k, s); break;
       default: rc = -1;
     }
     if (rc) return rc;

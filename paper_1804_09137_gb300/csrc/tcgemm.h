@@ -88,10 +88,10 @@ size_t oz_slices_elems(int rows, int depth, int block_rows, int S);
 // one GEMM alone does not fit.  Time-outs are recorded in d_stat.
 int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, long long* d_stat, cudaStream_t s);
 // The same for descriptors in device memory (written by a kernel): every entry has m <= max_m,
-// n <= max_n, k <= max_k; slice buffers are sized for those bounds.  Entries with k < k_min or n <= n_min
-// are skipped (left to the caller's CUDA-core path, which must skip the others).
+// n <= max_n, k <= max_k; slice buffers are sized for those bounds.  Entries with k < k_min are
+// skipped (left to the caller's CUDA-core path, which must skip k >= k_min).
 int oz_run_device(const GemmGen* d_g, int count, int max_m, int max_n, int max_k, int k_min, int S, void* ws,
-                  size_t ws_bytes, long long* d_stat, cudaStream_t s, int n_min = 0);
+                  size_t ws_bytes, long long* d_stat, cudaStream_t s);
 // bytes of workspace oz_run_device needs per descriptor for these bounds
 size_t oz_device_item_bytes(int max_m, int max_n, int max_k, int S);
 // split `count` operands (descriptors on the device); max_rows / max_depth bound the grid.

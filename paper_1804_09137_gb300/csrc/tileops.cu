@@ -332,9 +332,9 @@ __global__ void __launch_bounds__(256) k_gemm_tn_thin(const GemmGen* __restrict_
     cta_gemm_df_blocks(g.m, g.n, g.k, g.alpha, g.A, g.lda, g.tA, g.B, g.ldb, g.tB, g.beta, g.C, g.ldc, 0, 1, g.lower);
 }
 
-__global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip, int n_keep) {
+__global__ void k_gemm_gen(const GemmGen* __restrict__ desc, int k_skip) {
   const GemmGen g = desc[blockIdx.y];
-  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0 || (g.k >= k_skip && g.n > n_keep)) return;
+  if ((g.k <= 0 && g.beta == 1.0) || g.m <= 0 || g.n <= 0 || g.k >= k_skip) return;
   if (g.tA && !g.tB && g.beta == 0.0 && g.m <= 64 && g.n <= 64 && g.lda == g.k && g.ldb == g.k) {
     // A^T B of two thin column blocks (ranks x depth): warps on 4 x 4 blocks of the small result, lanes
     // along the depth, instead of a 64 x 64 block mostly outside it
@@ -627,15 +627,6 @@ int resident_pairs(int nb) {
 
 bool tops_cluster_mode() { return upd_pair_mode(); }
 
-int tops_thin_n() {
-  static int mode = -1;
-  if (mode < 0) {
-    const char* e = getenv("TLR_THIN_TC");
-    mode = (e && atoi(e) == 0) ? 0 : 1;
-  }
-  return mode == 1 ? 0 : 32;
-}
-
 int tops_gemm_thin(const GemmGen* d_desc, int count, cudaStream_t s) {
   for (int c0 = 0; c0 < count; c0 += 1 << 30) {
     const int cnt = count - c0 < (1 << 30) ? count - c0 : (1 << 30);
@@ -645,12 +636,12 @@ int tops_gemm_thin(const GemmGen* d_desc, int count, cudaStream_t s) {
   return TLR_OK;
 }
 
-int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip, int n_keep) {
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip) {
   if (count <= 0) return TLR_OK;
   const int blocks = ((m + 63) / 64) * ((n + 63) / 64);
   for (int c0 = 0; c0 < count; c0 += 65535) {
     const int cnt = count - c0 < 65535 ? count - c0 : 65535;
-    k_gemm_gen<<<dim3(blocks, cnt), 256, 0, s>>>(d_desc + c0, k_skip, n_keep);
+    k_gemm_gen<<<dim3(blocks, cnt), 256, 0, s>>>(d_desc + c0, k_skip);
     TLR_LAUNCH_CHECK();
   }
   return TLR_OK;
@@ -674,10 +665,9 @@ int tops_gemm_mixed(tlr_ctx* h, const GemmGen* d_desc, int count, int m, int n, 
                     cudaStream_t s, bool all_deep = false) {
   const int S = tlr_tc_slices(h);
   if (!S || kmax < TC_MIN_DEPTH || !tc_doubles) return tops_gemm(d_desc, count, m, n, s);
-  const int n_keep = tops_thin_n();
-  int rc = oz_run_device(d_desc, count, m, n, kmax, TC_MIN_DEPTH, S, tc, tc_doubles * 8, h->d_stat, s, n_keep);
-  if (rc || (all_deep && n_keep == 0)) return rc;
-  return tops_gemm(d_desc, count, m, n, s, TC_MIN_DEPTH, n_keep);
+  int rc = oz_run_device(d_desc, count, m, n, kmax, TC_MIN_DEPTH, S, tc, tc_doubles * 8, h->d_stat, s);
+  if (rc || all_deep) return rc;
+  return tops_gemm(d_desc, count, m, n, s, TC_MIN_DEPTH);
 }
 }  // namespace
 

@@ -46,13 +46,8 @@ int tlr_smem_optin(const void* f, size_t dyn);
 // selects one CTA each)
 bool tops_cluster_mode();
 // batched general GEMM from a device descriptor array
-// (descriptors with k >= k_skip and more than n_keep columns are left out: another path computes them)
-int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30,
-              int n_keep = 0);
-// results with at most this many columns stay on the CUDA cores at any depth (0: every product of depth
-// >= 256 in the gradient's inverse goes to the tensor cores; 32 when the environment variable TLR_THIN_TC
-// is 0)
-int tops_thin_n();
+// (descriptors with k >= k_skip are left out: another path computes them)
+int tops_gemm(const GemmGen* d_desc, int count, int m, int n, cudaStream_t s, int k_skip = 1 << 30);
 // the same for products mostly A^T B of thin column blocks (one CTA a descriptor, four rows a lane in flight)
 int tops_gemm_thin(const GemmGen* d_desc, int count, cudaStream_t s);
 
