@@ -1,6 +1,6 @@
 // C ABI entry points (include/tlr.h) and the host-side drivers.
 //
-// The driver owns the ordering of the tile algorithm; each step is a batched
+// The host code owns the ordering of the tile algorithm; each step is a batched
 // launch over every tile it touches, enqueued on the caller's stream.  The
 // Morton ordering of the points (setup, once per handle) runs on the host.
 #include <math.h>
