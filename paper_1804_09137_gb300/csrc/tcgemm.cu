@@ -25,6 +25,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "df.cuh"
@@ -651,47 +653,75 @@ size_t oz_item_bytes(const GemmGen& g, int S) {
 }  // namespace
 
 int oz_run_host(const GemmGen* g, int count, int S, void* ws, size_t ws_bytes, long long* d_stat, cudaStream_t s) {
+  // An operand that several products of a chunk share (the same matrix, layout and extent, e.g. one dense
+  // tile against many thin factors) is split once and its slices read by all of them.
+  struct Key {
+    const double* X;
+    int ld, col, rows, depth, block_rows;
+    bool operator<(const Key& o) const {
+      return std::tie(X, ld, col, rows, depth, block_rows) < std::tie(o.X, o.ld, o.col, o.rows, o.depth, o.block_rows);
+    }
+  };
   char* base = static_cast<char*>(ws);
   int q0 = 0;
   while (q0 < count) {
-    // greedy chunk within the workspace: slices and exponents first, descriptors at the end
-    size_t need = 256;
-    int q1 = q0;
-    while (q1 < count && need + oz_item_bytes(g[q1], S) <= ws_bytes) need += oz_item_bytes(g[q1++], S);
-    if (q1 == q0) TLR_RETURN_OOM();
     std::vector<OzSrc> src;
     std::vector<OzGemm> gem;
+    std::map<Key, std::pair<uint16_t*, int*>> seen;
     char* p = base;
     int max_rows = 1, max_depth = 1, max_m = 1, max_n = 1;
-    for (int q = q0; q < q1; ++q) {
-      const GemmGen& x = g[q];
-      if (x.m <= 0 || x.n <= 0) continue;
+    int q1 = q0;
+    // greedy chunk within the workspace: slices and exponents first, descriptors at the end
+    auto fits = [&](size_t slice_bytes, size_t n_src, size_t n_gem) {
+      return (size_t)(p - base) + slice_bytes + align128(n_src * sizeof(OzSrc)) + align128(n_gem * sizeof(OzGemm)) +
+                 256 <= ws_bytes;
+    };
+    for (; q1 < count; ++q1) {
+      const GemmGen& x = g[q1];
       OzGemm og;
       memset(&og, 0, sizeof(og));
       og.C = x.C; og.ldc = x.ldc; og.m = x.m; og.n = x.n; og.alpha = x.alpha; og.beta = x.beta; og.lower = x.lower;
+      if (x.m <= 0 || x.n <= 0) continue;
+      if (x.k <= 0) {
+        if (!fits(0, src.size(), gem.size() + 1)) break;
+        gem.push_back(og);
+        max_m = std::max(max_m, x.m);
+        max_n = std::max(max_n, x.n);
+        continue;
+      }
+      // rows of op(A): (r, c) at A[c lda + r] unless transposed; rows of op(B)^T: (j, c) at B[j ldb + c]
+      // unless transposed
+      const Key ka{x.A, x.lda, x.tA ? 0 : 1, x.m, x.k, OZ_BM}, kb{x.B, x.ldb, x.tB ? 1 : 0, x.n, x.k, OZ_BN};
+      const bool new_a = !seen.count(ka), nb_new = !seen.count(kb);  // ka != kb: their block rows differ
+      auto bytes_of = [&](const Key& k) {
+        return align128(oz_slices_elems(k.rows, k.depth, k.block_rows, S) * 2) +
+               align128((size_t)round_up(k.rows, k.block_rows) * 4);
+      };
+      const size_t add = (new_a ? bytes_of(ka) : 0) + (nb_new ? bytes_of(kb) : 0);
+      if (!fits(add, src.size() + (new_a ? 1 : 0) + (nb_new ? 1 : 0), gem.size() + 1)) break;
+      auto place = [&](const Key& k) -> std::pair<uint16_t*, int*> {
+        auto it = seen.find(k);
+        if (it != seen.end()) return it->second;
+        uint16_t* sl = reinterpret_cast<uint16_t*>(p);
+        p += align128(oz_slices_elems(k.rows, k.depth, k.block_rows, S) * 2);
+        int* ex = reinterpret_cast<int*>(p);
+        p += align128((size_t)round_up(k.rows, k.block_rows) * 4);
+        src.push_back({k.X, k.ld, k.col, k.rows, k.depth, sl, ex, k.block_rows});
+        seen[k] = {sl, ex};
+        max_rows = std::max(max_rows, k.rows);
+        return {sl, ex};
+      };
+      const auto pa = place(ka);
+      const auto pb = place(kb);
+      const int nkb = round_up(x.k, OZ_BK) / OZ_BK;
+      og.a = {pa.first, pa.second, x.m, nkb};
+      og.b = {pb.first, pb.second, x.n, nkb};
+      max_depth = std::max(max_depth, x.k);
       max_m = std::max(max_m, x.m);
       max_n = std::max(max_n, x.n);
-      if (x.k > 0) {
-        uint16_t* sa = reinterpret_cast<uint16_t*>(p);
-        p += align128(oz_slices_elems(x.m, x.k, OZ_BM, S) * 2);
-        uint16_t* sb = reinterpret_cast<uint16_t*>(p);
-        p += align128(oz_slices_elems(x.n, x.k, OZ_BN, S) * 2);
-        int* xa = reinterpret_cast<int*>(p);
-        p += align128((size_t)round_up(x.m, OZ_BM) * 4);
-        int* xb = reinterpret_cast<int*>(p);
-        p += align128((size_t)round_up(x.n, OZ_BN) * 4);
-        // rows of op(A): (r, c) at A[c lda + r] unless transposed; rows of op(B)^T: (j, c) at B[j ldb + c]
-        // unless transposed
-        src.push_back({x.A, x.lda, x.tA ? 0 : 1, x.m, x.k, sa, xa, OZ_BM});
-        src.push_back({x.B, x.ldb, x.tB ? 1 : 0, x.n, x.k, sb, xb, OZ_BN});
-        const int nkb = round_up(x.k, OZ_BK) / OZ_BK;
-        og.a = {sa, xa, x.m, nkb};
-        og.b = {sb, xb, x.n, nkb};
-        max_rows = std::max(max_rows, std::max(x.m, x.n));
-        max_depth = std::max(max_depth, x.k);
-      }
       gem.push_back(og);
     }
+    if (q1 == q0) TLR_RETURN_OOM();
     char* dp = reinterpret_cast<char*>(align128(reinterpret_cast<size_t>(p)));
     OzSrc* dsrc = reinterpret_cast<OzSrc*>(dp);
     dp += align128(src.size() * sizeof(OzSrc));
