@@ -21,3 +21,31 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["measured_n"] == 64 and line["cpu_baseline"]["measured_s"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_traffic_figure_follows_the_kernel_source(tmp_path):
+    """The DRAM traffic in the bench line comes from the committed ncu summary only while the measured
+    kernel's source is unchanged: comments and layout do not count, code does."""
+    import importlib.util
+    import shutil
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    csrc = tmp_path / "paper_1804_09137_gb300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_1804_09137_gb300", "csrc"), csrc,
+                    ignore=shutil.ignore_patterns("*.so", "*.o", "_build*"))
+    (tmp_path / "profiles").mkdir()
+    shutil.copy(os.path.join(ROOT, "profiles", "dram_traffic_n22500.json"), tmp_path / "profiles")
+    b.ROOT = str(tmp_path)
+    b.TRAFFIC_FILE = str(tmp_path / "profiles" / "dram_traffic_n22500.json")
+    h0 = b.kernel_hash("k_upd_lr_pair")
+    src = (csrc / "recompress.cuh").read_text()
+    (csrc / "recompress.cuh").write_text(src + "\n// a comment only\n\n")
+    assert b.kernel_hash("k_upd_lr_pair") == h0
+    (csrc / "recompress.cuh").write_text(src + "\n__device__ int an_extra_function() { return 1; }\n")
+    assert b.kernel_hash("k_upd_lr_pair") != h0
+    assert b.measured_traffic("k_upd_lr_pair") is None
+    (csrc / "tcgemm.cu").write_text((csrc / "tcgemm.cu").read_text() + "\n// another comment\n")
+    ok = b.measured_traffic("k_oz_gemm")
+    assert ok is None or ok > 0
