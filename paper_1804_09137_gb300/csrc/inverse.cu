@@ -505,6 +505,15 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, doub
     TLR_CUDA_TRY(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     s = h->aux;
   }
+  // on every way out, including an error inside the batch loop, the caller's stream waits for the
+  // second one, so that nothing the LAUUM enqueued there outlives the call unordered
+  struct Join {
+    tlr_ctx* h;
+    cudaStream_t from, to;
+    ~Join() {
+      if (from != to && cudaEventRecord(h->ev_join, from) == cudaSuccess) cudaStreamWaitEvent(to, h->ev_join, 0);
+    }
+  } join{h, s, s_user};
   int nbatch = 0;
   size_t b0 = 0;
   std::vector<char> host;
@@ -758,6 +767,7 @@ static int lauum_left(tlr_ctx* h, cudaStream_t s_user, const double* alpha, doub
   if (overlap) {  // the caller's stream continues after the last batch (its reductions are already on it)
     TLR_CUDA_TRY(cudaEventRecord(h->ev_join, s));
     TLR_CUDA_TRY(cudaStreamWaitEvent(s_user, h->ev_join, 0));
+    join.from = join.to;  // joined
     s = s_user;
   }
   if (fused) {  // dl/dbeta, dl/dnu from the partial sums, in a fixed order
