@@ -66,7 +66,9 @@ typedef struct {
  * gradient's inverse keeps L^{-1} in tile low-rank form truncated at
  * inv_scale * eps * zeta^(1/2), zeta = the largest 1 / L_aa^2 (0 = 1: the same
  * truncation relative to the size of L^{-1} as eps is to Sigma);
- * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile.
+ * Sigma^{-1} = L^{-T} L^{-1} is then formed densely tile by tile, a batch of
+ * tiles at a time, each batch reduced into the gradient and overwritten by a
+ * later one (with tensor cores; the double-float path keeps every tile).
  * metric: 0 = Euclidean distance; 1 = great-circle distance of eq. 6 (Sec. IV,
  * haversine) with x = longitude and y = latitude in degrees (also for the new
  * points of tlr_predict / tlr_predict_var) on a sphere of the given radius
